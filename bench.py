@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark of the multirate DG shallow-water hot path on GB300.
+
+Metric: DOF-updates/s per RHS stage = (sum over finest substeps of active
+elements x Np x 3) / wall time. One benchmark "step" is one MRAB macro step
+(2^{L-1} finest substeps, every level advanced once or more) of the tsunami-like
+workload: 500,000 triangles graded 8:1 toward a tanh beach, N = 4, 4 levels,
+positivity + TVB limiting, FP32, replayed as one CUDA graph. The state and the
+Adams-Bashforth history (~0.56 GB) exceed L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0). Multi-GPU runs are independent replicas (the
+scenarios do not exchange data); value sums all ranks' DOF-updates over the max time.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (there is no reference implementation to install: the paper ships no code).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DOF-updates/s per RHS stage"
+UNIT = "DOF-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nx", type=int, default=1000)
+    ap.add_argument("--ny", type=int, default=250)
+    ap.add_argument("--order", type=int, default=4)
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args, nx=None, ny=None):
+    from workloads import scenarios as sc
+    return sc.tsunami(nx=nx or args.nx, ny=ny or args.ny, N=args.order, nlevels=4)
+
+
+def workload_config(args, K, extra=None):
+    cfg = {"workload": f"tsunami_{2 * args.nx * args.ny}_N{args.order}_L4",
+           "mesh": f"{args.nx}x{args.ny}x2 triangles, x-graded 8:1, jitter 0.15, seed 3",
+           "triangles": K, "N": args.order, "levels_max": 4, "limiters": "PP+TVB",
+           "scheme": "MRAB3 (Algorithm 2)", "precision": args.precision,
+           "step": "one macro step = 2^(L-1) finest substeps (CUDA graph)",
+           "l2": "no flush: state + AB history > L2 (129 MB)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+
+def stage_bytes_per_element(N, ts):
+    """Algorithmic HBM bytes one element moves in the stage kernel: read Q (3Np),
+    B (Np), two older R slots (6Np), geometry (4) and connectivity (4 words);
+    write R (3Np), Q (3Np), means (3) and the dry byte. Neighbour traces are
+    counted as L2 hits."""
+    Np = (N + 1) * (N + 2) // 2
+    return (16 * Np + 4 + 3) * ts + 4 * 4 + 1
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1403_1661_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cuh", ".inc", ".cu")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(N, precision):
+    """DRAM bytes per element of the stage kernel from a committed ncu summary, if
+    it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", f"ncu_stage_{precision}_n{N}.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_element")
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample
+
+def oracle_sample(args, nsteps=1, nx=200, ny=50):
+    from oracle import problem
+    scn = workload(args, nx=nx, ny=ny)
+    om, ref, model, integ = problem.build(scn)
+    period = 2 ** (integ.L - 1)
+    t = time.perf_counter()
+    d0 = integ.dof_updates
+    for _ in range(nsteps * period):
+        integ.substep()
+    dt = time.perf_counter() - t
+    return (integ.dof_updates - d0) / dt, dt, om.K, period
+
+
+def cpu_info():
+    model = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return os.cpu_count(), model
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    nx, ny = 100, 25
+    for _ in range(args.warmup):
+        oracle_sample(args, 1, nx, ny)
+    vals, secs = [], []
+    dofs_total, t_total = 0.0, 0.0
+    for _ in range(args.steps):
+        v, dt, K, period = oracle_sample(args, 1, nx, ny)
+        dofs_total += v * dt
+        t_total += dt
+    value = dofs_total / t_total
+    cores, model = cpu_info()
+    sample = (f"same scenario at {nx}x{ny}x2 = {2 * nx * ny} triangles (N={args.order}, 4 levels, PP+TVB), "
+              f"one macro step per bench step, FP64 numpy oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args, 2 * args.nx * args.ny),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample, "cpu": model},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+
+    from paper_1403_1661_gb300 import build as _build
+    _build.build()
+    import paper_1403_1661_gb300 as P
+
+    scn = workload(args)
+    s = P.solver_from_scenario(scn, precision=args.precision)
+    L, counts, dt_min = s.level_info()
+    period = 2 ** (L - 1)
+    stream = s.stream
+
+    # warm-up (also captures the graph)
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    d0 = s.stats()["dof_updates"]
+    launches0 = s.kernel_launches()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        s.step(args.steps)
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    st = s.stats()
+    dofs = st["dof_updates"] - d0
+    launches = s.kernel_launches() - launches0
+    if dist:
+        t = torch.tensor([ms, float(dofs)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        ms_all, dofs_all = float(tmax[0]), float(t[1])
+    else:
+        ms_all, dofs_all = ms, float(dofs)
+    value = dofs_all / (ms_all / 1e3)
+
+    # per-kernel timing of one more macro step (events around every launch)
+    prof = s.profile_substeps(2 * period)
+    ts = 4 if args.precision == "fp32" else 8
+    bpe = stage_bytes_per_element(args.order, ts)
+    stage_bytes = prof["stage_elements"] * bpe
+    achieved = stage_bytes / (prof["stage_ms"] / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    per_launch_elems = prof["stage_elements"] / max(1, prof["stage_launches"])
+    traffic_pe = recorded_traffic(args.order, args.precision)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": (traffic_pe * per_launch_elems) if traffic_pe else None,
+                "kernel": f"k_stage<{'float' if ts == 4 else 'double'},{args.order}>",
+                "algorithmic_bytes_per_launch": bpe * per_launch_elems,
+                "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                "stage_share_of_step": prof["stage_ms"] / max(1e-9, prof["stage_ms"] + prof["tvb_ms"] + prof["other_ms"]),
+                "tvb_ms_per_step": prof["tvb_ms"] / 2, "stage_ms_per_step": prof["stage_ms"] / 2}
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "f32" if ts == 4 else "f64",
+              "data": "synthetic", "gpu_launches": int(launches),
+              "config": workload_config(args, s.K, {"levels": int(L), "elements_per_level": counts.tolist(),
+                                                   "parallelism": f"replicas x{world}"}),
+              "roofline": roofline, "clocks": clk}
+
+    # end to end through the public API with host buffers: state in, one macro step, state out
+    if not args.no_e2e:
+        B, h, hu, hv = P.scenario_inputs(scn, s.mesh)
+        ne = 2
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        de = 0
+        for _ in range(ne):
+            s.set_state(h, hu, hv)
+            d_before = s.stats()["dof_updates"]
+            s.step(1)
+            out = s.get_state()
+            de += s.stats()["dof_updates"] - d_before
+        te = (time.perf_counter() - t0) / ne
+        npp = ((args.order + 1) * (args.order + 2) // 2 + 3) // 4 * 4
+        result["e2e"] = {"value": (de / ne) / te, "unit": UNIT,
+                         "h2d_bytes_per_step": 3 * s.K * npp * ts,
+                         "d2h_bytes_per_step": 2 * 3 * s.K * npp * ts + 64,
+                         "note": "swe_set_state (FP64 host arrays) + swe_step(1) + swe_get_state per step"}
+
+    # the plain FP64 GPU form on the same workload (fewer steps: ~60x slower)
+    if not args.no_fp64 and rank == 0:
+        s64 = P.solver_from_scenario(scn, precision="fp64")
+        s64.step(1)
+        torch.cuda.synchronize()
+        d0 = s64.stats()["dof_updates"]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        n64 = 2
+        e0.record(s64.stream)
+        s64.step(n64)
+        e1.record(s64.stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        d64 = s64.stats()["dof_updates"] - d0
+        result["fp64_gpu"] = {"value": d64 / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64 / n64,
+                              "fp32_speedup": value / (d64 / (ms64 / 1e3))}
+        del s64
+
+    if rank == 0 and not args.no_cpu_baseline:
+        v, dt, Ks, _ = oracle_sample(args, 1, 400, 100)
+        cores, model = cpu_info()
+        result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                  "sample": f"same scenario at 400x100x2 = {Ks} triangles (N={args.order}, 4 levels, "
+                                            f"PP+TVB), one macro step, FP64 numpy oracle ({dt:.1f} s)",
+                                  "cpu": model}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

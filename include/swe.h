@@ -1,0 +1,212 @@
+/*
+ * swe.h -- C ABI of the GB300 nodal discontinuous Galerkin shallow-water engine.
+ *
+ * The library evaluates and advances the semi-discrete nodal DG discretisation
+ * of the 2D nonlinear shallow water equations on triangles described in
+ * "GPU Accelerated Discontinuous Galerkin Methods for Shallow Water Equations"
+ * (Gandham, Medina, Warburton, arXiv:1403.1661):
+ *   - Section 2, Eq. swe_conservative: Q = (h, hu, hv), fluxes F, G, source S;
+ *   - Section 3, Eq. weak_form / Eq. ode: Lagrange basis on Warp & Blend nodes,
+ *     cubature volume integrals, Gauss surface integrals, dQ/dt = R(Q);
+ *   - Section 4, Eq. cfl and Algorithm 1: per-element time step, levels,
+ *     multirate Adams-Bashforth (MRAB3);
+ *   - Section 5.1, Eq. well_balance: well-balanced Lax-Friedrichs flux;
+ *   - Section 5.2, Algorithms 2 and 3: limiting and the positivity limiter;
+ *   - Section 5.3, Eq. modified_TVB: TVB limiter with positivity modification;
+ *   - Section 7 (Eq. kernels): volume, surface and update kernels.
+ *
+ * Conventions (all entry points):
+ *   - Every call returns SWE_OK (0) or a negative SWE_E* code; swe_last_error()
+ *     gives a message for the calling thread's last failure.
+ *   - Host arrays are read (or written) during the call only; the caller keeps
+ *     ownership. Device memory is owned by the caller: swe_solver_create takes
+ *     one device workspace of swe_workspace_bytes() bytes and the library never
+ *     calls cudaMalloc/cudaFree. The library owns only the opaque handles.
+ *   - All device work is enqueued on the caller's CUDA stream (cudaStream_t
+ *     passed as void*). Calls that return host data (swe_get_state,
+ *     swe_stats, swe_get_full_state) synchronise that stream.
+ *   - Nodal arrays are element-major [K][Np] in the caller's element order and
+ *     the library's node order (swe_ref_nodes); K = number of triangles,
+ *     Np = (N+1)(N+2)/2.
+ *   - Triangle vertices may come in either orientation; each element is made
+ *     counter-clockwise (its vertices 1 and 2 swapped) and face f joins vertices
+ *     f and f+1 mod 3 of the oriented element.
+ */
+#ifndef SWE_GB300_H
+#define SWE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define SWE_OK 0
+#define SWE_EINVAL (-1)       /* bad argument, bad mesh, call out of order      */
+#define SWE_ENOMEM (-2)       /* workspace too small / over a memory budget      */
+#define SWE_ECUDA (-3)        /* a CUDA runtime call failed                      */
+#define SWE_ENAN (-4)         /* non-finite values detected in the state         */
+#define SWE_ETIMEOUT (-5)     /* a bounded device wait gave up                   */
+#define SWE_EUNSUPPORTED (-6) /* order / precision not built into this library   */
+
+/* ---- precision tiers ---------------------------------------------------- */
+#define SWE_FP64 0            /* everything in double precision                  */
+#define SWE_FP32 1            /* single precision, FP64 in the positivity limiter */
+
+/* ---- limiter mask bits (Algorithm 2) ----------------------------------- */
+#define SWE_LIM_PP 1          /* positivity-preserving limiter M Pi (Algorithm 3) */
+#define SWE_LIM_TVB 2         /* TVB limiter Lambda Pi (Section 5.3)              */
+
+typedef struct swe_mesh swe_mesh;
+typedef struct swe_solver swe_solver;
+
+/* Physical and numerical parameters.
+ *   g        gravity (Eq. swe_conservative)
+ *   h0       dry threshold (Algorithm 3); eps of Algorithm 3 is taken equal to h0
+ *            when eps <= 0
+ *   eps      positivity trigger of Algorithm 3 (<= 0: use h0)
+ *   tvb_M    TVB constant M; tvb_nu the minmod weight nu (<= 0: 1.5)
+ *   cfl      CFL number; the per-element step is cfl/(N+1)^2 * H_k / a_k (Eq. cfl)
+ *   N        polynomial order (2..5 in this build)
+ *   nlevels_max  number of MRAB levels allowed (>= 1; 1 = single-rate AB3)
+ *   precision    SWE_FP64 or SWE_FP32
+ *   limiter_mask SWE_LIM_PP | SWE_LIM_TVB applied after every update
+ *   dry_mode     0: a dry element is reset to h = h0, hu = hv = 0 (Algorithm 3,
+ *                injected mass tallied); 1: reset to its mean depth (mass kept) */
+typedef struct {
+  double g, h0, eps, tvb_M, tvb_nu, cfl;
+  int32_t N, nlevels_max, precision, limiter_mask, dry_mode, reserved;
+} swe_params;
+
+/* ---- library ------------------------------------------------------------ */
+int swe_version(void);                      /* 10000*major + 100*minor + patch */
+const char* swe_strerror(int code);
+const char* swe_last_error(void);
+
+/* Reference element sizes for order N (Section 7, Table "Notation"):
+ * Np nodes, Ncub cubature points (volume rule exact to degree 3N-1),
+ * Ng Gauss points per face (exact to degree 3N). Any pointer may be NULL. */
+int swe_ref_sizes(int32_t N, int32_t* Np, int32_t* Ncub, int32_t* Ng);
+
+/* Warp & Blend interpolation nodes (Section 3) in the library's node order,
+ * reference triangle (-1,-1),(1,-1),(-1,1). r, s: Np doubles each (host). */
+int swe_ref_nodes(int32_t N, double* r, double* s);
+
+/* Reference operators in FP64, row-major (host), for checking against an
+ * independent construction. which: 0 Ic (Ncub x Np), 1 Icr, 2 Ics,
+ * 3 Pr (Np x Ncub), 4 Ps, 5 P, 6 Lg (Np x 3Ng, Section 7.2), 7 face
+ * interpolation from the Nfp face nodes to the Ng Gauss points (Ng x Nfp),
+ * 8 element-mean weights (Np), 9 P1-projection vertex map (3 x Np),
+ * 10 cubature weights (Ncub), 11 Gauss weights (Ng). count: capacity in doubles. */
+int swe_ref_operator(int32_t N, int32_t which, double* out, size_t count);
+
+/* ---- mesh (host only) --------------------------------------------------- */
+/* vx, vy: nv vertex coordinates; EToV: K x 3 vertex indices. Faces are matched
+ * by their vertex pair; a face on one element only is a reflecting wall
+ * (Section 6.5). Fails with SWE_EINVAL on degenerate triangles, bad indices or
+ * faces shared by more than two triangles. */
+int swe_mesh_create(const double* vx, const double* vy, int32_t nv,
+                    const int32_t* EToV, int32_t K, swe_mesh** out);
+void swe_mesh_destroy(swe_mesh* mesh);
+int swe_mesh_num_elements(const swe_mesh* mesh, int32_t* K);
+/* EToE, EToF: K x 3 (host); neighbour element / face, -1 on a boundary face. */
+int swe_mesh_connectivity(const swe_mesh* mesh, int32_t* EToE, int32_t* EToF);
+/* Physical coordinates of the nodes of order N: x, y are K x Np (host). */
+int swe_mesh_node_coords(const swe_mesh* mesh, int32_t N, double* x, double* y);
+
+/* The level grouping swe_setup_levels would make for nodal state (h, hu, hv)
+ * (K x Np each, host, caller order): level_out (K, 1-based), dt_min_out. Host only. */
+int swe_mesh_levels(const swe_mesh* mesh, int32_t N, const double* h, const double* hu,
+                    const double* hv, double g, double cfl, int32_t nlevels_max,
+                    int32_t* level_out, double* dt_min_out);
+
+/* ---- solver -------------------------------------------------------------- */
+/* Bytes of caller-owned device memory a solver for (mesh, params) needs. */
+int swe_workspace_bytes(const swe_mesh* mesh, const swe_params* params, size_t* bytes);
+
+/* Create a solver in caller-owned device memory dev_workspace (bytes >= the
+ * size above, 256-byte aligned) bound to stream (cudaStream_t, may be NULL for
+ * the legacy default stream). Uploads geometry and operators; no allocation of
+ * device memory. The mesh may be destroyed afterwards. */
+int swe_solver_create(const swe_mesh* mesh, const swe_params* params,
+                      void* dev_workspace, size_t bytes, void* stream, swe_solver** out);
+void swe_solver_destroy(swe_solver* solver);
+
+/* Nodal bathymetry B (K x Np, host, FP64). Must precede swe_set_state. */
+int swe_set_bathymetry(swe_solver* solver, const double* B);
+
+/* Initial state (K x Np each, host, FP64): interpolated nodal values (the caller
+ * does Pi_H). Applies the limiters of the mask to it (Algorithm 2, first line),
+ * clears the Adams-Bashforth history and sets t = 0. */
+int swe_set_state(swe_solver* solver, const double* h, const double* hu, const double* hv);
+
+/* Group elements into MRAB levels from the current state (Eq. cfl, Section 4):
+ * dt_k = cfl/(N+1)^2 * H_k / a_k, H_k = twice the inradius, a_k = max over the
+ * element's nodes of |u| + sqrt(g max(h, 1e-2 max h)); level l holds
+ * 2^{l-1} dt_min <= dt_k < 2^l dt_min (capped at nlevels_max). level_out (K,
+ * caller order, 1-based) and dt_min_out may be NULL. Restarts the history. */
+int swe_setup_levels(swe_solver* solver, int32_t* level_out, double* dt_min_out);
+
+/* Force a level assignment (K, caller order, values 1..nlevels_max) and the
+ * finest step dt_min. Restarts the history. */
+int swe_set_levels(swe_solver* solver, const int32_t* level, double dt_min);
+
+/* One evaluation of R(Q) = N(Q) + S(Q^{g,+}, Q^{g,-}) (Eq. ode) at the current,
+ * level-synchronous state. dev_R: device array [3][K][Np] of the solver's
+ * precision (double for SWE_FP64, float for SWE_FP32), caller order, written on
+ * the solver's stream. */
+int swe_rhs(swe_solver* solver, void* dev_R);
+
+/* Advance n finest substeps of the multirate schedule (Algorithm 2). At every
+ * substep k, the levels l with k mod 2^{l-1} = 0 evaluate R, take one
+ * Adams-Bashforth step of 2^{l-1} dt_min and are limited. */
+int swe_substep(swe_solver* solver, int32_t n);
+
+/* Advance n macro steps (2^{L-1} finest substeps each, L = levels in use) by
+ * replaying a captured CUDA graph of one macro step. Requires a
+ * level-synchronous state (a multiple of 2^{L-1} substeps taken). */
+int swe_step(swe_solver* solver, int32_t n_macro);
+
+/* Apply the limiters in mask to the current level-synchronous state. */
+int swe_limit(swe_solver* solver, int32_t mask);
+
+/* Copy the current state to the host (K x Np each, FP64, caller order) and the
+ * simulated time t. Requires a level-synchronous state. Synchronises the stream. */
+int swe_get_state(const swe_solver* solver, double* h, double* hu, double* hv, double* t);
+
+/* Diagnostics (synchronises): mass = sum_k |D^k| mean(h), injected mass of dry
+ * resets since set_state, minimum nodal depth, DOF-updates done (elements x Np x 3
+ * per element step). Any pointer may be NULL. Returns SWE_ENAN if the device
+ * flagged non-finite values. */
+int swe_stats(const swe_solver* solver, double* mass, double* injected_mass,
+              double* hmin, int64_t* dof_updates);
+
+/* Checkpoint: swe_full_state_bytes gives the size of an opaque host buffer
+ * holding the state, the Adams-Bashforth history and the substep counter;
+ * restoring it into a solver created for the same mesh and parameters resumes
+ * bit-identically. */
+int swe_full_state_bytes(const swe_solver* solver, size_t* bytes);
+int swe_get_full_state(const swe_solver* solver, void* host_buf, size_t bytes);
+int swe_set_full_state(swe_solver* solver, const void* host_buf, size_t bytes);
+
+/* Levels in use (L), elements per level (counts[0..L-1]) and dt_min. */
+int swe_level_info(const swe_solver* solver, int32_t* L, int32_t* counts, double* dt_min);
+
+/* Advance n finest substeps like swe_substep, timing every kernel launch with CUDA
+ * events on the solver's stream (synchronises at the end). out[0..5]: total ms of
+ * the stage kernels (R + commit + positivity), of the TVB kernels, of the other
+ * kernels; number of stage launches; elements processed by the stage kernels; by
+ * the TVB kernels. For measurement only: the events add a little launch overhead. */
+int swe_profile_substeps(swe_solver* solver, int32_t n, double* out);
+
+/* Number of CUDA kernel launches this solver has issued (direct or inside
+ * replayed graphs), for launch accounting. */
+int swe_kernel_launches(const swe_solver* solver, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWE_GB300_H */

@@ -1,0 +1,94 @@
+// Plain data shared by the host launch code and the device kernels (no device
+// code, so host-only translation units can include it).
+#pragma once
+
+#include <stdint.h>
+#include <vector_types.h>
+
+namespace swe {
+
+constexpr int kMaxLevels = 8;
+constexpr int kBlock = 128;
+
+template <int N>
+struct Dims {
+  static constexpr int NP = (N + 1) * (N + 2) / 2;
+  static constexpr int NPP = (NP + 3) / 4 * 4;
+  static constexpr int NFP = N + 1;
+  static constexpr int NFPP = (NFP + 3) / 4 * 4;
+  static constexpr int Q = (3 * N + 1) / 2;
+  static constexpr int NCUB = Q * Q;
+  static constexpr int NG = (3 * N + 2) / 2;
+};
+
+// Operator block (element type T), packed by the host, staged in shared memory.
+template <int N>
+struct OpLayout {
+  using D = Dims<N>;
+  static constexpr int IC = 0;                                 // [NCUB][NPP]
+  static constexpr int ICR = IC + D::NCUB * D::NPP;            // [NCUB][NPP]
+  static constexpr int ICS = ICR + D::NCUB * D::NPP;           // [NCUB][NPP]
+  static constexpr int PRT = ICS + D::NCUB * D::NPP;           // [NCUB][NPP], Pr^T
+  static constexpr int PST = PRT + D::NCUB * D::NPP;           // [NCUB][NPP], Ps^T
+  static constexpr int PT = PST + D::NCUB * D::NPP;            // [NCUB][NPP], P^T
+  static constexpr int LGT = PT + D::NCUB * D::NPP;            // [3 NG][NPP], Lg^T
+  static constexpr int I1D = LGT + 3 * D::NG * D::NPP;         // [NG][NFPP]
+  static constexpr int MW = I1D + D::NG * D::NFPP;             // [NPP] mean weights
+  static constexpr int T1 = MW + D::NPP;                       // [3][NPP] P1 vertex map
+  static constexpr int BARY = T1 + 3 * D::NPP;                 // [NPP][4] barycentric
+  static constexpr int SIZE = BARY + 4 * D::NPP;
+};
+
+// Pointers into the caller-owned workspace.
+template <typename T>
+struct DevState {
+  T* q;                 // [2][3][K][NPP] double-buffered (eta, hu, hv)
+  T* ring;              // [3][3][K][NPP] Adams-Bashforth history of R
+  const T* B;           // [K][NPP]
+  const T* geo;         // [K][4] rx, ry, sx, sy
+  const int4* conn;     // [K] neighbour across faces 0,1,2 (-1: wall); .w packs faces/stencil
+  const T* tvbg;        // [K][8] alpha_i, beta_i (i = 0..2)
+  T* means;             // [K][4] element means (eta, hu, hv)
+  uint8_t* dry;         // [K] dry flag of the latest positivity pass
+  const double* Bbar;   // [K] mean of B (FP64)
+  const T* ops;         // operator block
+  double* acc;          // accumulators: [0] injected mass
+  int* flags;           // [0] non-finite state detected
+  long long* macro;     // macro-step counter (advanced on the device)
+};
+
+struct Sched {
+  int K;                     // elements
+  int L;                     // levels in use
+  int off[kMaxLevels + 1];   // level l (1-based) occupies [off[l-1], off[l])
+  double dt_min;
+};
+
+struct Phys {
+  double g, h0, eps, tvb_M, tvb_nu;
+  int pp, dry_mode;
+};
+
+template <typename T>
+struct StageParams {
+  DevState<T> s;
+  Sched sc;
+  Phys ph;
+  int j;          // substep within the macro step
+  int nactive;    // elements [0, nactive) are active
+  int mode;       // 0: R + commit + positivity; 1: R only, written to out
+  T* out;         // mode 1: [3][K][NP], caller order
+  const int* perm;
+};
+
+template <typename T>
+struct LimitParams {
+  DevState<T> s;
+  Sched sc;
+  Phys ph;
+  int j;
+  int nactive;
+  int post_stage;  // 1: limit the just-committed state of active elements; 0: current state
+};
+
+}  // namespace swe

@@ -1,0 +1,36 @@
+// Host-side launch entry points of the device kernels (one translation unit per
+// polynomial order instantiates them; dispatch by N happens in kernels_common.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "kernel_types.hpp"
+
+namespace swe {
+
+// Per (precision, order) kernel configuration: shared-memory bytes of the
+// operator block and the number of CTAs that fill the GPU once.
+struct KernelCfg {
+  int smem_bytes = 0;
+  int grid_stage = 0, grid_pos = 0, grid_tvb = 0, grid_stats = 0;
+};
+
+template <typename T>
+struct Launchers {
+  cudaError_t (*prepare)(KernelCfg*);
+  cudaError_t (*stage)(const StageParams<T>&, const KernelCfg&, cudaStream_t);
+  cudaError_t (*positivity)(const LimitParams<T>&, const KernelCfg&, cudaStream_t);
+  cudaError_t (*tvb)(const LimitParams<T>&, const KernelCfg&, cudaStream_t);
+  cudaError_t (*stats)(const DevState<T>&, const Sched&, int nblocks, double* partials,
+                       cudaStream_t);
+  int op_size;  // elements of the operator block
+};
+
+// Registered per order by kernels_n*.cu; nullptr when the order is not built.
+template <typename T>
+const Launchers<T>* launchers_for(int N);
+
+cudaError_t launch_advance(long long* macro, cudaStream_t st);
+cudaError_t launch_stats_finalize(const double* partials, int nblocks, double* out, cudaStream_t st);
+
+}  // namespace swe

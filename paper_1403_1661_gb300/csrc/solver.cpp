@@ -1,0 +1,1016 @@
+// Solver state, workspace layout, multirate schedule, CUDA-graph capture and the
+// C ABI declared in include/swe.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/swe.h"
+#include "launch.hpp"
+#include "mesh.hpp"
+#include "refelem.hpp"
+
+struct swe_mesh {
+  swe::Mesh m;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define SWE_CUDA(call)                                                                        \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(SWE_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));             \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int npp_of(int N) {
+  int np = (N + 1) * (N + 2) / 2;
+  return (np + 3) / 4 * 4;
+}
+
+struct Layout {
+  size_t q, ring, B, geo, conn, tvbg, means, dry, Bbar, ops, perm, acc, flags, macro, partials, total;
+  int nb_stats;
+};
+
+Layout make_layout(int K, int N, size_t ts, int op_size) {
+  Layout L;
+  const size_t npp = (size_t)npp_of(N);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  L.q = take(2 * 3 * (size_t)K * npp * ts);
+  L.ring = take(3 * 3 * (size_t)K * npp * ts);
+  L.B = take((size_t)K * npp * ts);
+  L.geo = take((size_t)K * 4 * ts);
+  L.conn = take((size_t)K * 16);
+  L.tvbg = take((size_t)K * 8 * ts);
+  L.means = take((size_t)K * 4 * ts);
+  L.dry = take((size_t)K);
+  L.Bbar = take((size_t)K * 8);
+  L.ops = take((size_t)op_size * ts);
+  L.perm = take((size_t)K * 4);
+  L.acc = take(8 * 8);
+  L.flags = take(4 * 4);
+  L.macro = take(8);
+  L.nb_stats = std::max(1, std::min(1024, (K + 255) / 256));
+  L.partials = take((size_t)L.nb_stats * 2 * 8 + 16);
+  L.total = off;
+  return L;
+}
+
+int check_params(const swe_params* p) {
+  if (!p) return fail(SWE_EINVAL, "params is NULL");
+  if (p->N < 2 || p->N > 5) return fail(SWE_EUNSUPPORTED, "this build supports N = 2..5");
+  if (p->precision != SWE_FP64 && p->precision != SWE_FP32)
+    return fail(SWE_EUNSUPPORTED, "precision must be SWE_FP64 or SWE_FP32");
+  if (!(p->g > 0) || !(p->h0 > 0) || !(p->cfl > 0)) return fail(SWE_EINVAL, "g, h0 and cfl must be > 0");
+  if (p->nlevels_max < 1 || p->nlevels_max > swe::kMaxLevels)
+    return fail(SWE_EINVAL, "nlevels_max must be in 1..8");
+  if (p->limiter_mask & ~3) return fail(SWE_EINVAL, "unknown limiter bits");
+  return SWE_OK;
+}
+
+// Base class so the C handle does not depend on the precision.
+struct SolverBase {
+  virtual ~SolverBase() {}
+};
+
+}  // namespace
+
+struct swe_solver {
+  swe::Mesh mesh;
+  swe_params prm;
+  swe::RefElem ref;
+  int N = 0, K = 0, Np = 0, NPP = 0;
+  bool fp64 = false;
+  size_t ts = 4;
+  cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  Layout lay;
+  swe::KernelCfg cfg;
+  const swe::Launchers<float>* lf = nullptr;
+  const swe::Launchers<double>* ld = nullptr;
+  // host copies
+  std::vector<double> B_in;      // caller order, as given
+  std::vector<double> B_dev;     // caller order, device-precision values
+  bool have_B = false, have_state = false, have_levels = false;
+  std::vector<int32_t> level;    // caller order
+  std::vector<int32_t> perm;     // device index -> caller index
+  std::vector<int32_t> iperm;    // caller index -> device index
+  int L = 1;
+  std::vector<int> off;          // size L+1
+  double dt_min = 0.0;
+  int64_t k = 0;                 // finest substeps since the last restart
+  double t0 = 0.0;               // time at the last restart
+  int64_t dof_updates = 0;
+  int64_t launches = 0;
+  cudaGraphExec_t graph = nullptr;
+  int graph_launches = 0;
+  int64_t graph_dofs = 0;
+};
+
+namespace {
+
+template <typename T>
+swe::DevState<T> dev_state(swe_solver* s) {
+  swe::DevState<T> d;
+  char* w = s->ws;
+  d.q = reinterpret_cast<T*>(w + s->lay.q);
+  d.ring = reinterpret_cast<T*>(w + s->lay.ring);
+  d.B = reinterpret_cast<const T*>(w + s->lay.B);
+  d.geo = reinterpret_cast<const T*>(w + s->lay.geo);
+  d.conn = reinterpret_cast<const int4*>(w + s->lay.conn);
+  d.tvbg = reinterpret_cast<const T*>(w + s->lay.tvbg);
+  d.means = reinterpret_cast<T*>(w + s->lay.means);
+  d.dry = reinterpret_cast<uint8_t*>(w + s->lay.dry);
+  d.Bbar = reinterpret_cast<const double*>(w + s->lay.Bbar);
+  d.ops = reinterpret_cast<const T*>(w + s->lay.ops);
+  d.acc = reinterpret_cast<double*>(w + s->lay.acc);
+  d.flags = reinterpret_cast<int*>(w + s->lay.flags);
+  d.macro = reinterpret_cast<long long*>(w + s->lay.macro);
+  return d;
+}
+
+swe::Sched sched_of(const swe_solver* s) {
+  swe::Sched sc;
+  std::memset(&sc, 0, sizeof(sc));
+  sc.K = s->K;
+  sc.L = s->L;
+  for (int l = 0; l <= s->L; ++l) sc.off[l] = s->off[l];
+  for (int l = s->L + 1; l <= swe::kMaxLevels; ++l) sc.off[l] = s->K;
+  sc.dt_min = s->dt_min;
+  return sc;
+}
+
+swe::Phys phys_of(const swe_solver* s, int mask) {
+  swe::Phys ph;
+  ph.g = s->prm.g;
+  ph.h0 = s->prm.h0;
+  ph.eps = s->prm.eps > 0 ? s->prm.eps : s->prm.h0;
+  ph.tvb_M = s->prm.tvb_M;
+  ph.tvb_nu = s->prm.tvb_nu > 0 ? s->prm.tvb_nu : 1.5;
+  ph.pp = (mask & SWE_LIM_PP) ? 1 : 0;
+  ph.dry_mode = s->prm.dry_mode;
+  return ph;
+}
+
+int upload(swe_solver* s, size_t off, const void* host, size_t bytes) {
+  SWE_CUDA(cudaMemcpyAsync(s->ws + off, host, bytes, cudaMemcpyHostToDevice, s->stream));
+  return SWE_OK;
+}
+
+template <typename T>
+std::vector<T> to_t(const std::vector<double>& v) {
+  std::vector<T> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = (T)v[i];
+  return o;
+}
+
+template <typename T>
+int upload_ops_t(swe_solver* s) {
+  const swe::RefElem& e = s->ref;
+  const int np = e.Np, npp = s->NPP, nc = e.Ncub, ng = e.Ng, nfp = e.Nfp;
+  const int nfpp = (nfp + 3) / 4 * 4;
+  const int opsz = s->fp64 ? s->ld->op_size : s->lf->op_size;
+  std::vector<double> o(opsz, 0.0);
+  size_t p = 0;
+  auto put_rows = [&](const std::vector<double>& M, int rows, int cols, bool transpose_src) {
+    // destination [rows][npp]; source M is rows x cols (or cols x rows if transposed)
+    for (int r = 0; r < rows; ++r)
+      for (int c = 0; c < cols; ++c)
+        o[p + (size_t)r * npp + c] = transpose_src ? M[(size_t)c * rows + r] : M[(size_t)r * cols + c];
+    p += (size_t)rows * npp;
+  };
+  put_rows(e.Ic, nc, np, false);
+  put_rows(e.Icr, nc, np, false);
+  put_rows(e.Ics, nc, np, false);
+  put_rows(e.Pr, nc, np, true);   // Pr is np x nc -> rows c
+  put_rows(e.Ps, nc, np, true);
+  put_rows(e.P, nc, np, true);
+  put_rows(e.Lg, 3 * ng, np, true);  // Lg is np x 3ng
+  for (int g = 0; g < ng; ++g)
+    for (int m = 0; m < nfp; ++m) o[p + (size_t)g * nfpp + m] = e.I1d[(size_t)g * nfp + m];
+  p += (size_t)ng * nfpp;
+  for (int j = 0; j < np; ++j) o[p + j] = e.mean_w[j];
+  p += npp;
+  for (int v = 0; v < 3; ++v)
+    for (int j = 0; j < np; ++j) o[p + (size_t)v * npp + j] = e.T1[(size_t)v * np + j];
+  p += 3 * (size_t)npp;
+  for (int j = 0; j < np; ++j)
+    for (int v = 0; v < 3; ++v) o[p + (size_t)j * 4 + v] = e.bary[(size_t)j * 3 + v];
+  p += 4 * (size_t)npp;
+  if ((int)p != opsz) return fail(SWE_EINVAL, "internal: operator block size mismatch");
+  std::vector<T> ot = to_t<T>(o);
+  int rc = upload(s, s->lay.ops, ot.data(), ot.size() * sizeof(T));
+  if (rc) return rc;
+  SWE_CUDA(cudaStreamSynchronize(s->stream));
+  return SWE_OK;
+}
+
+// Upload everything that depends on the element order (geometry, connectivity,
+// stencil, bathymetry, permutation).
+template <typename T>
+int upload_mesh_t(swe_solver* s) {
+  const int K = s->K, npp = s->NPP;
+  const swe::Mesh& m = s->mesh;
+  std::vector<double> alpha, beta;
+  std::vector<int32_t> jsel;
+  swe::tvb_stencil(m, alpha, beta, jsel);
+  std::vector<T> geo((size_t)K * 4), tvbg((size_t)K * 8, T(0));
+  std::vector<int32_t> conn((size_t)K * 4);
+  for (int e = 0; e < K; ++e) {
+    const int c = s->perm[e];
+    geo[4 * (size_t)e + 0] = (T)m.rx[c];
+    geo[4 * (size_t)e + 1] = (T)m.ry[c];
+    geo[4 * (size_t)e + 2] = (T)m.sx[c];
+    geo[4 * (size_t)e + 3] = (T)m.sy[c];
+    int w = 0;
+    for (int f = 0; f < 3; ++f) {
+      const int nb = m.EToE[3 * (size_t)c + f];
+      conn[4 * (size_t)e + f] = nb >= 0 ? s->iperm[nb] : -1;
+      const int fn = nb >= 0 ? m.EToF[3 * (size_t)c + f] : 0;
+      w |= (fn & 3) << (2 * f);
+      w |= (jsel[3 * (size_t)c + f] & 3) << (6 + 2 * f);
+      tvbg[8 * (size_t)e + 2 * f] = (T)alpha[3 * (size_t)c + f];
+      tvbg[8 * (size_t)e + 2 * f + 1] = (T)beta[3 * (size_t)c + f];
+    }
+    conn[4 * (size_t)e + 3] = w;
+  }
+  int rc;
+  if ((rc = upload(s, s->lay.geo, geo.data(), geo.size() * sizeof(T)))) return rc;
+  if ((rc = upload(s, s->lay.conn, conn.data(), conn.size() * 4))) return rc;
+  if ((rc = upload(s, s->lay.tvbg, tvbg.data(), tvbg.size() * sizeof(T)))) return rc;
+  if ((rc = upload(s, s->lay.perm, s->perm.data(), (size_t)K * 4))) return rc;
+  if (s->have_B) {
+    std::vector<T> b((size_t)K * npp, T(0));
+    std::vector<double> bbar(K, 0.0);
+    for (int e = 0; e < K; ++e) {
+      const int c = s->perm[e];
+      double acc = 0.0;
+      for (int j = 0; j < s->Np; ++j) {
+        const T v = (T)s->B_in[(size_t)c * s->Np + j];
+        b[(size_t)e * npp + j] = v;
+        acc += s->ref.mean_w[j] * (double)v;
+      }
+      bbar[e] = acc;
+    }
+    if ((rc = upload(s, s->lay.B, b.data(), b.size() * sizeof(T)))) return rc;
+    if ((rc = upload(s, s->lay.Bbar, bbar.data(), bbar.size() * 8))) return rc;
+    SWE_CUDA(cudaStreamSynchronize(s->stream));
+  }
+  SWE_CUDA(cudaStreamSynchronize(s->stream));
+  return SWE_OK;
+}
+
+int upload_mesh(swe_solver* s) { return s->fp64 ? upload_mesh_t<double>(s) : upload_mesh_t<float>(s); }
+
+// level-sorted permutation (finest level first, caller order kept inside a level)
+void build_order(swe_solver* s) {
+  const int K = s->K;
+  s->perm.resize(K);
+  s->iperm.resize(K);
+  int L = 1;
+  for (int v : s->level) L = std::max(L, v);
+  s->L = L;
+  s->off.assign(L + 1, 0);
+  std::vector<int> cnt(L + 1, 0);
+  for (int c = 0; c < K; ++c) cnt[s->level[c]]++;
+  for (int l = 1; l <= L; ++l) s->off[l] = s->off[l - 1] + cnt[l];
+  std::vector<int> pos(s->off.begin(), s->off.end());
+  for (int c = 0; c < K; ++c) {
+    const int e = pos[s->level[c] - 1]++;
+    s->perm[e] = c;
+    s->iperm[c] = e;
+  }
+}
+
+int invalidate_graph(swe_solver* s) {
+  if (s->graph) {
+    cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+  }
+  return SWE_OK;
+}
+
+int reset_counters(swe_solver* s) {
+  s->k = 0;
+  SWE_CUDA(cudaMemsetAsync(s->ws + s->lay.macro, 0, 8, s->stream));
+  return SWE_OK;
+}
+
+template <typename T>
+int upload_state_t(swe_solver* s, const double* h, const double* hu, const double* hv) {
+  const int K = s->K, npp = s->NPP, np = s->Np;
+  std::vector<T> q(3 * (size_t)K * npp, T(0));
+  for (int e = 0; e < K; ++e) {
+    const int c = s->perm[e];
+    for (int j = 0; j < np; ++j) {
+      const size_t ci = (size_t)c * np + j;
+      q[(size_t)e * npp + j] = (T)(h[ci] + s->B_in[ci]);
+      q[(size_t)K * npp + (size_t)e * npp + j] = (T)hu[ci];
+      q[2 * (size_t)K * npp + (size_t)e * npp + j] = (T)hv[ci];
+    }
+  }
+  int rc = upload(s, s->lay.q, q.data(), q.size() * sizeof(T));
+  if (rc) return rc;
+  SWE_CUDA(cudaStreamSynchronize(s->stream));
+  return SWE_OK;
+}
+
+// limiter launches on the current (post_stage = 0) or just-committed state
+template <typename T>
+int launch_limit_t(swe_solver* s, int mask, int post_stage, int j, int nactive) {
+  const swe::Launchers<T>* lt;
+  if constexpr (sizeof(T) == 8) lt = s->ld; else lt = s->lf;
+  swe::LimitParams<T> p;
+  p.s = dev_state<T>(s);
+  p.sc = sched_of(s);
+  p.ph = phys_of(s, mask);
+  p.j = j;
+  p.nactive = nactive;
+  p.post_stage = post_stage;
+  if ((mask & SWE_LIM_PP) && !post_stage) {
+    SWE_CUDA(lt->positivity(p, s->cfg, s->stream));
+    s->launches++;
+  } else if (!post_stage) {
+    // means and dry flags are still needed by the TVB limiter: positivity pass without limiting
+    p.ph.pp = 0;
+    SWE_CUDA(lt->positivity(p, s->cfg, s->stream));
+    s->launches++;
+    p.ph.pp = (mask & SWE_LIM_PP) ? 1 : 0;
+  }
+  if (mask & SWE_LIM_TVB) {
+    SWE_CUDA(lt->tvb(p, s->cfg, s->stream));
+    s->launches++;
+  }
+  return SWE_OK;
+}
+
+int launch_limit(swe_solver* s, int mask, int post_stage, int j, int nactive) {
+  return s->fp64 ? launch_limit_t<double>(s, mask, post_stage, j, nactive)
+                 : launch_limit_t<float>(s, mask, post_stage, j, nactive);
+}
+
+int active_levels(const swe_solver* s, int j) {
+  if (j == 0) return s->L;
+  int m = 1;
+  while (m < s->L && (j % (1 << m)) == 0) ++m;
+  return m;
+}
+
+// enqueue one finest substep j of the current macro step
+struct KernelTimer {
+  std::vector<cudaEvent_t> ev;   // pairs (start, stop)
+  std::vector<int> kind;         // 0 stage, 1 tvb, 2 other
+  std::vector<int64_t> elems;
+};
+
+int timer_mark(swe_solver* s, KernelTimer* t, bool start, int kind, int64_t elems) {
+  if (!t) return SWE_OK;
+  cudaEvent_t e;
+  SWE_CUDA(cudaEventCreate(&e));
+  SWE_CUDA(cudaEventRecord(e, s->stream));
+  t->ev.push_back(e);
+  if (start) {
+    t->kind.push_back(kind);
+    t->elems.push_back(elems);
+  }
+  return SWE_OK;
+}
+
+template <typename T>
+int enqueue_substep_t(swe_solver* s, int j, KernelTimer* tm = nullptr) {
+  const swe::Launchers<T>* lt;
+  if constexpr (sizeof(T) == 8) lt = s->ld; else lt = s->lf;
+  const int m = active_levels(s, j);
+  const int nactive = s->off[m];
+  swe::StageParams<T> p;
+  p.s = dev_state<T>(s);
+  p.sc = sched_of(s);
+  p.ph = phys_of(s, s->prm.limiter_mask);
+  p.j = j;
+  p.nactive = nactive;
+  p.mode = 0;
+  p.out = nullptr;
+  p.perm = nullptr;
+  int rc;
+  if ((rc = timer_mark(s, tm, true, 0, nactive))) return rc;
+  SWE_CUDA(lt->stage(p, s->cfg, s->stream));
+  if ((rc = timer_mark(s, tm, false, 0, 0))) return rc;
+  int nl = 1;
+  if (s->prm.limiter_mask & SWE_LIM_TVB) {
+    swe::LimitParams<T> lp;
+    lp.s = p.s;
+    lp.sc = p.sc;
+    lp.ph = p.ph;
+    lp.j = j;
+    lp.nactive = nactive;
+    lp.post_stage = 1;
+    if ((rc = timer_mark(s, tm, true, 1, nactive))) return rc;
+    SWE_CUDA(lt->tvb(lp, s->cfg, s->stream));
+    if ((rc = timer_mark(s, tm, false, 1, 0))) return rc;
+    ++nl;
+  }
+  const int period = 1 << (s->L - 1);
+  if (j == period - 1) {
+    if ((rc = timer_mark(s, tm, true, 2, 0))) return rc;
+    SWE_CUDA(swe::launch_advance(p.s.macro, s->stream));
+    if ((rc = timer_mark(s, tm, false, 2, 0))) return rc;
+    ++nl;
+  }
+  return nl;
+}
+
+int enqueue_substep(swe_solver* s, int j, KernelTimer* tm = nullptr) {
+  return s->fp64 ? enqueue_substep_t<double>(s, j, tm) : enqueue_substep_t<float>(s, j, tm);
+}
+
+int64_t substep_dofs(const swe_solver* s, int j) {
+  return (int64_t)s->off[active_levels(s, j)] * s->Np * 3;
+}
+
+bool synchronous(const swe_solver* s) { return (s->k % (1LL << (s->L - 1))) == 0; }
+
+template <typename T>
+int download_state_t(const swe_solver* s, double* h, double* hu, double* hv) {
+  const int K = s->K, npp = s->NPP, np = s->Np;
+  std::vector<T> q(2 * 3 * (size_t)K * npp);
+  SWE_CUDA(cudaMemcpyAsync(q.data(), s->ws + s->lay.q, q.size() * sizeof(T), cudaMemcpyDeviceToHost,
+                           s->stream));
+  SWE_CUDA(cudaStreamSynchronize(s->stream));
+  const size_t fs = (size_t)K * npp, bs = 3 * fs;
+  for (int e = 0; e < K; ++e) {
+    const int c = s->perm[e];
+    int l = 1;
+    while (l < s->L && e >= s->off[l]) ++l;
+    const int cur = (int)((s->k >> (l - 1)) & 1);
+    for (int j = 0; j < np; ++j) {
+      const size_t ci = (size_t)c * np + j, di = (size_t)cur * bs + (size_t)e * npp + j;
+      if (h) h[ci] = (double)q[di] - s->B_dev[ci];
+      if (hu) hu[ci] = (double)q[di + fs];
+      if (hv) hv[ci] = (double)q[di + 2 * fs];
+    }
+  }
+  return SWE_OK;
+}
+
+int download_state(const swe_solver* s, double* h, double* hu, double* hv) {
+  return s->fp64 ? download_state_t<double>(s, h, hu, hv) : download_state_t<float>(s, h, hu, hv);
+}
+
+int apply_levels(swe_solver* s, const std::vector<int32_t>& level, double dt_min) {
+  // keep the current state across a re-ordering
+  std::vector<double> h, hu, hv;
+  const bool had_state = s->have_state;
+  if (had_state) {
+    if (!synchronous(s)) return fail(SWE_EINVAL, "levels can change only at a level-synchronous state");
+    const size_t n = (size_t)s->K * s->Np;
+    h.resize(n); hu.resize(n); hv.resize(n);
+    int rc = download_state(s, h.data(), hu.data(), hv.data());
+    if (rc) return rc;
+    s->t0 += (double)s->k * s->dt_min;
+  }
+  s->level = level;
+  s->dt_min = dt_min;
+  build_order(s);
+  s->have_levels = true;
+  invalidate_graph(s);
+  int rc = upload_mesh(s);
+  if (rc) return rc;
+  if (had_state) {
+    rc = s->fp64 ? upload_state_t<double>(s, h.data(), hu.data(), hv.data())
+                 : upload_state_t<float>(s, h.data(), hu.data(), hv.data());
+    if (rc) return rc;
+    if ((rc = reset_counters(s))) return rc;
+    // recompute means / dry flags of the re-ordered state (positivity pass, no limiting)
+    if ((rc = launch_limit(s, 0, 0, 0, s->K))) return rc;
+    SWE_CUDA(cudaStreamSynchronize(s->stream));
+  }
+  return SWE_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+int swe_version(void) { return 100; }
+
+const char* swe_strerror(int code) {
+  switch (code) {
+    case SWE_OK: return "ok";
+    case SWE_EINVAL: return "invalid argument";
+    case SWE_ENOMEM: return "not enough memory";
+    case SWE_ECUDA: return "CUDA error";
+    case SWE_ENAN: return "non-finite state";
+    case SWE_ETIMEOUT: return "device wait timed out";
+    case SWE_EUNSUPPORTED: return "unsupported";
+    default: return "unknown error";
+  }
+}
+
+const char* swe_last_error(void) { return g_last_error.c_str(); }
+
+int swe_ref_sizes(int32_t N, int32_t* Np, int32_t* Ncub, int32_t* Ng) {
+  if (N < 1 || N > 7) return fail(SWE_EINVAL, "N out of range");
+  if (Np) *Np = (N + 1) * (N + 2) / 2;
+  if (Ncub) *Ncub = swe::ref_num_cubature(N);
+  if (Ng) *Ng = swe::ref_num_gauss(N);
+  return SWE_OK;
+}
+
+int swe_ref_nodes(int32_t N, double* r, double* s) {
+  if (N < 1 || N > 7 || !r || !s) return fail(SWE_EINVAL, "bad arguments");
+  swe::RefElem e = swe::RefElem::build(N);
+  std::copy(e.r.begin(), e.r.end(), r);
+  std::copy(e.s.begin(), e.s.end(), s);
+  return SWE_OK;
+}
+
+int swe_ref_operator(int32_t N, int32_t which, double* out, size_t count) {
+  if (N < 1 || N > 7 || !out) return fail(SWE_EINVAL, "bad arguments");
+  swe::RefElem e = swe::RefElem::build(N);
+  const std::vector<double>* src = nullptr;
+  switch (which) {
+    case 0: src = &e.Ic; break;
+    case 1: src = &e.Icr; break;
+    case 2: src = &e.Ics; break;
+    case 3: src = &e.Pr; break;
+    case 4: src = &e.Ps; break;
+    case 5: src = &e.P; break;
+    case 6: src = &e.Lg; break;
+    case 7: src = &e.I1d; break;
+    case 8: src = &e.mean_w; break;
+    case 9: src = &e.T1; break;
+    case 10: src = &e.wc; break;
+    case 11: src = &e.wg; break;
+    default: return fail(SWE_EINVAL, "unknown operator id");
+  }
+  if (count < src->size()) return fail(SWE_EINVAL, "output buffer too small");
+  std::copy(src->begin(), src->end(), out);
+  return SWE_OK;
+}
+
+int swe_mesh_create(const double* vx, const double* vy, int32_t nv, const int32_t* EToV, int32_t K,
+                    swe_mesh** out) {
+  if (!out) return fail(SWE_EINVAL, "out is NULL");
+  *out = nullptr;
+  std::unique_ptr<swe_mesh> m(new (std::nothrow) swe_mesh);
+  if (!m) return fail(SWE_ENOMEM, "host allocation failed");
+  std::string err = swe::Mesh::create(vx, vy, nv, EToV, K, m->m);
+  if (!err.empty()) return fail(SWE_EINVAL, err);
+  *out = m.release();
+  return SWE_OK;
+}
+
+void swe_mesh_destroy(swe_mesh* mesh) { delete mesh; }
+
+int swe_mesh_num_elements(const swe_mesh* mesh, int32_t* K) {
+  if (!mesh || !K) return fail(SWE_EINVAL, "NULL argument");
+  *K = mesh->m.K;
+  return SWE_OK;
+}
+
+int swe_mesh_connectivity(const swe_mesh* mesh, int32_t* EToE, int32_t* EToF) {
+  if (!mesh || !EToE || !EToF) return fail(SWE_EINVAL, "NULL argument");
+  std::copy(mesh->m.EToE.begin(), mesh->m.EToE.end(), EToE);
+  std::copy(mesh->m.EToF.begin(), mesh->m.EToF.end(), EToF);
+  return SWE_OK;
+}
+
+int swe_mesh_node_coords(const swe_mesh* mesh, int32_t N, double* x, double* y) {
+  if (!mesh || !x || !y || N < 1 || N > 7) return fail(SWE_EINVAL, "bad arguments");
+  swe::RefElem e = swe::RefElem::build(N);
+  const swe::Mesh& m = mesh->m;
+  for (int k = 0; k < m.K; ++k) {
+    const int32_t* v = &m.EToV[3 * (size_t)k];
+    for (int j = 0; j < e.Np; ++j) {
+      const double l0 = -(e.r[j] + e.s[j]) / 2, l1 = (1 + e.r[j]) / 2, l2 = (1 + e.s[j]) / 2;
+      x[(size_t)k * e.Np + j] = l0 * m.vx[v[0]] + l1 * m.vx[v[1]] + l2 * m.vx[v[2]];
+      y[(size_t)k * e.Np + j] = l0 * m.vy[v[0]] + l1 * m.vy[v[1]] + l2 * m.vy[v[2]];
+    }
+  }
+  return SWE_OK;
+}
+
+int swe_mesh_levels(const swe_mesh* mesh, int32_t N, const double* h, const double* hu, const double* hv,
+                    double g, double cfl, int32_t nlevels_max, int32_t* level_out, double* dt_min_out) {
+  if (!mesh || !h || !hu || !hv || !level_out) return fail(SWE_EINVAL, "NULL argument");
+  if (N < 1 || N > 7 || !(g > 0) || !(cfl > 0) || nlevels_max < 1 || nlevels_max > swe::kMaxLevels)
+    return fail(SWE_EINVAL, "bad arguments");
+  std::vector<double> dt;
+  swe::element_dt(mesh->m, N, h, hu, hv, g, cfl, dt);
+  std::vector<int32_t> lev;
+  double dtmin = swe::assign_levels(dt, nlevels_max, lev);
+  std::copy(lev.begin(), lev.end(), level_out);
+  if (dt_min_out) *dt_min_out = dtmin;
+  return SWE_OK;
+}
+
+int swe_workspace_bytes(const swe_mesh* mesh, const swe_params* params, size_t* bytes) {
+  if (!mesh || !bytes) return fail(SWE_EINVAL, "NULL argument");
+  int rc = check_params(params);
+  if (rc) return rc;
+  const bool fp64 = params->precision == SWE_FP64;
+  int opsz = fp64 ? swe::launchers_for<double>(params->N)->op_size
+                  : swe::launchers_for<float>(params->N)->op_size;
+  *bytes = make_layout(mesh->m.K, params->N, fp64 ? 8 : 4, opsz).total;
+  return SWE_OK;
+}
+
+int swe_solver_create(const swe_mesh* mesh, const swe_params* params, void* dev_workspace, size_t bytes,
+                      void* stream, swe_solver** out) {
+  if (!mesh || !out || !dev_workspace) return fail(SWE_EINVAL, "NULL argument");
+  *out = nullptr;
+  int rc = check_params(params);
+  if (rc) return rc;
+  if (((uintptr_t)dev_workspace & 255) != 0) return fail(SWE_EINVAL, "workspace must be 256-byte aligned");
+  std::unique_ptr<swe_solver> s(new (std::nothrow) swe_solver);
+  if (!s) return fail(SWE_ENOMEM, "host allocation failed");
+  s->mesh = mesh->m;
+  s->prm = *params;
+  s->N = params->N;
+  s->K = mesh->m.K;
+  s->ref = swe::RefElem::build(s->N);
+  s->Np = s->ref.Np;
+  s->NPP = npp_of(s->N);
+  s->fp64 = params->precision == SWE_FP64;
+  s->ts = s->fp64 ? 8 : 4;
+  s->stream = reinterpret_cast<cudaStream_t>(stream);
+  s->ws = reinterpret_cast<char*>(dev_workspace);
+  s->ws_bytes = bytes;
+  if (s->fp64) {
+    s->ld = swe::launchers_for<double>(s->N);
+    if (!s->ld) return fail(SWE_EUNSUPPORTED, "order not built");
+  } else {
+    s->lf = swe::launchers_for<float>(s->N);
+    if (!s->lf) return fail(SWE_EUNSUPPORTED, "order not built");
+  }
+  s->lay = make_layout(s->K, s->N, s->ts, s->fp64 ? s->ld->op_size : s->lf->op_size);
+  if (bytes < s->lay.total) return fail(SWE_ENOMEM, "workspace smaller than swe_workspace_bytes()");
+  cudaError_t ce = s->fp64 ? s->ld->prepare(&s->cfg) : s->lf->prepare(&s->cfg);
+  if (ce != cudaSuccess) return fail(SWE_ECUDA, std::string("kernel setup: ") + cudaGetErrorString(ce));
+  // single level until levels are set up
+  s->level.assign(s->K, 1);
+  s->dt_min = 0.0;
+  build_order(s.get());
+  SWE_CUDA(cudaMemsetAsync(s->ws, 0, s->lay.total, s->stream));
+  rc = s->fp64 ? upload_ops_t<double>(s.get()) : upload_ops_t<float>(s.get());
+  if (rc) return rc;
+  rc = upload_mesh(s.get());
+  if (rc) return rc;
+  SWE_CUDA(cudaStreamSynchronize(s->stream));
+  *out = s.release();
+  return SWE_OK;
+}
+
+void swe_solver_destroy(swe_solver* solver) {
+  if (!solver) return;
+  cudaStreamSynchronize(solver->stream);
+  invalidate_graph(solver);
+  delete solver;
+}
+
+int swe_set_bathymetry(swe_solver* s, const double* B) {
+  if (!s || !B) return fail(SWE_EINVAL, "NULL argument");
+  const size_t n = (size_t)s->K * s->Np;
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(B[i])) return fail(SWE_EINVAL, "non-finite bathymetry");
+  s->B_in.assign(B, B + n);
+  s->B_dev.resize(n);
+  for (size_t i = 0; i < n; ++i) s->B_dev[i] = s->fp64 ? B[i] : (double)(float)B[i];
+  s->have_B = true;
+  s->have_state = false;
+  return upload_mesh(s);
+}
+
+int swe_set_state(swe_solver* s, const double* h, const double* hu, const double* hv) {
+  if (!s || !h || !hu || !hv) return fail(SWE_EINVAL, "NULL argument");
+  if (!s->have_B) return fail(SWE_EINVAL, "swe_set_bathymetry must come first");
+  const size_t n = (size_t)s->K * s->Np;
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(h[i]) || !std::isfinite(hu[i]) || !std::isfinite(hv[i]))
+      return fail(SWE_EINVAL, "non-finite state");
+  int rc = s->fp64 ? upload_state_t<double>(s, h, hu, hv) : upload_state_t<float>(s, h, hu, hv);
+  if (rc) return rc;
+  if ((rc = reset_counters(s))) return rc;
+  s->t0 = 0.0;
+  s->dof_updates = 0;
+  SWE_CUDA(cudaMemsetAsync(s->ws + s->lay.acc, 0, 64, s->stream));
+  SWE_CUDA(cudaMemsetAsync(s->ws + s->lay.flags, 0, 16, s->stream));
+  s->have_state = true;
+  // Algorithm 2, first line: limit the initial state
+  if ((rc = launch_limit(s, s->prm.limiter_mask, 0, 0, s->K))) return rc;
+  SWE_CUDA(cudaStreamSynchronize(s->stream));
+  return SWE_OK;
+}
+
+int swe_setup_levels(swe_solver* s, int32_t* level_out, double* dt_min_out) {
+  if (!s) return fail(SWE_EINVAL, "NULL argument");
+  if (!s->have_state) return fail(SWE_EINVAL, "swe_set_state must come first");
+  if (!synchronous(s)) return fail(SWE_EINVAL, "state is not level-synchronous");
+  const size_t n = (size_t)s->K * s->Np;
+  std::vector<double> h(n), hu(n), hv(n), dt;
+  int rc = download_state(s, h.data(), hu.data(), hv.data());
+  if (rc) return rc;
+  swe::element_dt(s->mesh, s->N, h.data(), hu.data(), hv.data(), s->prm.g, s->prm.cfl, dt);
+  std::vector<int32_t> lev;
+  double dtmin = swe::assign_levels(dt, s->prm.nlevels_max, lev);
+  if ((rc = apply_levels(s, lev, dtmin))) return rc;
+  if (level_out) std::copy(lev.begin(), lev.end(), level_out);
+  if (dt_min_out) *dt_min_out = dtmin;
+  return SWE_OK;
+}
+
+int swe_set_levels(swe_solver* s, const int32_t* level, double dt_min) {
+  if (!s || !level) return fail(SWE_EINVAL, "NULL argument");
+  if (!(dt_min > 0)) return fail(SWE_EINVAL, "dt_min must be > 0");
+  std::vector<int32_t> lev(level, level + s->K);
+  for (int32_t v : lev)
+    if (v < 1 || v > s->prm.nlevels_max) return fail(SWE_EINVAL, "level out of 1..nlevels_max");
+  return apply_levels(s, lev, dt_min);
+}
+
+int swe_rhs(swe_solver* s, void* dev_R) {
+  if (!s || !dev_R) return fail(SWE_EINVAL, "NULL argument");
+  if (!s->have_state) return fail(SWE_EINVAL, "no state");
+  if (!synchronous(s)) return fail(SWE_EINVAL, "state is not level-synchronous");
+  const int period = 1 << (s->L - 1);
+  (void)period;
+  if (s->fp64) {
+    swe::StageParams<double> p;
+    p.s = dev_state<double>(s);
+    p.sc = sched_of(s);
+    p.ph = phys_of(s, s->prm.limiter_mask);
+    p.j = 0;
+    p.nactive = s->K;
+    p.mode = 1;
+    p.out = reinterpret_cast<double*>(dev_R);
+    p.perm = reinterpret_cast<const int*>(s->ws + s->lay.perm);
+    SWE_CUDA(s->ld->stage(p, s->cfg, s->stream));
+  } else {
+    swe::StageParams<float> p;
+    p.s = dev_state<float>(s);
+    p.sc = sched_of(s);
+    p.ph = phys_of(s, s->prm.limiter_mask);
+    p.j = 0;
+    p.nactive = s->K;
+    p.mode = 1;
+    p.out = reinterpret_cast<float*>(dev_R);
+    p.perm = reinterpret_cast<const int*>(s->ws + s->lay.perm);
+    SWE_CUDA(s->lf->stage(p, s->cfg, s->stream));
+  }
+  s->launches++;
+  return SWE_OK;
+}
+
+int swe_substep(swe_solver* s, int32_t n) {
+  if (!s || n < 0) return fail(SWE_EINVAL, "bad arguments");
+  if (!s->have_state) return fail(SWE_EINVAL, "no state");
+  if (!(s->dt_min > 0)) return fail(SWE_EINVAL, "levels / dt_min not set up");
+  const int64_t period = 1LL << (s->L - 1);
+  for (int32_t i = 0; i < n; ++i) {
+    const int j = (int)(s->k % period);
+    int nl = enqueue_substep(s, j);
+    if (nl < 0) return nl;
+    s->launches += nl;
+    s->dof_updates += substep_dofs(s, j);
+    s->k++;
+  }
+  return SWE_OK;
+}
+
+int swe_step(swe_solver* s, int32_t n_macro) {
+  if (!s || n_macro < 0) return fail(SWE_EINVAL, "bad arguments");
+  if (!s->have_state) return fail(SWE_EINVAL, "no state");
+  if (!(s->dt_min > 0)) return fail(SWE_EINVAL, "levels / dt_min not set up");
+  if (!synchronous(s)) return fail(SWE_EINVAL, "state is not level-synchronous");
+  if (n_macro == 0) return SWE_OK;
+  const int period = 1 << (s->L - 1);
+  if (!s->graph) {
+    cudaGraph_t g = nullptr;
+    SWE_CUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    int total = 0;
+    int64_t dofs = 0;
+    for (int j = 0; j < period; ++j) {
+      int nl = enqueue_substep(s, j);
+      if (nl < 0) {
+        cudaStreamEndCapture(s->stream, &g);
+        if (g) cudaGraphDestroy(g);
+        return nl;
+      }
+      total += nl;
+      dofs += substep_dofs(s, j);
+    }
+    SWE_CUDA(cudaStreamEndCapture(s->stream, &g));
+    cudaError_t ce = cudaGraphInstantiate(&s->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+      s->graph = nullptr;
+      return fail(SWE_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ce));
+    }
+    s->graph_launches = total;
+    s->graph_dofs = dofs;
+  }
+  for (int32_t i = 0; i < n_macro; ++i) {
+    SWE_CUDA(cudaGraphLaunch(s->graph, s->stream));
+    s->launches += s->graph_launches;
+    s->dof_updates += s->graph_dofs;
+    s->k += period;
+  }
+  return SWE_OK;
+}
+
+int swe_limit(swe_solver* s, int32_t mask) {
+  if (!s) return fail(SWE_EINVAL, "NULL argument");
+  if (!s->have_state) return fail(SWE_EINVAL, "no state");
+  if (!synchronous(s)) return fail(SWE_EINVAL, "state is not level-synchronous");
+  if (mask & ~3) return fail(SWE_EINVAL, "unknown limiter bits");
+  return launch_limit(s, mask, 0, 0, s->K);
+}
+
+int swe_get_state(const swe_solver* s, double* h, double* hu, double* hv, double* t) {
+  if (!s) return fail(SWE_EINVAL, "NULL argument");
+  if (!s->have_state) return fail(SWE_EINVAL, "no state");
+  if (!synchronous(s)) return fail(SWE_EINVAL, "state is not level-synchronous");
+  int rc = download_state(s, h, hu, hv);
+  if (rc) return rc;
+  if (t) *t = s->t0 + (double)s->k * s->dt_min;
+  return SWE_OK;
+}
+
+int swe_stats(const swe_solver* cs, double* mass, double* injected_mass, double* hmin, int64_t* dof_updates) {
+  swe_solver* s = const_cast<swe_solver*>(cs);
+  if (!s) return fail(SWE_EINVAL, "NULL argument");
+  if (!s->have_state) return fail(SWE_EINVAL, "no state");
+  if (!synchronous(s)) return fail(SWE_EINVAL, "state is not level-synchronous");
+  double* partials = reinterpret_cast<double*>(s->ws + s->lay.partials);
+  double* outd = partials + 2 * (size_t)s->lay.nb_stats;
+  cudaError_t ce = s->fp64 ? s->ld->stats(dev_state<double>(s), sched_of(s), s->lay.nb_stats, partials, s->stream)
+                           : s->lf->stats(dev_state<float>(s), sched_of(s), s->lay.nb_stats, partials, s->stream);
+  if (ce != cudaSuccess) return fail(SWE_ECUDA, std::string("stats: ") + cudaGetErrorString(ce));
+  SWE_CUDA(swe::launch_stats_finalize(partials, s->lay.nb_stats, outd, s->stream));
+  s->launches += 2;
+  double res[2], acc[1];
+  int flags = 0;
+  SWE_CUDA(cudaMemcpyAsync(res, outd, 16, cudaMemcpyDeviceToHost, s->stream));
+  SWE_CUDA(cudaMemcpyAsync(acc, s->ws + s->lay.acc, 8, cudaMemcpyDeviceToHost, s->stream));
+  SWE_CUDA(cudaMemcpyAsync(&flags, s->ws + s->lay.flags, 4, cudaMemcpyDeviceToHost, s->stream));
+  SWE_CUDA(cudaStreamSynchronize(s->stream));
+  if (mass) *mass = res[0];
+  if (hmin) *hmin = res[1];
+  if (injected_mass) *injected_mass = acc[0];
+  if (dof_updates) *dof_updates = s->dof_updates;
+  if (flags & 1) return fail(SWE_ENAN, "non-finite values in the state");
+  return SWE_OK;
+}
+
+// checkpoint: header + level array + raw device regions [q, ring) .. [means, dry], acc, macro
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int32_t K, N, precision, L;
+  int64_t k, dof_updates;
+  double t0, dt_min;
+  uint64_t bytes_q, bytes_ring, bytes_means, bytes_dry;
+};
+}  // namespace
+
+int swe_full_state_bytes(const swe_solver* s, size_t* bytes) {
+  if (!s || !bytes) return fail(SWE_EINVAL, "NULL argument");
+  const size_t qb = 2 * 3 * (size_t)s->K * s->NPP * s->ts, rb = 3 * qb / 2;
+  *bytes = sizeof(CkptHeader) + (size_t)s->K * 4 + qb + rb + (size_t)s->K * 4 * s->ts + s->K + 64 + 8;
+  return SWE_OK;
+}
+
+int swe_get_full_state(const swe_solver* s, void* host_buf, size_t bytes) {
+  size_t need;
+  int rc = swe_full_state_bytes(s, &need);
+  if (rc) return rc;
+  if (!host_buf || bytes < need) return fail(SWE_EINVAL, "buffer too small");
+  if (!s->have_state) return fail(SWE_EINVAL, "no state");
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "SWEGB300", 8);
+  h.K = s->K; h.N = s->N; h.precision = s->prm.precision; h.L = s->L;
+  h.k = s->k; h.dof_updates = s->dof_updates; h.t0 = s->t0; h.dt_min = s->dt_min;
+  h.bytes_q = 2 * 3 * (uint64_t)s->K * s->NPP * s->ts;
+  h.bytes_ring = 3 * h.bytes_q / 2;
+  h.bytes_means = (uint64_t)s->K * 4 * s->ts;
+  h.bytes_dry = s->K;
+  char* p = reinterpret_cast<char*>(host_buf);
+  std::memcpy(p, &h, sizeof(h)); p += sizeof(h);
+  std::memcpy(p, s->level.data(), (size_t)s->K * 4); p += (size_t)s->K * 4;
+  cudaStream_t st = s->stream;
+  SWE_CUDA(cudaMemcpyAsync(p, s->ws + s->lay.q, h.bytes_q, cudaMemcpyDeviceToHost, st)); p += h.bytes_q;
+  SWE_CUDA(cudaMemcpyAsync(p, s->ws + s->lay.ring, h.bytes_ring, cudaMemcpyDeviceToHost, st)); p += h.bytes_ring;
+  SWE_CUDA(cudaMemcpyAsync(p, s->ws + s->lay.means, h.bytes_means, cudaMemcpyDeviceToHost, st)); p += h.bytes_means;
+  SWE_CUDA(cudaMemcpyAsync(p, s->ws + s->lay.dry, h.bytes_dry, cudaMemcpyDeviceToHost, st)); p += h.bytes_dry;
+  SWE_CUDA(cudaMemcpyAsync(p, s->ws + s->lay.acc, 64, cudaMemcpyDeviceToHost, st)); p += 64;
+  SWE_CUDA(cudaMemcpyAsync(p, s->ws + s->lay.macro, 8, cudaMemcpyDeviceToHost, st));
+  SWE_CUDA(cudaStreamSynchronize(st));
+  return SWE_OK;
+}
+
+int swe_set_full_state(swe_solver* s, const void* host_buf, size_t bytes) {
+  size_t need;
+  int rc = swe_full_state_bytes(s, &need);
+  if (rc) return rc;
+  if (!host_buf || bytes < need) return fail(SWE_EINVAL, "buffer too small");
+  if (!s->have_B) return fail(SWE_EINVAL, "swe_set_bathymetry must come first");
+  CkptHeader h;
+  const char* p = reinterpret_cast<const char*>(host_buf);
+  std::memcpy(&h, p, sizeof(h)); p += sizeof(h);
+  if (std::memcmp(h.magic, "SWEGB300", 8) != 0 || h.K != s->K || h.N != s->N || h.precision != s->prm.precision)
+    return fail(SWE_EINVAL, "checkpoint does not match this solver");
+  std::vector<int32_t> lev(s->K);
+  std::memcpy(lev.data(), p, (size_t)s->K * 4); p += (size_t)s->K * 4;
+  s->have_state = false;  // no state to carry across the re-ordering
+  if ((rc = apply_levels(s, lev, h.dt_min))) return rc;
+  cudaStream_t st = s->stream;
+  SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.q, p, h.bytes_q, cudaMemcpyHostToDevice, st)); p += h.bytes_q;
+  SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.ring, p, h.bytes_ring, cudaMemcpyHostToDevice, st)); p += h.bytes_ring;
+  SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.means, p, h.bytes_means, cudaMemcpyHostToDevice, st)); p += h.bytes_means;
+  SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.dry, p, h.bytes_dry, cudaMemcpyHostToDevice, st)); p += h.bytes_dry;
+  SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.acc, p, 64, cudaMemcpyHostToDevice, st)); p += 64;
+  SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.macro, p, 8, cudaMemcpyHostToDevice, st));
+  SWE_CUDA(cudaMemsetAsync(s->ws + s->lay.flags, 0, 16, st));
+  SWE_CUDA(cudaStreamSynchronize(st));
+  s->k = h.k;
+  s->t0 = h.t0;
+  s->dof_updates = h.dof_updates;
+  s->have_state = true;
+  return SWE_OK;
+}
+
+int swe_level_info(const swe_solver* s, int32_t* L, int32_t* counts, double* dt_min) {
+  if (!s) return fail(SWE_EINVAL, "NULL argument");
+  if (L) *L = s->L;
+  if (counts)
+    for (int l = 1; l <= s->L; ++l) counts[l - 1] = s->off[l] - s->off[l - 1];
+  if (dt_min) *dt_min = s->dt_min;
+  return SWE_OK;
+}
+
+int swe_profile_substeps(swe_solver* s, int32_t n, double* out) {
+  if (!s || n < 0 || !out) return fail(SWE_EINVAL, "bad arguments");
+  if (!s->have_state) return fail(SWE_EINVAL, "no state");
+  if (!(s->dt_min > 0)) return fail(SWE_EINVAL, "levels / dt_min not set up");
+  KernelTimer tm;
+  const int64_t period = 1LL << (s->L - 1);
+  int rc = SWE_OK;
+  for (int32_t i = 0; i < n && rc == SWE_OK; ++i) {
+    const int j = (int)(s->k % period);
+    int nl = enqueue_substep(s, j, &tm);
+    if (nl < 0) { rc = nl; break; }
+    s->launches += nl;
+    s->dof_updates += substep_dofs(s, j);
+    s->k++;
+  }
+  cudaError_t ce = cudaStreamSynchronize(s->stream);
+  for (int i = 0; i < 6; ++i) out[i] = 0.0;
+  for (size_t i = 0; 2 * i + 1 < tm.ev.size(); ++i) {
+    float ms = 0.f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, tm.ev[2 * i], tm.ev[2 * i + 1]);
+    const int kind = tm.kind[i];
+    out[kind] += ms;
+    if (kind == 0) { out[3] += 1; out[4] += (double)tm.elems[i]; }
+    if (kind == 1) out[5] += (double)tm.elems[i];
+  }
+  for (cudaEvent_t e : tm.ev) cudaEventDestroy(e);
+  if (rc) return rc;
+  if (ce != cudaSuccess) return fail(SWE_ECUDA, std::string("profile: ") + cudaGetErrorString(ce));
+  return SWE_OK;
+}
+
+int swe_kernel_launches(const swe_solver* s, int64_t* launches) {
+  if (!s || !launches) return fail(SWE_EINVAL, "NULL argument");
+  *launches = s->launches;
+  return SWE_OK;
+}
+
+}  // extern "C"

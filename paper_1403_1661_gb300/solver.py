@@ -1,0 +1,277 @@
+"""Python front end of the C ABI: mesh and solver handles with torch-owned device memory.
+
+PyTorch provides the device workspace (one uint8 tensor) and the CUDA stream; all
+numerical work runs in the native library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _native as nat
+
+
+def _prec_code(precision):
+    if isinstance(precision, int):
+        return precision
+    p = str(precision).lower()
+    if p in ("fp64", "f64", "double"):
+        return nat.SWE_FP64
+    if p in ("fp32", "f32", "float"):
+        return nat.SWE_FP32
+    raise ValueError(f"unknown precision {precision!r}")
+
+
+class Mesh:
+    """Triangle mesh (host): connectivity and geometry built by the library."""
+
+    def __init__(self, vx, vy, EToV):
+        L = nat.lib()
+        self.vx = np.ascontiguousarray(vx, np.float64)
+        self.vy = np.ascontiguousarray(vy, np.float64)
+        self.EToV = np.ascontiguousarray(EToV, np.int32)
+        h = C.c_void_p()
+        nat.check(L.swe_mesh_create(nat.dptr(self.vx), nat.dptr(self.vy), self.vx.size,
+                                    nat.iptr(self.EToV), self.EToV.shape[0], C.byref(h)),
+                  "swe_mesh_create")
+        self.handle = h
+        self.K = int(self.EToV.shape[0])
+
+    def connectivity(self):
+        L = nat.lib()
+        E = np.zeros((self.K, 3), np.int32)
+        F = np.zeros((self.K, 3), np.int32)
+        nat.check(L.swe_mesh_connectivity(self.handle, nat.iptr(E), nat.iptr(F)), "swe_mesh_connectivity")
+        return E, F
+
+    def node_coords(self, N):
+        L = nat.lib()
+        np_ = (N + 1) * (N + 2) // 2
+        x = np.zeros((self.K, np_))
+        y = np.zeros((self.K, np_))
+        nat.check(L.swe_mesh_node_coords(self.handle, N, nat.dptr(x), nat.dptr(y)), "swe_mesh_node_coords")
+        return x, y
+
+    def levels(self, N, h, hu, hv, g, cfl, nlevels_max):
+        """Level grouping (Section 4) the solver would make for this nodal state."""
+        h, hu, hv = (np.ascontiguousarray(a, np.float64) for a in (h, hu, hv))
+        lev = np.zeros(self.K, np.int32)
+        dtm = C.c_double()
+        nat.check(nat.lib().swe_mesh_levels(self.handle, N, nat.dptr(h), nat.dptr(hu), nat.dptr(hv), g, cfl,
+                                            nlevels_max, nat.iptr(lev), C.byref(dtm)), "swe_mesh_levels")
+        return lev, dtm.value
+
+    def centroids(self):
+        return self.vx[self.EToV].mean(axis=1), self.vy[self.EToV].mean(axis=1)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            nat.lib().swe_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ref_sizes(N):
+    L = nat.lib()
+    a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+    nat.check(L.swe_ref_sizes(N, C.byref(a), C.byref(b), C.byref(c)), "swe_ref_sizes")
+    return a.value, b.value, c.value
+
+
+def ref_nodes(N):
+    np_ = ref_sizes(N)[0]
+    r = np.zeros(np_)
+    s = np.zeros(np_)
+    nat.check(nat.lib().swe_ref_nodes(N, nat.dptr(r), nat.dptr(s)), "swe_ref_nodes")
+    return r, s
+
+
+_OP_SHAPES = {0: ("Ncub", "Np"), 1: ("Ncub", "Np"), 2: ("Ncub", "Np"), 3: ("Np", "Ncub"),
+              4: ("Np", "Ncub"), 5: ("Np", "Ncub"), 6: ("Np", "3Ng"), 7: ("Ng", "Nfp"),
+              8: ("Np",), 9: ("3", "Np"), 10: ("Ncub",), 11: ("Ng",)}
+
+
+def ref_operator(N, which):
+    Np, Ncub, Ng = ref_sizes(N)
+    dims = {"Np": Np, "Ncub": Ncub, "Ng": Ng, "3Ng": 3 * Ng, "Nfp": N + 1, "3": 3}
+    shape = tuple(dims[d] for d in _OP_SHAPES[which])
+    out = np.zeros(int(np.prod(shape)))
+    nat.check(nat.lib().swe_ref_operator(N, which, nat.dptr(out), out.size), "swe_ref_operator")
+    return out.reshape(shape)
+
+
+class Solver:
+    """One shallow-water problem resident on the GPU (state, history, geometry)."""
+
+    def __init__(self, mesh: Mesh, N: int, g: float = 9.81, h0: float = 1e-5, cfl: float = 0.5,
+                 nlevels_max: int = 1, precision="fp32", limiter_mask: int = 0, tvb_M: float = 0.0,
+                 tvb_nu: float = 1.5, dry_mode: int = 0, eps: float = 0.0, device=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        L = nat.lib()
+        self.mesh = mesh
+        self.N = N
+        self.K = mesh.K
+        self.Np = (N + 1) * (N + 2) // 2
+        self.prm = nat.swe_params(g, h0, eps, tvb_M, tvb_nu, cfl, N, nlevels_max,
+                                  _prec_code(precision), limiter_mask, dry_mode, 0)
+        self.precision = self.prm.precision
+        nbytes = C.c_size_t()
+        nat.check(L.swe_workspace_bytes(mesh.handle, C.byref(self.prm), C.byref(nbytes)),
+                  "swe_workspace_bytes")
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        with torch.cuda.device(self.device):
+            # a stream of its own: CUDA graphs cannot be captured on the legacy default stream
+            self.stream = torch.cuda.Stream(self.device) if stream is None else stream
+            self.workspace = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=self.device)
+            self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            nat.check(L.swe_solver_create(mesh.handle, C.byref(self.prm), C.c_void_p(self._ws_ptr),
+                                          nbytes.value, C.c_void_p(self.stream.cuda_stream), C.byref(h)),
+                      "swe_solver_create")
+        self.handle = h
+        self.workspace_bytes = int(nbytes.value)
+
+    # -- inputs -----------------------------------------------------------
+    def set_bathymetry(self, B):
+        B = np.ascontiguousarray(B, np.float64).reshape(self.K, self.Np)
+        nat.check(nat.lib().swe_set_bathymetry(self.handle, nat.dptr(B)), "swe_set_bathymetry")
+
+    def set_state(self, h, hu, hv):
+        h, hu, hv = (np.ascontiguousarray(a, np.float64).reshape(self.K, self.Np) for a in (h, hu, hv))
+        nat.check(nat.lib().swe_set_state(self.handle, nat.dptr(h), nat.dptr(hu), nat.dptr(hv)),
+                  "swe_set_state")
+
+    def setup_levels(self):
+        lev = np.zeros(self.K, np.int32)
+        dtm = C.c_double()
+        nat.check(nat.lib().swe_setup_levels(self.handle, nat.iptr(lev), C.byref(dtm)), "swe_setup_levels")
+        return lev, dtm.value
+
+    def set_levels(self, level, dt_min):
+        lev = np.ascontiguousarray(level, np.int32)
+        nat.check(nat.lib().swe_set_levels(self.handle, nat.iptr(lev), float(dt_min)), "swe_set_levels")
+
+    # -- the hot path -----------------------------------------------------
+    def rhs(self):
+        """R(Q) as a device tensor of shape (3, K, Np) in the solver's precision."""
+        import torch
+        dt = torch.float64 if self.precision == nat.SWE_FP64 else torch.float32
+        out = torch.empty((3, self.K, self.Np), dtype=dt, device=self.device)
+        cur = torch.cuda.current_stream(self.device)
+        self.stream.wait_stream(cur)
+        nat.check(nat.lib().swe_rhs(self.handle, C.c_void_p(out.data_ptr())), "swe_rhs")
+        cur.wait_stream(self.stream)
+        out.record_stream(self.stream)
+        return out
+
+    def substep(self, n=1):
+        nat.check(nat.lib().swe_substep(self.handle, int(n)), "swe_substep")
+
+    def step(self, n_macro=1):
+        nat.check(nat.lib().swe_step(self.handle, int(n_macro)), "swe_step")
+
+    def limit(self, mask):
+        nat.check(nat.lib().swe_limit(self.handle, int(mask)), "swe_limit")
+
+    # -- outputs ------------------------------------------------------------
+    def get_state(self):
+        h = np.zeros((self.K, self.Np))
+        hu = np.zeros_like(h)
+        hv = np.zeros_like(h)
+        t = C.c_double()
+        nat.check(nat.lib().swe_get_state(self.handle, nat.dptr(h), nat.dptr(hu), nat.dptr(hv), C.byref(t)),
+                  "swe_get_state")
+        return h, hu, hv, t.value
+
+    def stats(self):
+        m, inj, hmin = C.c_double(), C.c_double(), C.c_double()
+        dofs = C.c_int64()
+        rc = nat.lib().swe_stats(self.handle, C.byref(m), C.byref(inj), C.byref(hmin), C.byref(dofs))
+        out = {"mass": m.value, "injected_mass": inj.value, "hmin": hmin.value, "dof_updates": dofs.value,
+               "nonfinite": rc == nat.SWE_ENAN}
+        if rc not in (nat.SWE_OK, nat.SWE_ENAN):
+            nat.check(rc, "swe_stats")
+        return out
+
+    def level_info(self):
+        Lc = C.c_int32()
+        counts = np.zeros(8, np.int32)
+        dtm = C.c_double()
+        nat.check(nat.lib().swe_level_info(self.handle, C.byref(Lc), nat.iptr(counts), C.byref(dtm)),
+                  "swe_level_info")
+        return Lc.value, counts[:Lc.value].copy(), dtm.value
+
+    def kernel_launches(self):
+        n = C.c_int64()
+        nat.check(nat.lib().swe_kernel_launches(self.handle, C.byref(n)), "swe_kernel_launches")
+        return n.value
+
+    def profile_substeps(self, n):
+        """Run n substeps with CUDA events around every kernel; per-kernel totals."""
+        out = np.zeros(6)
+        nat.check(nat.lib().swe_profile_substeps(self.handle, int(n), nat.dptr(out)), "swe_profile_substeps")
+        return {"stage_ms": out[0], "tvb_ms": out[1], "other_ms": out[2], "stage_launches": int(out[3]),
+                "stage_elements": int(out[4]), "tvb_elements": int(out[5])}
+
+    def full_state(self):
+        nb = C.c_size_t()
+        nat.check(nat.lib().swe_full_state_bytes(self.handle, C.byref(nb)), "swe_full_state_bytes")
+        buf = np.zeros(nb.value, np.uint8)
+        nat.check(nat.lib().swe_get_full_state(self.handle, buf.ctypes.data_as(C.c_void_p), nb.value),
+                  "swe_get_full_state")
+        return buf
+
+    def load_full_state(self, buf):
+        buf = np.ascontiguousarray(buf, np.uint8)
+        nat.check(nat.lib().swe_set_full_state(self.handle, buf.ctypes.data_as(C.c_void_p), buf.size),
+                  "swe_set_full_state")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            nat.lib().swe_solver_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def scenario_inputs(scn, mesh: Mesh):
+    """Evaluate a workloads.scenarios.Scenario at this library's nodes."""
+    x, y = mesh.node_coords(scn.N)
+    cx, cy = mesh.centroids()
+    cx = np.repeat(cx[:, None], x.shape[1], axis=1)
+    cy = np.repeat(cy[:, None], x.shape[1], axis=1)
+    B = np.asarray(scn.bathymetry(x, y, cx, cy), np.float64)
+    h, hu, hv = scn.init(x, y, cx, cy, B)
+    return B, np.asarray(h, np.float64), np.asarray(hu, np.float64), np.asarray(hv, np.float64)
+
+
+def solver_from_scenario(scn, precision="fp32", levels=None, dt_min=None, mesh_arrays=None, **kw):
+    """Mesh + solver + inputs for a scenario; levels from the CFL rule unless given."""
+    vx, vy, E = scn.build_mesh() if mesh_arrays is None else mesh_arrays
+    mesh = Mesh(vx, vy, E)
+    s = Solver(mesh, scn.N, g=scn.g, h0=scn.h0, cfl=scn.cfl, nlevels_max=max(scn.nlevels, 1),
+               precision=precision, limiter_mask=scn.limiter_mask, tvb_M=scn.tvb_M, tvb_nu=scn.tvb_nu,
+               dry_mode=scn.dry_mode, **kw)
+    B, h, hu, hv = scenario_inputs(scn, mesh)
+    s.set_bathymetry(B)
+    s.set_state(h, hu, hv)
+    if levels is None:
+        s.setup_levels()
+    else:
+        s.set_levels(levels, dt_min)
+    return s

@@ -1,0 +1,25 @@
+"""Shared set-up for the GPU parity tests: the same seeded scenario built on the
+oracle side and on the CUDA side (the CUDA side uses the oracle's level
+assignment so both follow the same multirate schedule; level grouping itself is
+compared bit-exactly in test_lib_host.py)."""
+import numpy as np
+
+from oracle import problem
+
+
+def both(scn, precision, levels=None, dt_min=None, mesh_arrays=None):
+    import paper_1403_1661_gb300 as P
+    arrays = scn.build_mesh() if mesh_arrays is None else mesh_arrays
+    om, ref, model, integ = problem.build(scn, levels=levels, dt_min=dt_min, mesh_arrays=arrays)
+    solver = P.solver_from_scenario(scn, precision=precision, levels=integ.level, dt_min=integ.dt_min,
+                                    mesh_arrays=arrays)
+    return om, ref, model, integ, solver
+
+
+def state_errors(solver, integ):
+    """max-norm differences of (h, hu, hv) and the scales they are measured against."""
+    h, hu, hv, t = solver.get_state()
+    q = integ.q_end
+    eh = np.abs(h - q[0]).max()
+    em = max(np.abs(hu - q[1]).max(), np.abs(hv - q[2]).max())
+    return eh, em, (h, hu, hv, t)

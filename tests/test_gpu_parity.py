@@ -1,0 +1,186 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (derived from the arithmetic; see the design notes):
+* FP64 tier: every output within 1e-11 of the oracle, relative to the field's
+  max-norm (the two sides differ only in rounding order and in the pre-balanced
+  rewrite of the momentum flux, both O(1e-16) per operation over O(10^3) operations).
+* FP32 tier: R within 2e-5 of max|R| per field (single-precision rounding of the
+  state, bed and operators, amplified by the ~Np*Ncub-term contractions); states
+  after T steps within 2e-5 max(h) (depth) and 2e-5 max(h) sqrt(g max h) (momentum)
+  on smooth configurations.
+"""
+import numpy as np
+import pytest
+
+from tests.gpu_helpers import both, state_errors
+from workloads import meshes, scenarios as sc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_1661_gb300 import build
+    build.build()
+
+
+def _report(name, **vals):
+    print("PARITY", name, " ".join(f"{k}={v:.3e}" for k, v in vals.items()), flush=True)
+
+
+def _rhs_case(N, precision, moving=True, bed="smooth", nx=9, ny=7, limiter_mask=0):
+    """Hump on a jittered graded mesh over a bed; velocities from a smooth field."""
+    scn = sc.Scenario(
+        name=f"rhs_case_N{N}", N=N, g=9.81, h0=1e-5, cfl=0.5, nlevels=1, limiter_mask=limiter_mask,
+        tvb_M=0.0,
+        mesh=lambda: meshes.graded_jittered_rect(0.0, 1.0, 0.0, 1.0, nx, ny, ratio=2.0, jitter=0.2, seed=11),
+        bathymetry=(sc.smooth_bump_bed(depth=1.0, amp=0.3) if bed == "smooth"
+                    else sc.step_bed_by_centroid(0.5, -1.0, -0.8, 0.2)),
+        init=None)
+
+    def init(x, y, cx, cy, B):
+        eta = 0.05 * np.exp(-((x - 0.4) ** 2 + (y - 0.6) ** 2) / 0.05)
+        h = eta - B
+        if not moving:
+            return h, 0 * h, 0 * h
+        return h, h * 0.3 * np.sin(3 * x + y), h * (-0.2) * np.cos(2 * y - x)
+    scn.init = init
+    return scn
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_rhs_matches_oracle(N, precision):
+    scn = _rhs_case(N, precision)
+    om, ref, model, integ, s = both(scn, precision)
+    q = integ.q_end
+    R_o = model.rhs(q[0], q[1], q[2])
+    R_g = s.rhs().cpu().numpy().astype(np.float64)
+    errs = [np.abs(R_g[c] - R_o[c]).max() / np.abs(R_o[c]).max() for c in range(3)]
+    _report(f"rhs N={N} {precision}", e_h=errs[0], e_hu=errs[1], e_hv=errs[2])
+    tol = 1e-11 if precision == "fp64" else 2e-5
+    assert max(errs) < tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("bed", ["smooth", "discontinuous"])
+def test_lake_at_rest(precision, bed):
+    """Still water over a smooth or a face-discontinuous bed (Section 5.1): R = 0.
+    At the datum eta = 0 the pre-balanced form is exact in any precision."""
+    scn = _rhs_case(3, precision, moving=False, bed=bed)
+    scn.init = lambda x, y, cx, cy, B: (0.0 - B, 0 * B, 0 * B)
+    om, ref, model, integ, s = both(scn, precision)
+    R = s.rhs().cpu().numpy()
+    _report(f"lake eta=0 {bed} {precision}", maxR=float(np.abs(R).max()))
+    assert np.abs(R).max() == 0.0
+    # away from the datum: round-off of the still-water pressure only
+    scn.init = lambda x, y, cx, cy, B: (0.3 - B, 0 * B, 0 * B)
+    om, ref, model, integ, s = both(scn, precision)
+    R = s.rhs().cpu().numpy()
+    scale = 9.81 * 1.3 ** 2 * max(np.abs(om.rx).max(), np.abs(om.sy).max())
+    _report(f"lake eta=0.3 {bed} {precision}", rel=float(np.abs(R).max() / scale))
+    assert np.abs(R).max() < (1e-13 if precision == "fp64" else 1e-6) * scale
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_hump_square_ab3_100_steps(precision):
+    """The plain-method configuration at full size: 512 triangles, N = 2, AB3, 100 steps."""
+    scn = sc.hump_square()
+    om, ref, model, integ, s = both(scn, precision)
+    for _ in range(scn.steps):
+        integ.substep()
+    s.substep(scn.steps)
+    eh, em, (h, hu, hv, t) = state_errors(s, integ)
+    hmax = integ.q_end[0].max()
+    _report(f"hump100 {precision}", eh=eh / hmax, em=em / (hmax * np.sqrt(9.81 * hmax)))
+    assert abs(t - integ.time) < 1e-12 * integ.time
+    if precision == "fp64":
+        assert eh < 1e-11 * hmax and em < 1e-11 * hmax * np.sqrt(9.81 * hmax)
+    else:
+        assert eh < 2e-5 * hmax and em < 2e-5 * hmax * np.sqrt(9.81 * hmax)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_mrab_tsunami_levels(precision):
+    """Graded beach, 3-4 MRAB levels, positivity + TVB: two macro steps."""
+    scn = sc.tsunami(nx=40, ny=10, N=3, nlevels=4)
+    om, ref, model, integ, s = both(scn, precision)
+    nsub = 2 * 2 ** (integ.L - 1)
+    for _ in range(nsub):
+        integ.substep()
+    s.substep(nsub)
+    eh, em, _ = state_errors(s, integ)
+    hmax = integ.q_end[0].max()
+    _report(f"tsunami L={integ.L} {precision}", eh=eh / hmax, em=em / (hmax * np.sqrt(9.81 * hmax)))
+    if precision == "fp64":
+        assert eh < 1e-11 * hmax and em < 1e-11 * hmax * np.sqrt(9.81 * hmax)
+    else:
+        assert eh < 2e-5 * hmax and em < 2e-5 * hmax * np.sqrt(9.81 * hmax)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_dam_break_small_pp_tvb(precision):
+    """Wet/dry dam break with positivity + TVB (M = 0) every stage, 40 steps."""
+    scn = sc.dam_break(nx=40, ny=4, N=3, steps=40)
+    om, ref, model, integ, s = both(scn, precision)
+    for _ in range(scn.steps):
+        integ.substep()
+    s.substep(scn.steps)
+    h, hu, hv, t = s.get_state()
+    q = integ.q_end
+    eh = np.abs(h - q[0]).max()
+    em = max(np.abs(hu - q[1]).max(), np.abs(hv - q[2]).max())
+    l1 = np.abs(h - q[0]).sum() / np.abs(q[0]).sum()
+    _report(f"dambreak {precision}", eh=eh, em=em, l1=l1, hmin=h.min())
+    assert h.min() >= -1e-6
+    if precision == "fp64":
+        assert eh < 1e-9 and em < 1e-9
+    else:
+        assert l1 < 1e-4
+
+
+def test_graph_replay_equals_direct_launches():
+    scn = sc.tsunami(nx=40, ny=10, N=3, nlevels=4)
+    _, _, _, integ, a = both(scn, "fp32")
+    import paper_1403_1661_gb300 as P
+    b = P.solver_from_scenario(scn, precision="fp32", levels=integ.level, dt_min=integ.dt_min)
+    L = integ.L
+    a.substep(3 * 2 ** (L - 1))
+    b.step(3)
+    ha = a.get_state()
+    hb = b.get_state()
+    for x, y in zip(ha[:3], hb[:3]):
+        assert np.array_equal(x, y)
+    assert a.stats()["dof_updates"] == b.stats()["dof_updates"]
+
+
+def test_checkpoint_resume_bit_identical():
+    scn = sc.tsunami(nx=40, ny=10, N=3, nlevels=4)
+    _, _, _, integ, a = both(scn, "fp32")
+    L = integ.L
+    a.step(1)
+    ck = a.full_state()
+    a.step(2)
+    ref = a.get_state()
+    import paper_1403_1661_gb300 as P
+    b = P.solver_from_scenario(scn, precision="fp32")
+    b.load_full_state(ck)
+    b.step(2)
+    got = b.get_state()
+    for x, y in zip(ref, got):
+        assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_mass_conservation_and_stats():
+    scn = sc.hump_square(n=16, N=3)
+    _, _, model, integ, s = both(scn, "fp64")
+    m0 = s.stats()["mass"]
+    assert abs(m0 - model.mass(integ.q_end[0])) < 1e-12 * m0
+    s.substep(50)
+    st = s.stats()
+    _report("mass fp64", drift=abs(st["mass"] - m0) / m0)
+    assert abs(st["mass"] - m0) < 1e-13 * m0 * 50
+    assert st["dof_updates"] == 50 * integ.model.mesh.K * 10 * 3 and not st["nonfinite"]

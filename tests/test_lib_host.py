@@ -1,0 +1,118 @@
+"""CPU tests of the native library: exports, host-side reference element, mesh
+connectivity and level grouping against the oracle (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import mesh as omesh
+from oracle import refelem as oref
+from workloads import meshes, scenarios as sc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1403_1661_gb300 import build
+    build.build()
+    from paper_1403_1661_gb300 import _native
+    return _native
+
+
+def _declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(swe_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    L = C.CDLL(lib.LIB_PATH)
+    declared = _declared_symbols()
+    assert len(declared) >= 30
+    missing = [n for n in sorted(declared) if not hasattr(L, n)]
+    assert not missing, missing
+    # and the Python binding binds every one of them
+    assert declared == set(lib.SIGNATURES), declared ^ set(lib.SIGNATURES)
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5])
+def test_reference_element_matches_oracle(lib, N):
+    import paper_1403_1661_gb300 as P
+    Np, Ncub, Ng = P.ref_sizes(N)
+    ref = oref.RefElement(N)
+    assert (Np, Ncub, Ng) == (ref.Np, ref.Ncub, ref.Ng)
+    r, s = P.ref_nodes(N)
+    assert np.abs(r - ref.r).max() < 1e-13 and np.abs(s - ref.s).max() < 1e-13
+    tol = 1e-11
+    # the cubature ordering is the same tensor ordering on both sides
+    for which, M in ((0, ref.Ic), (1, ref.Icr), (2, ref.Ics), (3, ref.Pr), (4, ref.Ps), (5, ref.P)):
+        got = P.ref_operator(N, which)
+        assert np.abs(got - M).max() < tol * max(1.0, np.abs(M).max()), which
+    Lg = P.ref_operator(N, 6)
+    want = np.concatenate(ref.Lg, axis=1)
+    assert np.abs(Lg - want).max() < tol * np.abs(want).max()
+    # face interpolation from the face nodes equals the full interpolation restricted to them
+    I1 = P.ref_operator(N, 7)
+    fn = [i for i in range(ref.Np) if abs(ref.s[i] + 1) < 1e-12]
+    fn = sorted(fn, key=lambda i: ref.r[i])
+    assert np.abs(I1 - ref.Ig[0][:, fn]).max() < 1e-12
+    assert np.abs(P.ref_operator(N, 8) - ref.mean_w).max() < 1e-14
+    assert np.abs(P.ref_operator(N, 9) - ref.Pi1[ref.vertex_nodes]).max() < 1e-12
+    assert np.abs(P.ref_operator(N, 10) - ref.wc).max() < 1e-14
+    assert np.abs(P.ref_operator(N, 11) - ref.wg).max() < 1e-14
+
+
+@pytest.mark.parametrize("gen", [
+    lambda: meshes.structured_rect(0, 1, 0, 1, 7, 5),
+    lambda: meshes.graded_jittered_rect(0, 10, 0, 3, 9, 6, ratio=4, jitter=0.2, seed=7),
+])
+def test_connectivity_and_nodes_bit_exact(lib, gen):
+    import paper_1403_1661_gb300 as P
+    vx, vy, E = gen()
+    E = E.copy()
+    E[::4, 1], E[::4, 2] = E[::4, 2].copy(), E[::4, 1].copy()   # mixed orientation
+    m = P.Mesh(vx, vy, E)
+    om = omesh.Mesh(vx, vy, E)
+    EToE, EToF = m.connectivity()
+    assert np.array_equal(EToE, om.EToE) and np.array_equal(EToF, om.EToF)
+    for N in (2, 4):
+        x, y = m.node_coords(N)
+        ref = oref.RefElement(N)
+        ox, oy = om.map_to_physical(ref.r, ref.s)
+        assert np.abs(x - ox).max() < 1e-12 and np.abs(y - oy).max() < 1e-12
+
+
+def test_levels_bit_exact(lib):
+    import paper_1403_1661_gb300 as P
+    scn = sc.tsunami(nx=60, ny=15, N=3)
+    vx, vy, E = scn.build_mesh()
+    m = P.Mesh(vx, vy, E)
+    om = omesh.Mesh(vx, vy, E)
+    ref = oref.RefElement(scn.N)
+    from oracle.problem import nodal_inputs
+    B, h, hu, hv = nodal_inputs(scn, om, ref)
+    lev, dtmin = m.levels(scn.N, h, hu, hv, scn.g, scn.cfl, scn.nlevels)
+    olev, odtmin = omesh.assign_levels(omesh.element_dt(om, scn.N, h, hu, hv, scn.g, scn.cfl), scn.nlevels)
+    assert np.array_equal(lev, olev)
+    assert abs(dtmin - odtmin) <= 1e-15 * odtmin
+    assert len(np.unique(lev)) >= 3
+
+
+def test_bad_meshes_are_rejected(lib):
+    import paper_1403_1661_gb300 as P
+    vx = np.array([0.0, 1.0, 0.0, 1.0, 0.5])
+    vy = np.array([0.0, 0.0, 1.0, 1.0, -1.0])
+    with pytest.raises(lib.SWEError) as ei:
+        P.Mesh(vx, vy, np.array([[0, 1, 2], [1, 0, 3], [0, 1, 4]]))   # face 0-1 shared 3 times
+    assert ei.value.code == lib.SWE_EINVAL
+    with pytest.raises(lib.SWEError):
+        P.Mesh(vx, vy, np.array([[0, 1, 7]]))                           # bad index
+    with pytest.raises(lib.SWEError):
+        P.Mesh(np.array([0.0, 1.0, 2.0]), np.array([0.0, 0.0, 0.0]), np.array([[0, 1, 2]]))  # degenerate
