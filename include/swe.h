@@ -143,7 +143,7 @@ int swe_set_bathymetry(swe_solver* solver, const double* B);
 int swe_set_state(swe_solver* solver, const double* h, const double* hu, const double* hv);
 
 /* Group elements into MRAB levels from the current state (Eq. cfl, Section 4):
- * dt_k = cfl/(N+1)^2 * H_k / a_k, H_k = twice the inradius, a_k = max over the
+ * dt_k = cfl/(N+1)^2 * H_k / a_k, H_k = the inradius, a_k = max over the
  * element's nodes of |u| + sqrt(g max(h, 1e-2 max h)); level l holds
  * 2^{l-1} dt_min <= dt_k < 2^l dt_min (capped at nlevels_max). level_out (K,
  * caller order, 1-based) and dt_min_out may be NULL. Restarts the history. */

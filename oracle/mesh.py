@@ -125,11 +125,11 @@ class Mesh:
 
 
 def element_dt(mesh: Mesh, N: int, h, hu, hv, g: float, cfl: float):
-    """dt_k = C H^k / a_k with H^k = 2 * inradius, C = cfl / (N+1)^2 and
+    """dt_k = C H^k / a_k with H^k = the inradius, C = cfl / (N+1)^2 and
     a_k = max over the element's nodes of |(u,v)| + sqrt(g max(h, h_ref)),
     h_ref = 1e-2 * max(h) so that dry elements keep a finite step."""
     perim = mesh.L.sum(axis=1)
-    H = 4.0 * mesh.area / perim
+    H = 2.0 * mesh.area / perim          # inradius = area / semi-perimeter
     hmax = float(np.max(h))
     href = 1e-2 * hmax
     hh = np.maximum(h, href)

@@ -152,7 +152,7 @@ void element_dt(const Mesh& m, int N, const double* h, const double* hu, const d
     }
     const double* L = &m.flen[3 * (size_t)k];
     double area = 2.0 * m.J[k];
-    double H = 4.0 * area / (L[0] + L[1] + L[2]);
+    double H = 2.0 * area / (L[0] + L[1] + L[2]);  // inradius
     dt[k] = C * H / amax;
   }
 }

@@ -31,7 +31,7 @@ struct Mesh {
 void tvb_stencil(const Mesh& m, std::vector<double>& alpha, std::vector<double>& beta,
                  std::vector<int32_t>& jsel);
 
-// dt_k = cfl/(N+1)^2 * H_k / a_k (Eq. cfl) with H_k = twice the inradius and
+// dt_k = cfl/(N+1)^2 * H_k / a_k (Eq. cfl) with H_k = the inradius and
 // a_k = max over the element's nodes of |u| + sqrt(g max(h, 1e-2 max h)),
 // u = hu/h where h exceeds that reference depth and 0 elsewhere.
 void element_dt(const Mesh& m, int N, const double* h, const double* hu, const double* hv, double g,

@@ -479,16 +479,59 @@ int download_state(const swe_solver* s, double* h, double* hu, double* hv) {
   return s->fp64 ? download_state_t<double>(s, h, hu, hv) : download_state_t<float>(s, h, hu, hv);
 }
 
+// current state in device precision, caller order, [3][K][NPP] (no conversion)
+template <typename T>
+int download_raw_t(const swe_solver* s, std::vector<char>& raw) {
+  const int K = s->K, npp = s->NPP;
+  std::vector<T> q(2 * 3 * (size_t)K * npp);
+  SWE_CUDA(cudaMemcpyAsync(q.data(), s->ws + s->lay.q, q.size() * sizeof(T), cudaMemcpyDeviceToHost,
+                           s->stream));
+  SWE_CUDA(cudaStreamSynchronize(s->stream));
+  raw.assign(3 * (size_t)K * npp * sizeof(T), 0);
+  T* out = reinterpret_cast<T*>(raw.data());
+  const size_t fs = (size_t)K * npp, bs = 3 * fs;
+  for (int e = 0; e < K; ++e) {
+    const int c = s->perm[e];
+    int l = 1;
+    while (l < s->L && e >= s->off[l]) ++l;
+    const int cur = (int)((s->k >> (l - 1)) & 1);
+    for (int f = 0; f < 3; ++f)
+      std::memcpy(out + f * fs + (size_t)c * npp, q.data() + cur * bs + f * fs + (size_t)e * npp,
+                  npp * sizeof(T));
+  }
+  return SWE_OK;
+}
+
+template <typename T>
+int upload_raw_t(swe_solver* s, const std::vector<char>& raw) {
+  const int K = s->K, npp = s->NPP;
+  const T* in = reinterpret_cast<const T*>(raw.data());
+  std::vector<T> q(3 * (size_t)K * npp);
+  const size_t fs = (size_t)K * npp;
+  for (int e = 0; e < K; ++e) {
+    const int c = s->perm[e];
+    for (int f = 0; f < 3; ++f)
+      std::memcpy(q.data() + f * fs + (size_t)e * npp, in + f * fs + (size_t)c * npp, npp * sizeof(T));
+  }
+  int rc = upload(s, s->lay.q, q.data(), q.size() * sizeof(T));
+  if (rc) return rc;
+  SWE_CUDA(cudaStreamSynchronize(s->stream));
+  return SWE_OK;
+}
+
 int apply_levels(swe_solver* s, const std::vector<int32_t>& level, double dt_min) {
-  // keep the current state across a re-ordering
-  std::vector<double> h, hu, hv;
+  // keep the current state (bit for bit, in device precision) across a re-ordering
+  std::vector<char> raw;
+  std::vector<uint8_t> dry_dev, dry_caller;
   const bool had_state = s->have_state;
   if (had_state) {
     if (!synchronous(s)) return fail(SWE_EINVAL, "levels can change only at a level-synchronous state");
-    const size_t n = (size_t)s->K * s->Np;
-    h.resize(n); hu.resize(n); hv.resize(n);
-    int rc = download_state(s, h.data(), hu.data(), hv.data());
+    int rc = s->fp64 ? download_raw_t<double>(s, raw) : download_raw_t<float>(s, raw);
     if (rc) return rc;
+    dry_dev.resize(s->K);
+    dry_caller.resize(s->K);
+    SWE_CUDA(cudaMemcpy(dry_dev.data(), s->ws + s->lay.dry, s->K, cudaMemcpyDeviceToHost));
+    for (int e = 0; e < s->K; ++e) dry_caller[s->perm[e]] = dry_dev[e];
     s->t0 += (double)s->k * s->dt_min;
   }
   s->level = level;
@@ -499,12 +542,14 @@ int apply_levels(swe_solver* s, const std::vector<int32_t>& level, double dt_min
   int rc = upload_mesh(s);
   if (rc) return rc;
   if (had_state) {
-    rc = s->fp64 ? upload_state_t<double>(s, h.data(), hu.data(), hv.data())
-                 : upload_state_t<float>(s, h.data(), hu.data(), hv.data());
+    rc = s->fp64 ? upload_raw_t<double>(s, raw) : upload_raw_t<float>(s, raw);
     if (rc) return rc;
     if ((rc = reset_counters(s))) return rc;
-    // recompute means / dry flags of the re-ordered state (positivity pass, no limiting)
+    // recompute the means of the re-ordered state (positivity pass, no limiting),
+    // then restore the dry flags of the latest positivity pass
     if ((rc = launch_limit(s, 0, 0, 0, s->K))) return rc;
+    for (int e = 0; e < s->K; ++e) dry_dev[e] = dry_caller[s->perm[e]];
+    SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.dry, dry_dev.data(), s->K, cudaMemcpyHostToDevice, s->stream));
     SWE_CUDA(cudaStreamSynchronize(s->stream));
   }
   return SWE_OK;

@@ -95,5 +95,5 @@ def test_element_dt_formula():
     h = np.full((m.K, ref.Np), 4.0)
     dt = element_dt(m, 2, h, 0 * h, 0 * h, g=1.0, cfl=0.9)
     # right isoceles triangles with legs 1: inradius = (2 - sqrt2)/2
-    H = 2 - np.sqrt(2)
+    H = (2 - np.sqrt(2)) / 2
     assert np.allclose(dt, 0.9 / 9 * H / 2.0)
