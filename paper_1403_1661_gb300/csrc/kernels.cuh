@@ -83,6 +83,13 @@ __device__ __forceinline__ void store_row_global(T* __restrict__ p, const T (&o)
   for (int k = 0; k < LEN / V::n; ++k) pv[k] = V::pack(&o[k * V::n]);
 }
 
+// Reciprocal and square root: hardware approximations in FP32 (about 1-2 ulp, no
+// slow-path branches), correctly rounded in FP64.
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float sqrt_nn(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+__device__ __forceinline__ double sqrt_nn(double x) { return sqrt(x); }
+
 template <typename T>
 __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 template <typename T>
@@ -137,12 +144,13 @@ template <typename T>
 __device__ __forceinline__ void wb_flux(const Trace<T>& m, const Trace<T>& p, T nx, T ny, T g, T h0,
                                         T& f0, T& f1, T& f2) {
   const T hm = m.eta - m.B, hp = p.eta - p.B;
-  const T um = hm > h0 ? m.hu / hm : T(0), vm = hm > h0 ? m.hv / hm : T(0);
-  const T up = hp > h0 ? p.hu / hp : T(0), vp = hp > h0 ? p.hv / hp : T(0);
+  const T im = hm > h0 ? recip(hm) : T(0), ip = hp > h0 ? recip(hp) : T(0);
+  const T um = m.hu * im, vm = m.hv * im;
+  const T up = p.hu * ip, vp = p.hv * ip;
   const T bmax = tmax(m.B, p.B);
   const T sm = tmax(T(0), m.eta - bmax), sp = tmax(T(0), p.eta - bmax);
   const T unm = um * nx + vm * ny, unp = up * nx + vp * ny;
-  const T lam = tmax(fabs(unm) + sqrt(g * sm), fabs(unp) + sqrt(g * sp));
+  const T lam = tmax(fabs(unm) + sqrt_nn(g * sm), fabs(unp) + sqrt_nn(g * sp));
   const T half = T(0.5);
   f0 = half * (sm * unm + sp * unp) - half * lam * (sp - sm);
   const T pres = half * g * m.eta * (hm - m.B) + T(0.25) * g * (sp - sm) * (sp + sm);
@@ -287,7 +295,8 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
         bsc += ics[jn] * bb[jn];
       }
       const T hc = ec - bc;
-      const T u = hc > h0 ? huc / hc : T(0), v = hc > h0 ? hvc / hc : T(0);
+      const T ih = hc > h0 ? recip(hc) : T(0);
+      const T u = huc * ih, v = hvc * ih;
       const T pr = T(0.5) * g * ec * (hc - bc);
       const T F0 = huc, F1 = huc * u + pr, F2 = huc * v;
       const T G0 = hvc, G1 = hvc * u, G2 = hvc * v + pr;
