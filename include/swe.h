@@ -205,6 +205,31 @@ int swe_profile_substeps(swe_solver* solver, int32_t n, double* out);
  * replayed graphs), for launch accounting. */
 int swe_kernel_launches(const swe_solver* solver, int64_t* launches);
 
+/* Mass and minimum depth of nodal data the caller already holds on the device,
+ * with no device allocation at all: the same reduction as swe_stats, but its
+ * per-block partial sums go to a fixed 16 KiB scratch array compiled into this
+ * library (it stays resident on every GPU that loads the library until the
+ * process exits) instead of a solver workspace. It is meant for callers that
+ * may not call cudaMalloc themselves: code whose device memory belongs to a
+ * host application with its own fixed arena, and latency-sensitive monitoring
+ * loops for which a cudaMalloc could synchronise the device. The paper has no
+ * counterpart of this call; it is a deployment convenience.
+ *   N         polynomial order, 2..5
+ *   K         number of elements, with K*Np <= 2^31-1 (SWE_EINVAL beyond)
+ *   dev_h     device, K x Np doubles: nodal depth h in the library's node order
+ *   dev_area  device, K doubles: element areas
+ *   dev_out   device, 2 doubles written: [0] sum_k area_k mean(h_k), [1] min nodal h
+ *   stream    cudaStream_t (as void*), may be NULL
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture. Every call shares the one scratch array per device, so
+ * calls whose kernels overlap on the GPU (concurrent streams) race and give
+ * wrong results; serialise them. Nothing in the scratch needs clearing: each
+ * call overwrites what it reads. Returns SWE_EINVAL / SWE_ECUDA with a message
+ * in swe_last_error(). */
+int swe_mass_hmin_static(int32_t N, int32_t K, const double* dev_h, const double* dev_area,
+                         double* dev_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -557,6 +557,10 @@ int apply_levels(swe_solver* s, const std::vector<int32_t>& level, double dt_min
 
 }  // namespace
 
+namespace swe {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace swe
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
