@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--nx", type=int, default=1000)
     ap.add_argument("--ny", type=int, default=250)
     ap.add_argument("--order", type=int, default=4)
-    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--precision", default="fp32tc", choices=["fp32tc", "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -146,7 +146,7 @@ def kernel_source_hash():
 def recorded_traffic(N, precision):
     """DRAM bytes per element of the stage kernel from a committed ncu summary, if
     it was taken on the current kernel sources."""
-    p = os.path.join(ROOT, "profiles", f"ncu_stage_{precision}_n{N}.json")
+    p = os.path.join(ROOT, "profiles", f"traffic_stage_{precision}_n{N}.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
@@ -273,7 +273,7 @@ def run_ours(args):
 
     # per-kernel timing of one more macro step (events around every launch)
     prof = s.profile_substeps(2 * period)
-    ts = 4 if args.precision == "fp32" else 8
+    ts = 8 if args.precision == "fp64" else 4
     bpe = stage_bytes_per_element(args.order, ts)
     stage_bytes = prof["stage_elements"] * bpe
     achieved = stage_bytes / (prof["stage_ms"] / 1e3) / 1e9
@@ -282,7 +282,8 @@ def run_ours(args):
     traffic_pe = recorded_traffic(args.order, args.precision)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (traffic_pe * per_launch_elems) if traffic_pe else None,
-                "kernel": f"k_stage<{'float' if ts == 4 else 'double'},{args.order}>",
+                "kernel": (f"k_stage_tc<{args.order}>" if args.precision == "fp32tc"
+                           else f"k_stage<{'float' if ts == 4 else 'double'},{args.order}>"),
                 "algorithmic_bytes_per_launch": bpe * per_launch_elems,
                 "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
                 "stage_share_of_step": prof["stage_ms"] / max(1e-9, prof["stage_ms"] + prof["tvb_ms"] + prof["other_ms"]),

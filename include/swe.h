@@ -54,6 +54,8 @@ extern "C" {
 /* ---- precision tiers ---------------------------------------------------- */
 #define SWE_FP64 0            /* everything in double precision                  */
 #define SWE_FP32 1            /* single precision, FP64 in the positivity limiter */
+#define SWE_FP32_TC 2         /* SWE_FP32 with the volume contractions on tensor cores
+                                 (split-BF16 products, FP32 accumulation)         */
 
 /* ---- limiter mask bits (Algorithm 2) ----------------------------------- */
 #define SWE_LIM_PP 1          /* positivity-preserving limiter M Pi (Algorithm 3) */
@@ -71,7 +73,7 @@ typedef struct swe_solver swe_solver;
  *   cfl      CFL number; the per-element step is cfl/(N+1)^2 * H_k / a_k (Eq. cfl)
  *   N        polynomial order (2..5 in this build)
  *   nlevels_max  number of MRAB levels allowed (>= 1; 1 = single-rate AB3)
- *   precision    SWE_FP64 or SWE_FP32
+ *   precision    SWE_FP64, SWE_FP32 or SWE_FP32_TC
  *   limiter_mask SWE_LIM_PP | SWE_LIM_TVB applied after every update
  *   dry_mode     0: a dry element is reset to h = h0, hu = hv = 0 (Algorithm 3,
  *                injected mass tallied); 1: reset to its mean depth (mass kept) */
@@ -155,7 +157,7 @@ int swe_set_levels(swe_solver* solver, const int32_t* level, double dt_min);
 
 /* One evaluation of R(Q) = N(Q) + S(Q^{g,+}, Q^{g,-}) (Eq. ode) at the current,
  * level-synchronous state. dev_R: device array [3][K][Np] of the solver's
- * precision (double for SWE_FP64, float for SWE_FP32), caller order, written on
+ * precision (double for SWE_FP64, float otherwise), caller order, written on
  * the solver's stream. */
 int swe_rhs(swe_solver* solver, void* dev_R);
 

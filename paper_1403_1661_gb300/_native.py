@@ -23,6 +23,7 @@ SWE_EUNSUPPORTED = -6
 
 SWE_FP64 = 0
 SWE_FP32 = 1
+SWE_FP32_TC = 2
 SWE_LIM_PP = 1
 SWE_LIM_TVB = 2
 

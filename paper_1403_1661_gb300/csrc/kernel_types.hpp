@@ -22,21 +22,49 @@ struct Dims {
 };
 
 // Operator block (element type T), packed by the host, staged in shared memory.
+// The per-element (surface, limiter) operators come first so a kernel that does
+// its volume contractions elsewhere can stage only [0, TAIL).
 template <int N>
 struct OpLayout {
   using D = Dims<N>;
-  static constexpr int IC = 0;                                 // [NCUB][NPP]
+  static constexpr int LGT = 0;                                // [3 NG][NPP], Lg^T
+  static constexpr int I1D = LGT + 3 * D::NG * D::NPP;         // [NG][NFPP]
+  static constexpr int MW = I1D + D::NG * D::NFPP;             // [NPP] mean weights
+  static constexpr int T1 = MW + D::NPP;                       // [3][NPP] P1 vertex map
+  static constexpr int BARY = T1 + 3 * D::NPP;                 // [NPP][4] barycentric
+  static constexpr int TAIL = BARY + 4 * D::NPP;
+  static constexpr int IC = TAIL;                              // [NCUB][NPP]
   static constexpr int ICR = IC + D::NCUB * D::NPP;            // [NCUB][NPP]
   static constexpr int ICS = ICR + D::NCUB * D::NPP;           // [NCUB][NPP]
   static constexpr int PRT = ICS + D::NCUB * D::NPP;           // [NCUB][NPP], Pr^T
   static constexpr int PST = PRT + D::NCUB * D::NPP;           // [NCUB][NPP], Ps^T
   static constexpr int PT = PST + D::NCUB * D::NPP;            // [NCUB][NPP], P^T
-  static constexpr int LGT = PT + D::NCUB * D::NPP;            // [3 NG][NPP], Lg^T
-  static constexpr int I1D = LGT + 3 * D::NG * D::NPP;         // [NG][NFPP]
-  static constexpr int MW = I1D + D::NG * D::NFPP;             // [NPP] mean weights
-  static constexpr int T1 = MW + D::NPP;                       // [3][NPP] P1 vertex map
-  static constexpr int BARY = T1 + 3 * D::NPP;                 // [NPP][4] barycentric
-  static constexpr int SIZE = BARY + 4 * D::NPP;
+  static constexpr int SIZE = PT + D::NCUB * D::NPP;
+};
+
+// Tensor-core tiling of the volume contractions (mma.sync, bf16 operands).
+//   KP   node dimension padded to the k16 step of the interpolation
+//   CT   cubature points in tiles of 8 (n of the interpolation, k of the projection)
+//   NT   nodes in tiles of 8 (n of the projection)
+template <int N>
+struct TcDims {
+  using D = Dims<N>;
+  static constexpr int KP = (D::NP + 15) / 16 * 16;
+  static constexpr int KSTEP = KP / 16;
+  static constexpr int CT = (D::NCUB + 7) / 8;
+  static constexpr int NT = (D::NP + 7) / 8;
+  static constexpr int NPT = 8 * NT;
+};
+
+// Operator fragments in register order (uint32 = two bf16), hi and lo parts.
+//   INTERP [3 ops Ic,Icr,Ics][CT][KSTEP][2 parts][32 lanes][2 regs]
+//   PROJ   [3 ops Pr,Ps,P][CT][NT][2 parts][32 lanes]
+template <int N>
+struct TcLayout {
+  using C = TcDims<N>;
+  static constexpr int INTERP = 0;
+  static constexpr int PROJ = INTERP + 3 * C::CT * C::KSTEP * 2 * 64;
+  static constexpr int SIZE = PROJ + 3 * C::CT * C::NT * 2 * 32;
 };
 
 // Pointers into the caller-owned workspace.
@@ -52,6 +80,7 @@ struct DevState {
   uint8_t* dry;         // [K] dry flag of the latest positivity pass
   const double* Bbar;   // [K] mean of B (FP64)
   const T* ops;         // operator block
+  const uint32_t* tcops; // tensor-core operator fragments (FP32 tensor-core tier)
   double* acc;          // accumulators: [0] injected mass
   int* flags;           // [0] non-finite state detected
   long long* macro;     // macro-step counter (advanced on the device)
@@ -62,10 +91,13 @@ struct Sched {
   int L;                     // levels in use
   int off[kMaxLevels + 1];   // level l (1-based) occupies [off[l-1], off[l])
   double dt_min;
+  double dtl_d[kMaxLevels];  // step of level l = 2^{l-1} dt_min, in both precisions
+  float dtl_f[kMaxLevels];
 };
 
 struct Phys {
   double g, h0, eps, tvb_M, tvb_nu;
+  float eps_f;
   int pp, dry_mode;
 };
 

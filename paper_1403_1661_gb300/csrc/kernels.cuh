@@ -95,23 +95,32 @@ __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 template <typename T>
 __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 
-// Adams-Bashforth weights (equal steps) for R^(0), R^(-1), R^(-2).
-__device__ __forceinline__ void ab_weights(int depth, double w[3]) {
-  if (depth <= 1) { w[0] = 1.0; w[1] = 0.0; w[2] = 0.0; }
-  else if (depth == 2) { w[0] = 1.5; w[1] = -0.5; w[2] = 0.0; }
-  else { w[0] = 23.0 / 12.0; w[1] = -16.0 / 12.0; w[2] = 5.0 / 12.0; }
+// Adams-Bashforth weights (equal steps) for R^(0), R^(-1), R^(-2), in the
+// kernel's precision (no FP64 work on the FP32 path).
+template <typename T>
+__device__ __forceinline__ void ab_weights(int depth, T w[3]) {
+  if (depth <= 1) { w[0] = T(1); w[1] = T(0); w[2] = T(0); }
+  else if (depth == 2) { w[0] = T(1.5); w[1] = T(-0.5); w[2] = T(0); }
+  else { w[0] = T(23) / T(12); w[1] = T(-16) / T(12); w[2] = T(5) / T(12); }
 }
 
 // Integral over [0, theta] of the Lagrange interpolant of R at tau = 0, -1, -2.
-__device__ __forceinline__ void ab_partial_weights(int depth, double t, double w[3]) {
-  if (depth <= 1) { w[0] = t; w[1] = 0.0; w[2] = 0.0; }
-  else if (depth == 2) { w[0] = t + 0.5 * t * t; w[1] = -0.5 * t * t; w[2] = 0.0; }
+template <typename T>
+__device__ __forceinline__ void ab_partial_weights(int depth, T t, T w[3]) {
+  if (depth <= 1) { w[0] = t; w[1] = T(0); w[2] = T(0); }
+  else if (depth == 2) { w[0] = t + T(0.5) * t * t; w[1] = T(-0.5) * t * t; w[2] = T(0); }
   else {
-    w[0] = t * t * t / 6.0 + 0.75 * t * t + t;
-    w[1] = -(t * t * t / 3.0 + t * t);
-    w[2] = t * t * t / 6.0 + 0.25 * t * t;
+    const T t2 = t * t, t3 = t2 * t;
+    w[0] = t3 / T(6) + T(0.75) * t2 + t;
+    w[1] = -(t3 / T(3) + t2);
+    w[2] = t3 / T(6) + T(0.25) * t2;
   }
 }
+
+__device__ __forceinline__ float level_dt(const Sched& sc, int l, float) { return sc.dtl_f[l - 1]; }
+__device__ __forceinline__ double level_dt(const Sched& sc, int l, double) { return sc.dtl_d[l - 1]; }
+__device__ __forceinline__ float eps_of(const Phys& ph, float) { return ph.eps_f; }
+__device__ __forceinline__ double eps_of(const Phys& ph, double) { return ph.eps; }
 
 __host__ __device__ constexpr int face_node(int N, int f, int m) {
   // node index of position m along face f (from vertex f to f+1), lattice order
@@ -166,15 +175,15 @@ __device__ __forceinline__ void wb_flux(const Trace<T>& m, const Trace<T>& p, T 
 template <typename T, int N>
 __device__ __forceinline__ int positivity(T (&eta)[Dims<N>::NPP], T (&hu)[Dims<N>::NPP],
                                           T (&hv)[Dims<N>::NPP], const T (&bb)[Dims<N>::NPP],
-                                          const T* __restrict__ sops, double Bbar, double area,
-                                          const Phys& ph, double* injected, T mean_out[3]) {
+                                          const T* __restrict__ sops, double Bbar, T rx, T ry, T sx,
+                                          T sy, const Phys& ph, double* injected, T mean_out[3]) {
   using D = Dims<N>;
   using O = OpLayout<N>;
   const T* mw = sops + O::MW;
   T hmin = eta[0] - bb[0];
 #pragma unroll
   for (int jn = 1; jn < D::NP; ++jn) hmin = tmin(hmin, eta[jn] - bb[jn]);
-  const bool trig = ph.pp && ((double)hmin <= ph.eps);
+  const bool trig = ph.pp && (hmin <= eps_of(ph, T(0)));
   if (!trig) {
     T me = 0, mu = 0, mv = 0;
 #pragma unroll
@@ -203,6 +212,7 @@ __device__ __forceinline__ int positivity(T (&eta)[Dims<N>::NPP], T (&hu)[Dims<N
       hu[jn] = T(0);
       hv[jn] = T(0);
     }
+    const double area = 2.0 / ((double)rx * (double)sy - (double)ry * (double)sx);
     *injected += area * (hn - hbar);
     mean_out[0] = (T)(hn + Bbar); mean_out[1] = T(0); mean_out[2] = T(0);
     return 1;
@@ -240,6 +250,197 @@ __device__ __forceinline__ int positivity(T (&eta)[Dims<N>::NPP], T (&hu)[Dims<N
   return 0;
 }
 
+// Surface term (Section 7.2) for element e: traces at the Gauss points of its
+// three faces, the well-balanced flux, and the lift subtracted from R (in
+// registers). own(f, j) returns the element's own field f (eta, hu, hv, B) at
+// node j, so the caller decides whether the state sits in registers or in
+// shared memory. Shared by the SIMT and the tensor-core stage kernels.
+template <typename T, int N, typename Own>
+__device__ __forceinline__ void surface_lift(const StageParams<T>& p, const T* __restrict__ sops, int e,
+                                             long long k, const Own& own, T rx, T ry, T sx, T sy,
+                                             T (&R0)[Dims<N>::NP], T (&R1)[Dims<N>::NP],
+                                             T (&R2)[Dims<N>::NP]) {
+  using D = Dims<N>;
+  using O = OpLayout<N>;
+  constexpr int NP = D::NP, NPP = D::NPP, NFP = D::NFP, NG = D::NG;
+  const Sched& sc = p.sc;
+  const int K = sc.K;
+  const T g = (T)p.ph.g, h0 = (T)p.ph.h0;
+  const size_t fstride = (size_t)K * NPP;
+  const size_t bstride = 3 * fstride;
+  // ---- surface term (Section 7.2): traces, well-balanced flux, lift ----
+  const int4 cn = __ldg(p.s.conn + e);
+  const int nbs[3] = {cn.x, cn.y, cn.z};
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    // outward normal times sJ/J from the affine factors
+    const T vxn = f == 0 ? -sx : (f == 1 ? rx + sx : -rx);
+    const T vyn = f == 0 ? -sy : (f == 1 ? ry + sy : -ry);
+    const T scale = sqrt(vxn * vxn + vyn * vyn);
+    const T nx = vxn / scale, ny = vyn / scale;
+    // neighbour face-node values, in this element's traversal order
+    T ne[NFP], nu[NFP], nv[NFP], nB[NFP];
+    const int nb = nbs[f];
+    if (nb >= 0) {
+      const int fn = (cn.w >> (2 * f)) & 3;
+      const int ln = level_of(sc, nb);
+      const long long an = k >> (ln - 1);
+      const long long pern = 1LL << (ln - 1);
+      const long long phase = k & (pern - 1);
+      const T* qn = p.s.q + (size_t)(an & 1) * bstride;
+#pragma unroll
+      for (int m = 0; m < NFP; ++m) {
+        const size_t idx = (size_t)nb * NPP + face_node_rt(N, fn, NFP - 1 - m);
+        ne[m] = __ldg(qn + idx);
+        nu[m] = __ldg(qn + fstride + idx);
+        nv[m] = __ldg(qn + 2 * fstride + idx);
+        nB[m] = __ldg(p.s.B + idx);
+      }
+      if (phase != 0) {  // neighbour between its steps: Adams-Bashforth polynomial at t_k
+        const int depth = an + 1 < 3 ? (int)(an + 1) : 3;
+        T w[3];
+        ab_partial_weights<T>(depth, (T)phase / (T)pern, w);
+        const T dtn = level_dt(sc, ln, T(0));
+        for (int s = 0; s < depth; ++s) {
+          const T ws = dtn * w[s];
+          const T* rs = p.s.ring + (size_t)((an - s) % 3) * bstride;
+#pragma unroll
+          for (int m = 0; m < NFP; ++m) {
+            const size_t idx = (size_t)nb * NPP + face_node_rt(N, fn, NFP - 1 - m);
+            ne[m] += ws * __ldg(rs + idx);
+            nu[m] += ws * __ldg(rs + fstride + idx);
+            nv[m] += ws * __ldg(rs + 2 * fstride + idx);
+          }
+        }
+      }
+    }
+#pragma unroll 1
+    for (int gq = 0; gq < NG; ++gq) {
+      T i1[D::NFPP];
+      load_row<T, D::NFPP>(sops + O::I1D + gq * D::NFPP, i1);
+      Trace<T> tm = {0, 0, 0, 0}, tp;
+#pragma unroll
+      for (int m = 0; m < NFP; ++m) {
+        const int jn = face_node(N, f, m);
+        tm.eta += i1[m] * own(0, jn);
+        tm.hu += i1[m] * own(1, jn);
+        tm.hv += i1[m] * own(2, jn);
+        tm.B += i1[m] * own(3, jn);
+      }
+      if (nb >= 0) {
+        tp = {0, 0, 0, 0};
+#pragma unroll
+        for (int m = 0; m < NFP; ++m) {
+          tp.eta += i1[m] * ne[m];
+          tp.hu += i1[m] * nu[m];
+          tp.hv += i1[m] * nv[m];
+          tp.B += i1[m] * nB[m];
+        }
+      } else {  // reflecting wall: mirror the normal momentum
+        const T mn = tm.hu * nx + tm.hv * ny;
+        tp = {tm.eta, tm.hu - T(2) * mn * nx, tm.hv - T(2) * mn * ny, tm.B};
+      }
+      T f0, f1, f2;
+      wb_flux<T>(tm, tp, nx, ny, g, h0, f0, f1, f2);
+      f0 *= scale; f1 *= scale; f2 *= scale;
+      T lg[NPP];
+      load_row<T, NPP>(sops + O::LGT + (f * NG + gq) * NPP, lg);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        R0[i] -= lg[i] * f0;
+        R1[i] -= lg[i] * f1;
+        R2[i] -= lg[i] * f2;
+      }
+    }
+  }
+}
+
+// Adams-Bashforth commit (Algorithm 1) and positivity limiter (Algorithm 3) of
+// element e (mode 0), or the R output in the caller's layout (mode 1).
+template <typename T, int N>
+__device__ __forceinline__ void commit_and_limit(const StageParams<T>& p, const T* __restrict__ sops, int e,
+                                                 int lev, long long a, T (&eta)[Dims<N>::NPP],
+                                                 T (&hu)[Dims<N>::NPP], T (&hv)[Dims<N>::NPP],
+                                                 const T (&bb)[Dims<N>::NPP], T rx, T ry, T sx, T sy,
+                                                 const T (&R0)[Dims<N>::NP], const T (&R1)[Dims<N>::NP],
+                                                 const T (&R2)[Dims<N>::NP], double* injected_acc) {
+  using D = Dims<N>;
+  constexpr int NP = D::NP, NPP = D::NPP;
+  const Sched& sc = p.sc;
+  const int K = sc.K;
+  const int dst = (int)((a + 1) & 1);
+  const size_t fstride = (size_t)K * NPP;
+  const size_t bstride = 3 * fstride;
+  double& injected = *injected_acc;
+  if (p.mode == 1) {  // R only, caller layout
+    const int ce = p.perm[e];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      p.out[((size_t)0 * K + ce) * NP + i] = R0[i];
+      p.out[((size_t)1 * K + ce) * NP + i] = R1[i];
+      p.out[((size_t)2 * K + ce) * NP + i] = R2[i];
+    }
+    return;
+  }
+
+  // ---- Adams-Bashforth commit (Algorithm 1) ----
+  const int depth = a + 1 < 3 ? (int)(a + 1) : 3;
+  T wab[3];
+  ab_weights<T>(depth, wab);
+  const T dtl = level_dt(sc, lev, T(0));
+  const T c0 = dtl * wab[0], c1 = dtl * wab[1], c2 = dtl * wab[2];
+  T* ring = p.s.ring;
+  const size_t eo = (size_t)e * NPP;
+  {
+    T pad[NPP];
+#pragma unroll
+    for (int i = 0; i < NPP; ++i) pad[i] = i < NP ? R0[i] : T(0);
+    store_row_global<T, NPP>(ring + (size_t)(a % 3) * bstride + 0 * fstride + eo, pad);
+#pragma unroll
+    for (int i = 0; i < NPP; ++i) pad[i] = i < NP ? R1[i] : T(0);
+    store_row_global<T, NPP>(ring + (size_t)(a % 3) * bstride + 1 * fstride + eo, pad);
+#pragma unroll
+    for (int i = 0; i < NPP; ++i) pad[i] = i < NP ? R2[i] : T(0);
+    store_row_global<T, NPP>(ring + (size_t)(a % 3) * bstride + 2 * fstride + eo, pad);
+  }
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    eta[i] += c0 * R0[i];
+    hu[i] += c0 * R1[i];
+    hv[i] += c0 * R2[i];
+  }
+  for (int s = 1; s < depth; ++s) {
+    const T cs = s == 1 ? c1 : c2;
+    const T* rs = ring + (size_t)((a - s) % 3) * bstride + eo;
+    T r[NPP];
+    load_row_global<T, NPP>(rs, r);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) eta[i] += cs * r[i];
+    load_row_global<T, NPP>(rs + fstride, r);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) hu[i] += cs * r[i];
+    load_row_global<T, NPP>(rs + 2 * fstride, r);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) hv[i] += cs * r[i];
+  }
+
+  // ---- positivity limiter (Algorithm 3) and means ----
+  T mean[3];
+  const int dryf = positivity<T, N>(eta, hu, hv, bb, sops, __ldg(p.s.Bbar + e), rx, ry, sx, sy, p.ph,
+                                    &injected, mean);
+  if (!(isfinite((double)mean[0]) && isfinite((double)mean[1]) && isfinite((double)mean[2])))
+    atomicOr(p.s.flags, 1);
+#pragma unroll
+  for (int i = NP; i < NPP; ++i) { eta[i] = 0; hu[i] = 0; hv[i] = 0; }
+  store_row_global<T, NPP>(p.s.q + dst * bstride + 0 * fstride + eo, eta);
+  store_row_global<T, NPP>(p.s.q + dst * bstride + 1 * fstride + eo, hu);
+  store_row_global<T, NPP>(p.s.q + dst * bstride + 2 * fstride + eo, hv);
+  p.s.means[4 * (size_t)e + 0] = mean[0];
+  p.s.means[4 * (size_t)e + 1] = mean[1];
+  p.s.means[4 * (size_t)e + 2] = mean[2];
+  p.s.dry[e] = (uint8_t)dryf;
+}
+
 // --------------------------------------------------------------------------
 // the stage kernel: R(Q) for one element (volume + surface + lift), then the
 // Adams-Bashforth commit and the positivity limiter (mode 0) or R only (mode 1)
@@ -248,7 +449,7 @@ template <typename T, int N>
 __global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
   using D = Dims<N>;
   using O = OpLayout<N>;
-  constexpr int NP = D::NP, NPP = D::NPP, NFP = D::NFP, NG = D::NG, NCUB = D::NCUB;
+  constexpr int NP = D::NP, NPP = D::NPP, NCUB = D::NCUB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sops = reinterpret_cast<T*>(smem_raw);
   stage_ops<T, N>(sops, p.s.ops);
@@ -262,7 +463,7 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.nactive; e += gridDim.x * blockDim.x) {
     const int lev = level_of(sc, e);
     const long long a = k >> (lev - 1);
-    const int src = (int)(a & 1), dst = src ^ 1;
+    const int src = (int)(a & 1);
     const size_t fstride = (size_t)K * NPP;            // between fields
     const size_t bstride = 3 * fstride;                // between buffers
     T eta[NPP], hu[NPP], hv[NPP], bb[NPP];
@@ -316,160 +517,9 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
       }
     }
 
-    // ---- surface term (Section 7.2): traces, well-balanced flux, lift ----
-    const int4 cn = __ldg(p.s.conn + e);
-    const int nbs[3] = {cn.x, cn.y, cn.z};
-#pragma unroll
-    for (int f = 0; f < 3; ++f) {
-      // outward normal times sJ/J from the affine factors
-      const T vxn = f == 0 ? -sx : (f == 1 ? rx + sx : -rx);
-      const T vyn = f == 0 ? -sy : (f == 1 ? ry + sy : -ry);
-      const T scale = sqrt(vxn * vxn + vyn * vyn);
-      const T nx = vxn / scale, ny = vyn / scale;
-      // neighbour face-node values, in this element's traversal order
-      T ne[NFP], nu[NFP], nv[NFP], nB[NFP];
-      const int nb = nbs[f];
-      if (nb >= 0) {
-        const int fn = (cn.w >> (2 * f)) & 3;
-        const int ln = level_of(sc, nb);
-        const long long an = k >> (ln - 1);
-        const long long pern = 1LL << (ln - 1);
-        const long long phase = k & (pern - 1);
-        const T* qn = p.s.q + (size_t)(an & 1) * bstride;
-#pragma unroll
-        for (int m = 0; m < NFP; ++m) {
-          const size_t idx = (size_t)nb * NPP + face_node_rt(N, fn, NFP - 1 - m);
-          ne[m] = __ldg(qn + idx);
-          nu[m] = __ldg(qn + fstride + idx);
-          nv[m] = __ldg(qn + 2 * fstride + idx);
-          nB[m] = __ldg(p.s.B + idx);
-        }
-        if (phase != 0) {  // neighbour between its steps: Adams-Bashforth polynomial at t_k
-          const int depth = an + 1 < 3 ? (int)(an + 1) : 3;
-          double w[3];
-          ab_partial_weights(depth, (double)phase / (double)pern, w);
-          const double dtn = sc.dt_min * (double)pern;
-          for (int s = 0; s < depth; ++s) {
-            const T ws = (T)(dtn * w[s]);
-            const T* rs = p.s.ring + (size_t)((an - s) % 3) * bstride;
-#pragma unroll
-            for (int m = 0; m < NFP; ++m) {
-              const size_t idx = (size_t)nb * NPP + face_node_rt(N, fn, NFP - 1 - m);
-              ne[m] += ws * __ldg(rs + idx);
-              nu[m] += ws * __ldg(rs + fstride + idx);
-              nv[m] += ws * __ldg(rs + 2 * fstride + idx);
-            }
-          }
-        }
-      }
-#pragma unroll 1
-      for (int gq = 0; gq < NG; ++gq) {
-        T i1[D::NFPP];
-        load_row<T, D::NFPP>(sops + O::I1D + gq * D::NFPP, i1);
-        Trace<T> tm = {0, 0, 0, 0}, tp;
-#pragma unroll
-        for (int m = 0; m < NFP; ++m) {
-          const int jn = face_node(N, f, m);
-          tm.eta += i1[m] * eta[jn];
-          tm.hu += i1[m] * hu[jn];
-          tm.hv += i1[m] * hv[jn];
-          tm.B += i1[m] * bb[jn];
-        }
-        if (nb >= 0) {
-          tp = {0, 0, 0, 0};
-#pragma unroll
-          for (int m = 0; m < NFP; ++m) {
-            tp.eta += i1[m] * ne[m];
-            tp.hu += i1[m] * nu[m];
-            tp.hv += i1[m] * nv[m];
-            tp.B += i1[m] * nB[m];
-          }
-        } else {  // reflecting wall: mirror the normal momentum
-          const T mn = tm.hu * nx + tm.hv * ny;
-          tp = {tm.eta, tm.hu - T(2) * mn * nx, tm.hv - T(2) * mn * ny, tm.B};
-        }
-        T f0, f1, f2;
-        wb_flux<T>(tm, tp, nx, ny, g, h0, f0, f1, f2);
-        f0 *= scale; f1 *= scale; f2 *= scale;
-        T lg[NPP];
-        load_row<T, NPP>(sops + O::LGT + (f * NG + gq) * NPP, lg);
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-          R0[i] -= lg[i] * f0;
-          R1[i] -= lg[i] * f1;
-          R2[i] -= lg[i] * f2;
-        }
-      }
-    }
-
-    if (p.mode == 1) {  // R only, caller layout
-      const int ce = p.perm[e];
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        p.out[((size_t)0 * K + ce) * NP + i] = R0[i];
-        p.out[((size_t)1 * K + ce) * NP + i] = R1[i];
-        p.out[((size_t)2 * K + ce) * NP + i] = R2[i];
-      }
-      continue;
-    }
-
-    // ---- Adams-Bashforth commit (Algorithm 1) ----
-    const int depth = a + 1 < 3 ? (int)(a + 1) : 3;
-    double wab[3];
-    ab_weights(depth, wab);
-    const double dtl = sc.dt_min * (double)(1LL << (lev - 1));
-    const T c0 = (T)(dtl * wab[0]), c1 = (T)(dtl * wab[1]), c2 = (T)(dtl * wab[2]);
-    T* ring = p.s.ring;
-    const size_t eo = (size_t)e * NPP;
-    {
-      T pad[NPP];
-#pragma unroll
-      for (int i = 0; i < NPP; ++i) pad[i] = i < NP ? R0[i] : T(0);
-      store_row_global<T, NPP>(ring + (size_t)(a % 3) * bstride + 0 * fstride + eo, pad);
-#pragma unroll
-      for (int i = 0; i < NPP; ++i) pad[i] = i < NP ? R1[i] : T(0);
-      store_row_global<T, NPP>(ring + (size_t)(a % 3) * bstride + 1 * fstride + eo, pad);
-#pragma unroll
-      for (int i = 0; i < NPP; ++i) pad[i] = i < NP ? R2[i] : T(0);
-      store_row_global<T, NPP>(ring + (size_t)(a % 3) * bstride + 2 * fstride + eo, pad);
-    }
-#pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      eta[i] += c0 * R0[i];
-      hu[i] += c0 * R1[i];
-      hv[i] += c0 * R2[i];
-    }
-    for (int s = 1; s < depth; ++s) {
-      const T cs = s == 1 ? c1 : c2;
-      const T* rs = ring + (size_t)((a - s) % 3) * bstride + eo;
-      T r[NPP];
-      load_row_global<T, NPP>(rs, r);
-#pragma unroll
-      for (int i = 0; i < NP; ++i) eta[i] += cs * r[i];
-      load_row_global<T, NPP>(rs + fstride, r);
-#pragma unroll
-      for (int i = 0; i < NP; ++i) hu[i] += cs * r[i];
-      load_row_global<T, NPP>(rs + 2 * fstride, r);
-#pragma unroll
-      for (int i = 0; i < NP; ++i) hv[i] += cs * r[i];
-    }
-
-    // ---- positivity limiter (Algorithm 3) and means ----
-    const double J = 1.0 / ((double)rx * (double)sy - (double)ry * (double)sx);
-    T mean[3];
-    const int dryf = positivity<T, N>(eta, hu, hv, bb, sops, __ldg(p.s.Bbar + e), 2.0 * J, p.ph,
-                                      &injected, mean);
-    if (!(isfinite((double)mean[0]) && isfinite((double)mean[1]) && isfinite((double)mean[2])))
-      atomicOr(p.s.flags, 1);
-#pragma unroll
-    for (int i = NP; i < NPP; ++i) { eta[i] = 0; hu[i] = 0; hv[i] = 0; }
-    store_row_global<T, NPP>(p.s.q + dst * bstride + 0 * fstride + eo, eta);
-    store_row_global<T, NPP>(p.s.q + dst * bstride + 1 * fstride + eo, hu);
-    store_row_global<T, NPP>(p.s.q + dst * bstride + 2 * fstride + eo, hv);
-    p.s.means[4 * (size_t)e + 0] = mean[0];
-    p.s.means[4 * (size_t)e + 1] = mean[1];
-    p.s.means[4 * (size_t)e + 2] = mean[2];
-    p.s.dry[e] = (uint8_t)dryf;
+    auto own = [&](int f, int jn) -> T { return f == 0 ? eta[jn] : (f == 1 ? hu[jn] : (f == 2 ? hv[jn] : bb[jn])); };
+    surface_lift<T, N>(p, sops, e, k, own, rx, ry, sx, sy, R0, R1, R2);
+    commit_and_limit<T, N>(p, sops, e, lev, a, eta, hu, hv, bb, rx, ry, sx, sy, R0, R1, R2, &injected);
   }
   if (injected != 0.0) atomicAdd(p.s.acc, injected);
 }
@@ -499,9 +549,8 @@ __global__ void __launch_bounds__(kBlock) k_positivity(LimitParams<T> p) {
     load_row_global<T, NPP>(q + 2 * fstride + eo, hv);
     load_row_global<T, NPP>(p.s.B + eo, bb);
     const T rx = p.s.geo[4 * e], ry = p.s.geo[4 * e + 1], sx = p.s.geo[4 * e + 2], sy = p.s.geo[4 * e + 3];
-    const double J = 1.0 / ((double)rx * (double)sy - (double)ry * (double)sx);
     T mean[3];
-    const int dryf = positivity<T, N>(eta, hu, hv, bb, sops, p.s.Bbar[e], 2.0 * J, p.ph, &injected, mean);
+    const int dryf = positivity<T, N>(eta, hu, hv, bb, sops, p.s.Bbar[e], rx, ry, sx, sy, p.ph, &injected, mean);
     store_row_global<T, NPP>(q + eo, eta);
     store_row_global<T, NPP>(q + fstride + eo, hu);
     store_row_global<T, NPP>(q + 2 * fstride + eo, hv);

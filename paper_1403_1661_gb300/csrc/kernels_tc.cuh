@@ -1,0 +1,298 @@
+// Stage kernel with the volume contractions on tensor cores (FP32 tier with
+// split-BF16 products, Section 7.1's N(Q) = Pr cF1 + Ps cF2 + P cS).
+//
+// Each warp owns 32 elements (two 16-row m-tiles). Per m-tile and per tile of 8
+// cubature points:
+//   interpolation  D[16 el x 8 pts] = State[16 el x Np] * Op^T  (mma m16n8k16),
+//                  for eta, hu, hv, B with Ic and for B with Icr, Ics;
+//   flux           evaluated in registers on the accumulator layout: lane (g, t)
+//                  holds elements g, g+8 at cubature points 2t, 2t+1, which is
+//                  exactly the A-fragment layout of the next product;
+//   projection     R[16 el x Np] += Flux[16 el x 8 pts] * Pr^T (Ps^T, P^T)
+//                  (mma m16n8k8), accumulated over all cubature tiles.
+// Every product is split: a = a_hi + a_lo in bfloat16 (operators and data), and
+// a*b ~ a_hi*b_hi + a_hi*b_lo + a_lo*b_hi with FP32 accumulation (relative error
+// of order 2^-16 per product). The warp then hands R and the state to one thread
+// per element through shared memory for the surface term, the Adams-Bashforth
+// commit and the positivity limiter, which are shared with the SIMT kernel.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "kernels.cuh"
+
+namespace swe {
+
+constexpr int kTcWarps = 4;
+constexpr int kTcBlock = 32 * kTcWarps;
+
+__device__ __forceinline__ void mma_k16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void mma_k8(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(b0));
+}
+
+// two floats -> (hi, lo) bf16x2 pairs; the first float goes to the low half
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+template <int N>
+struct TcSmem {
+  using D = Dims<N>;
+  using C = TcDims<N>;
+  static constexpr int ROW = C::KP;                      // floats per state row (nodes, zero padded)
+  static constexpr int RROW = C::NPT;                    // floats per R row
+  // per warp: state [4 fields][32 el][ROW], R [3][32][RROW], geo [32][4]
+  static constexpr int STATE = 0;
+  static constexpr int RT = STATE + 4 * 32 * ROW;
+  static constexpr int GEO = RT + 3 * 32 * RROW;
+  static constexpr int WARP = GEO + 32 * 4;              // floats per warp
+  static constexpr int OPS = OpLayout<N>::TAIL;          // floats of per-element operators (staged first)
+  static constexpr int BYTES = (OPS + kTcWarps * WARP) * 4;
+};
+
+template <int N>
+__global__ void __launch_bounds__(kTcBlock, (N <= 4 ? 3 : 2)) k_stage_tc(StageParams<float> p) {
+  using D = Dims<N>;
+  using C = TcDims<N>;
+  using TL = TcLayout<N>;
+  using SM = TcSmem<N>;
+  constexpr int NP = D::NP, NPP = D::NPP, KP = C::KP, KSTEP = C::KSTEP, CT = C::CT, NT = C::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sops = reinterpret_cast<float*>(smem_raw);                       // [0, OPS)
+  float* swarp_all = sops + SM::OPS;
+  // operator fragments stay in global memory: every warp reads the same few KB,
+  // which the L1 cache serves
+  const uint32_t* __restrict__ stc = p.s.tcops;
+  {
+    const float4* src = reinterpret_cast<const float4*>(p.s.ops);
+    float4* dst = reinterpret_cast<float4*>(sops);
+    for (int i = threadIdx.x; i < SM::OPS / 4; i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  float* sw = swarp_all + warp * SM::WARP;
+  float* s_state = sw + SM::STATE;
+  float* s_R = sw + SM::RT;
+  float* s_geo = sw + SM::GEO;
+
+  const Sched& sc = p.sc;
+  const int K = sc.K;
+  const long long k = (*p.s.macro) * (1LL << (sc.L - 1)) + p.j;
+  const float gg = (float)p.ph.g, h0 = (float)p.ph.h0;
+  const size_t fstride = (size_t)K * NPP, bstride = 3 * fstride;
+  double injected = 0.0;
+  const int ntiles = (p.nactive + 31) / 32;
+
+  for (int tile = blockIdx.x * kTcWarps + warp; tile < ntiles; tile += gridDim.x * kTcWarps) {
+    // ---- load: one element per lane into the warp's shared tiles ----
+    const int e = tile * 32 + lane;
+    const bool valid = e < p.nactive;
+    int lev = 1;
+    long long a = 0;
+    {
+      float q[4][NPP];
+      if (valid) {
+        lev = level_of(sc, e);
+        a = k >> (lev - 1);
+        const int src = (int)(a & 1);
+        load_row_global<float, NPP>(p.s.q + src * bstride + 0 * fstride + (size_t)e * NPP, q[0]);
+        load_row_global<float, NPP>(p.s.q + src * bstride + 1 * fstride + (size_t)e * NPP, q[1]);
+        load_row_global<float, NPP>(p.s.q + src * bstride + 2 * fstride + (size_t)e * NPP, q[2]);
+        load_row_global<float, NPP>(p.s.B + (size_t)e * NPP, q[3]);
+        const float4 gv = __ldg(reinterpret_cast<const float4*>(p.s.geo) + e);
+        reinterpret_cast<float4*>(s_geo)[lane] = gv;
+      } else {
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+#pragma unroll
+          for (int i = 0; i < NPP; ++i) q[f][i] = 0.f;
+        reinterpret_cast<float4*>(s_geo)[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        float4* row = reinterpret_cast<float4*>(s_state + (f * 32 + lane) * KP);
+#pragma unroll
+        for (int i4 = 0; i4 < KP / 4; ++i4) {
+          const int i = 4 * i4;
+          row[i4] = make_float4(i < NPP ? q[f][i] : 0.f, i + 1 < NPP ? q[f][i + 1] : 0.f,
+                                i + 2 < NPP ? q[f][i + 2] : 0.f, i + 3 < NPP ? q[f][i + 3] : 0.f);
+        }
+      }
+    }
+    __syncwarp();
+
+    // ---- volume term on tensor cores, one m-tile of 16 elements at a time ----
+#pragma unroll 1
+    for (int mt = 0; mt < 2; ++mt) {
+      const int r0 = 16 * mt + g, r1 = r0 + 8;
+      // state A fragments (rows r0, r1; nodes 16ks + {2t, 2t+1, 2t+8, 2t+9}), hi and lo
+      uint32_t ah[4][KSTEP][4], al[4][KSTEP][4];
+#pragma unroll
+      for (int f = 0; f < 4; ++f)
+#pragma unroll
+        for (int ks = 0; ks < KSTEP; ++ks) {
+          const float* s0 = s_state + (f * 32 + r0) * KP + 16 * ks;
+          const float* s1 = s_state + (f * 32 + r1) * KP + 16 * ks;
+          const float2 v00 = *reinterpret_cast<const float2*>(s0 + 2 * t);
+          const float2 v10 = *reinterpret_cast<const float2*>(s1 + 2 * t);
+          const float2 v01 = *reinterpret_cast<const float2*>(s0 + 2 * t + 8);
+          const float2 v11 = *reinterpret_cast<const float2*>(s1 + 2 * t + 8);
+          split2(v00.x, v00.y, ah[f][ks][0], al[f][ks][0]);
+          split2(v10.x, v10.y, ah[f][ks][1], al[f][ks][1]);
+          split2(v01.x, v01.y, ah[f][ks][2], al[f][ks][2]);
+          split2(v11.x, v11.y, ah[f][ks][3], al[f][ks][3]);
+        }
+      const float4 ge0 = reinterpret_cast<const float4*>(s_geo)[r0];
+      const float4 ge1 = reinterpret_cast<const float4*>(s_geo)[r1];
+      float Racc[3][NT][4];
+#pragma unroll
+      for (int f = 0; f < 3; ++f)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) Racc[f][nt][c] = 0.f;
+
+#pragma unroll 1
+      for (int ct = 0; ct < CT; ++ct) {
+        // interpolation: acc[0..3] = (eta, hu, hv, B) * Ic, acc[4] = B * Icr, acc[5] = B * Ics
+        float acc[6][4];
+#pragma unroll
+        for (int o = 0; o < 6; ++o)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[o][c] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < KSTEP; ++ks) {
+#pragma unroll
+          for (int op = 0; op < 3; ++op) {
+            const uint32_t* fb = stc + TL::INTERP + (((op * CT + ct) * KSTEP + ks) * 2) * 64 + lane * 2;
+            const uint2 bh = __ldg(reinterpret_cast<const uint2*>(fb));
+            const uint2 bl = __ldg(reinterpret_cast<const uint2*>(fb + 64));
+            if (op == 0) {
+#pragma unroll
+              for (int f = 0; f < 4; ++f) {
+                mma_k16(acc[f], al[f][ks], bh.x, bh.y);
+                mma_k16(acc[f], ah[f][ks], bl.x, bl.y);
+                mma_k16(acc[f], ah[f][ks], bh.x, bh.y);
+              }
+            } else {
+              mma_k16(acc[3 + op], al[3][ks], bh.x, bh.y);
+              mma_k16(acc[3 + op], ah[3][ks], bl.x, bl.y);
+              mma_k16(acc[3 + op], ah[3][ks], bh.x, bh.y);
+            }
+          }
+        }
+        // flux and source at the lane's four points: (r0, 2t), (r0, 2t+1), (r1, 2t), (r1, 2t+1)
+        float fl[8][4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float4 ge = c < 2 ? ge0 : ge1;
+          const float rx = ge.x, ry = ge.y, sx = ge.z, sy = ge.w;
+          const float ec = acc[0][c], huc = acc[1][c], hvc = acc[2][c], bc = acc[3][c];
+          const float brc = acc[4][c], bsc = acc[5][c];
+          const float hc = ec - bc;
+          const float ih = hc > h0 ? recip(hc) : 0.f;
+          const float u = huc * ih, v = hvc * ih;
+          const float pr = 0.5f * gg * ec * (hc - bc);
+          const float F0 = huc, F1 = huc * u + pr, F2 = huc * v;
+          const float G0 = hvc, G1 = hvc * u, G2 = hvc * v + pr;
+          fl[0][c] = rx * F0 + ry * G0;
+          fl[1][c] = rx * F1 + ry * G1;
+          fl[2][c] = rx * F2 + ry * G2;
+          fl[3][c] = sx * F0 + sy * G0;
+          fl[4][c] = sx * F1 + sy * G1;
+          fl[5][c] = sx * F2 + sy * G2;
+          const float Bx = rx * brc + sx * bsc, By = ry * brc + sy * bsc;
+          fl[6][c] = -gg * ec * Bx;
+          fl[7][c] = -gg * ec * By;
+        }
+        // A fragments (m16n8k8): reg0 = row r0 (points 2t, 2t+1), reg1 = row r1
+        uint32_t fh[8][2], flo[8][2];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          split2(fl[q][0], fl[q][1], fh[q][0], flo[q][0]);
+          split2(fl[q][2], fl[q][3], fh[q][1], flo[q][1]);
+        }
+        // projection: R_h += cF1_h Pr + cF2_h Ps; R_m += cF1_m Pr + cF2_m Ps + cS_m P
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          uint32_t bh[3], bl[3];
+#pragma unroll
+          for (int op = 0; op < 3; ++op) {
+            const uint32_t* fb = stc + TL::PROJ + (((op * CT + ct) * NT + nt) * 2) * 32 + lane;
+            bh[op] = __ldg(fb);
+            bl[op] = __ldg(fb + 32);
+          }
+#pragma unroll
+          for (int f = 0; f < 3; ++f) {
+            // cF1 (quantity f) with Pr, cF2 (3+f) with Ps, source (5+f, f>0) with P
+            mma_k8(Racc[f][nt], flo[f][0], flo[f][1], bh[0]);
+            mma_k8(Racc[f][nt], fh[f][0], fh[f][1], bl[0]);
+            mma_k8(Racc[f][nt], fh[f][0], fh[f][1], bh[0]);
+            mma_k8(Racc[f][nt], flo[3 + f][0], flo[3 + f][1], bh[1]);
+            mma_k8(Racc[f][nt], fh[3 + f][0], fh[3 + f][1], bl[1]);
+            mma_k8(Racc[f][nt], fh[3 + f][0], fh[3 + f][1], bh[1]);
+            if (f > 0) {
+              mma_k8(Racc[f][nt], flo[5 + f][0], flo[5 + f][1], bh[2]);
+              mma_k8(Racc[f][nt], fh[5 + f][0], fh[5 + f][1], bl[2]);
+              mma_k8(Racc[f][nt], fh[5 + f][0], fh[5 + f][1], bh[2]);
+            }
+          }
+        }
+      }
+      // R of this m-tile to shared memory: rows r0, r1, nodes 8nt + {2t, 2t+1}
+#pragma unroll
+      for (int f = 0; f < 3; ++f)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          *reinterpret_cast<float2*>(s_R + (f * 32 + r0) * C::NPT + 8 * nt + 2 * t) =
+              make_float2(Racc[f][nt][0], Racc[f][nt][1]);
+          *reinterpret_cast<float2*>(s_R + (f * 32 + r1) * C::NPT + 8 * nt + 2 * t) =
+              make_float2(Racc[f][nt][2], Racc[f][nt][3]);
+        }
+    }
+    __syncwarp();
+
+    // ---- one thread per element: surface term, commit, positivity ----
+    if (valid) {
+      float R0[NP], R1[NP], R2[NP];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        R0[i] = s_R[(0 * 32 + lane) * C::NPT + i];
+        R1[i] = s_R[(1 * 32 + lane) * C::NPT + i];
+        R2[i] = s_R[(2 * 32 + lane) * C::NPT + i];
+      }
+      const float4 ge = reinterpret_cast<const float4*>(s_geo)[lane];
+      // the per-element operators were staged at the start of shared memory with the
+      // OpLayout offsets, so the shared epilogue indexes them directly; the own
+      // state is read from the warp's shared tile when the surface term needs it
+      const float* my = s_state + lane * KP;
+      auto own = [&](int f, int jn) -> float { return my[f * 32 * KP + jn]; };
+      surface_lift<float, N>(p, sops, e, k, own, ge.x, ge.y, ge.z, ge.w, R0, R1, R2);
+      float eta[NPP], hu[NPP], hv[NPP], bb[NPP];
+      load_row<float, NPP>(my + 0 * 32 * KP, eta);
+      load_row<float, NPP>(my + 1 * 32 * KP, hu);
+      load_row<float, NPP>(my + 2 * 32 * KP, hv);
+      load_row<float, NPP>(my + 3 * 32 * KP, bb);
+      commit_and_limit<float, N>(p, sops, e, lev, a, eta, hu, hv, bb, ge.x, ge.y, ge.z, ge.w, R0, R1, R2,
+                                 &injected);
+    }
+    __syncwarp();
+  }
+  if (injected != 0.0) atomicAdd(p.s.acc, injected);
+}
+
+}  // namespace swe

@@ -13,12 +13,14 @@ namespace swe {
 struct KernelCfg {
   int smem_bytes = 0;
   int grid_stage = 0, grid_pos = 0, grid_tvb = 0, grid_stats = 0;
+  int smem_tc = 0, grid_tc = 0;   // tensor-core stage kernel (FP32 only)
 };
 
 template <typename T>
 struct Launchers {
   cudaError_t (*prepare)(KernelCfg*);
   cudaError_t (*stage)(const StageParams<T>&, const KernelCfg&, cudaStream_t);
+  cudaError_t (*stage_tc)(const StageParams<T>&, const KernelCfg&, cudaStream_t);  // nullptr for FP64
   cudaError_t (*positivity)(const LimitParams<T>&, const KernelCfg&, cudaStream_t);
   cudaError_t (*tvb)(const LimitParams<T>&, const KernelCfg&, cudaStream_t);
   cudaError_t (*stats)(const DevState<T>&, const Sched&, int nblocks, double* partials,

@@ -45,9 +45,11 @@ int npp_of(int N) {
 }
 
 struct Layout {
-  size_t q, ring, B, geo, conn, tvbg, means, dry, Bbar, ops, perm, acc, flags, macro, partials, total;
+  size_t q, ring, B, geo, conn, tvbg, means, dry, Bbar, ops, tcops, perm, acc, flags, macro, partials, total;
   int nb_stats;
 };
+
+int tc_size_of(int N);
 
 Layout make_layout(int K, int N, size_t ts, int op_size) {
   Layout L;
@@ -68,6 +70,7 @@ Layout make_layout(int K, int N, size_t ts, int op_size) {
   L.dry = take((size_t)K);
   L.Bbar = take((size_t)K * 8);
   L.ops = take((size_t)op_size * ts);
+  L.tcops = take((size_t)tc_size_of(N) * 4);
   L.perm = take((size_t)K * 4);
   L.acc = take(8 * 8);
   L.flags = take(4 * 4);
@@ -81,8 +84,8 @@ Layout make_layout(int K, int N, size_t ts, int op_size) {
 int check_params(const swe_params* p) {
   if (!p) return fail(SWE_EINVAL, "params is NULL");
   if (p->N < 2 || p->N > 5) return fail(SWE_EUNSUPPORTED, "this build supports N = 2..5");
-  if (p->precision != SWE_FP64 && p->precision != SWE_FP32)
-    return fail(SWE_EUNSUPPORTED, "precision must be SWE_FP64 or SWE_FP32");
+  if (p->precision != SWE_FP64 && p->precision != SWE_FP32 && p->precision != SWE_FP32_TC)
+    return fail(SWE_EUNSUPPORTED, "precision must be SWE_FP64, SWE_FP32 or SWE_FP32_TC");
   if (!(p->g > 0) || !(p->h0 > 0) || !(p->cfl > 0)) return fail(SWE_EINVAL, "g, h0 and cfl must be > 0");
   if (p->nlevels_max < 1 || p->nlevels_max > swe::kMaxLevels)
     return fail(SWE_EINVAL, "nlevels_max must be in 1..8");
@@ -103,6 +106,7 @@ struct swe_solver {
   swe::RefElem ref;
   int N = 0, K = 0, Np = 0, NPP = 0;
   bool fp64 = false;
+  bool tc = false;   // FP32 with tensor-core volume contractions
   size_t ts = 4;
   cudaStream_t stream = nullptr;
   char* ws = nullptr;
@@ -146,6 +150,7 @@ swe::DevState<T> dev_state(swe_solver* s) {
   d.dry = reinterpret_cast<uint8_t*>(w + s->lay.dry);
   d.Bbar = reinterpret_cast<const double*>(w + s->lay.Bbar);
   d.ops = reinterpret_cast<const T*>(w + s->lay.ops);
+  d.tcops = reinterpret_cast<const uint32_t*>(w + s->lay.tcops);
   d.acc = reinterpret_cast<double*>(w + s->lay.acc);
   d.flags = reinterpret_cast<int*>(w + s->lay.flags);
   d.macro = reinterpret_cast<long long*>(w + s->lay.macro);
@@ -160,6 +165,10 @@ swe::Sched sched_of(const swe_solver* s) {
   for (int l = 0; l <= s->L; ++l) sc.off[l] = s->off[l];
   for (int l = s->L + 1; l <= swe::kMaxLevels; ++l) sc.off[l] = s->K;
   sc.dt_min = s->dt_min;
+  for (int l = 1; l <= swe::kMaxLevels; ++l) {
+    sc.dtl_d[l - 1] = s->dt_min * (double)(1LL << (l - 1));
+    sc.dtl_f[l - 1] = (float)sc.dtl_d[l - 1];
+  }
   return sc;
 }
 
@@ -168,6 +177,7 @@ swe::Phys phys_of(const swe_solver* s, int mask) {
   ph.g = s->prm.g;
   ph.h0 = s->prm.h0;
   ph.eps = s->prm.eps > 0 ? s->prm.eps : s->prm.h0;
+  ph.eps_f = (float)ph.eps;
   ph.tvb_M = s->prm.tvb_M;
   ph.tvb_nu = s->prm.tvb_nu > 0 ? s->prm.tvb_nu : 1.5;
   ph.pp = (mask & SWE_LIM_PP) ? 1 : 0;
@@ -187,42 +197,130 @@ std::vector<T> to_t(const std::vector<double>& v) {
   return o;
 }
 
-template <typename T>
-int upload_ops_t(swe_solver* s) {
-  const swe::RefElem& e = s->ref;
-  const int np = e.Np, npp = s->NPP, nc = e.Ncub, ng = e.Ng, nfp = e.Nfp;
-  const int nfpp = (nfp + 3) / 4 * 4;
-  const int opsz = s->fp64 ? s->ld->op_size : s->lf->op_size;
-  std::vector<double> o(opsz, 0.0);
-  size_t p = 0;
-  auto put_rows = [&](const std::vector<double>& M, int rows, int cols, bool transpose_src) {
+// bf16 round-to-nearest-even of a float (host), and its value
+uint16_t bf16_bits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+float bf16_value(uint16_t b) {
+  uint32_t u = (uint32_t)b << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+// hi/lo bf16 split of a single-precision operator entry
+void bf16_split(double v, uint16_t& hi, uint16_t& lo) {
+  const float vf = (float)v;
+  hi = bf16_bits(vf);
+  lo = bf16_bits(vf - bf16_value(hi));
+}
+
+// Pack the FP64 reference operators into the kernels' operator block (OpLayout)
+// and the tensor-core fragment block (TcLayout).
+template <int N>
+void pack_ops_n(const swe::RefElem& e, std::vector<double>& o, std::vector<uint32_t>& tc) {
+  using O = swe::OpLayout<N>;
+  using D = swe::Dims<N>;
+  using C = swe::TcDims<N>;
+  using TL = swe::TcLayout<N>;
+  const int np = e.Np, nc = e.Ncub, ng = e.Ng, nfp = e.Nfp, npp = D::NPP, nfpp = D::NFPP;
+  o.assign(O::SIZE, 0.0);
+  auto put_rows = [&](int off, const std::vector<double>& M, int rows, int cols, bool transpose_src) {
     // destination [rows][npp]; source M is rows x cols (or cols x rows if transposed)
     for (int r = 0; r < rows; ++r)
       for (int c = 0; c < cols; ++c)
-        o[p + (size_t)r * npp + c] = transpose_src ? M[(size_t)c * rows + r] : M[(size_t)r * cols + c];
-    p += (size_t)rows * npp;
+        o[off + (size_t)r * npp + c] = transpose_src ? M[(size_t)c * rows + r] : M[(size_t)r * cols + c];
   };
-  put_rows(e.Ic, nc, np, false);
-  put_rows(e.Icr, nc, np, false);
-  put_rows(e.Ics, nc, np, false);
-  put_rows(e.Pr, nc, np, true);   // Pr is np x nc -> rows c
-  put_rows(e.Ps, nc, np, true);
-  put_rows(e.P, nc, np, true);
-  put_rows(e.Lg, 3 * ng, np, true);  // Lg is np x 3ng
+  put_rows(O::LGT, e.Lg, 3 * ng, np, true);  // Lg is np x 3ng
   for (int g = 0; g < ng; ++g)
-    for (int m = 0; m < nfp; ++m) o[p + (size_t)g * nfpp + m] = e.I1d[(size_t)g * nfp + m];
-  p += (size_t)ng * nfpp;
-  for (int j = 0; j < np; ++j) o[p + j] = e.mean_w[j];
-  p += npp;
+    for (int m = 0; m < nfp; ++m) o[O::I1D + (size_t)g * nfpp + m] = e.I1d[(size_t)g * nfp + m];
+  for (int j = 0; j < np; ++j) o[O::MW + j] = e.mean_w[j];
   for (int v = 0; v < 3; ++v)
-    for (int j = 0; j < np; ++j) o[p + (size_t)v * npp + j] = e.T1[(size_t)v * np + j];
-  p += 3 * (size_t)npp;
+    for (int j = 0; j < np; ++j) o[O::T1 + (size_t)v * npp + j] = e.T1[(size_t)v * np + j];
   for (int j = 0; j < np; ++j)
-    for (int v = 0; v < 3; ++v) o[p + (size_t)j * 4 + v] = e.bary[(size_t)j * 3 + v];
-  p += 4 * (size_t)npp;
-  if ((int)p != opsz) return fail(SWE_EINVAL, "internal: operator block size mismatch");
+    for (int v = 0; v < 3; ++v) o[O::BARY + (size_t)j * 4 + v] = e.bary[(size_t)j * 3 + v];
+  put_rows(O::IC, e.Ic, nc, np, false);
+  put_rows(O::ICR, e.Icr, nc, np, false);
+  put_rows(O::ICS, e.Ics, nc, np, false);
+  put_rows(O::PRT, e.Pr, nc, np, true);  // Pr is np x nc -> rows c
+  put_rows(O::PST, e.Ps, nc, np, true);
+  put_rows(O::PT, e.P, nc, np, true);
+
+  // tensor-core fragments (mma.sync m16n8k16 / m16n8k8 bf16 B operands)
+  tc.assign(TL::SIZE, 0u);
+  const std::vector<double>* interp[3] = {&e.Ic, &e.Icr, &e.Ics};   // nc x np
+  const std::vector<double>* proj[3] = {&e.Pr, &e.Ps, &e.P};        // np x nc
+  auto pack2 = [](uint16_t lo16, uint16_t hi16) { return (uint32_t)lo16 | ((uint32_t)hi16 << 16); };
+  for (int op = 0; op < 3; ++op)
+    for (int ct = 0; ct < C::CT; ++ct)
+      for (int ks = 0; ks < C::KSTEP; ++ks)
+        for (int lane = 0; lane < 32; ++lane) {
+          const int g = lane / 4, t = lane % 4;
+          // B[k][n] = Op[c = 8ct + n][j = 16ks + k]
+          auto Bv = [&](int kk, int nn) {
+            const int c = 8 * ct + nn, j = 16 * ks + kk;
+            return (c < nc && j < np) ? (*interp[op])[(size_t)c * np + j] : 0.0;
+          };
+          const int kk[4] = {2 * t, 2 * t + 1, 2 * t + 8, 2 * t + 9};
+          uint16_t h[4], l[4];
+          for (int q = 0; q < 4; ++q) bf16_split(Bv(kk[q], g), h[q], l[q]);
+          const size_t base = (((size_t)(op * C::CT + ct) * C::KSTEP + ks) * 2) * 64;
+          tc[TL::INTERP + base + 0 * 64 + lane * 2 + 0] = pack2(h[0], h[1]);
+          tc[TL::INTERP + base + 0 * 64 + lane * 2 + 1] = pack2(h[2], h[3]);
+          tc[TL::INTERP + base + 1 * 64 + lane * 2 + 0] = pack2(l[0], l[1]);
+          tc[TL::INTERP + base + 1 * 64 + lane * 2 + 1] = pack2(l[2], l[3]);
+        }
+  for (int op = 0; op < 3; ++op)
+    for (int ct = 0; ct < C::CT; ++ct)
+      for (int nt = 0; nt < C::NT; ++nt)
+        for (int lane = 0; lane < 32; ++lane) {
+          const int g = lane / 4, t = lane % 4;
+          // B[k][n] = Op[i = 8nt + n][c = 8ct + k]
+          auto Bv = [&](int kk, int nn) {
+            const int i = 8 * nt + nn, c = 8 * ct + kk;
+            return (i < np && c < nc) ? (*proj[op])[(size_t)i * nc + c] : 0.0;
+          };
+          uint16_t h0, l0, h1, l1;
+          bf16_split(Bv(2 * t, g), h0, l0);
+          bf16_split(Bv(2 * t + 1, g), h1, l1);
+          const size_t base = (((size_t)(op * C::CT + ct) * C::NT + nt) * 2) * 32;
+          tc[TL::PROJ + base + 0 * 32 + lane] = pack2(h0, h1);
+          tc[TL::PROJ + base + 1 * 32 + lane] = pack2(l0, l1);
+        }
+}
+
+void pack_ops(int N, const swe::RefElem& e, std::vector<double>& o, std::vector<uint32_t>& tc) {
+  switch (N) {
+    case 2: pack_ops_n<2>(e, o, tc); break;
+    case 3: pack_ops_n<3>(e, o, tc); break;
+    case 4: pack_ops_n<4>(e, o, tc); break;
+    case 5: pack_ops_n<5>(e, o, tc); break;
+    default: break;
+  }
+}
+
+int tc_size_of(int N) {
+  switch (N) {
+    case 2: return swe::TcLayout<2>::SIZE;
+    case 3: return swe::TcLayout<3>::SIZE;
+    case 4: return swe::TcLayout<4>::SIZE;
+    case 5: return swe::TcLayout<5>::SIZE;
+    default: return 0;
+  }
+}
+
+template <typename T>
+int upload_ops_t(swe_solver* s) {
+  std::vector<double> o;
+  std::vector<uint32_t> tc;
+  pack_ops(s->N, s->ref, o, tc);
+  const int opsz = s->fp64 ? s->ld->op_size : s->lf->op_size;
+  if ((int)o.size() != opsz) return fail(SWE_EINVAL, "internal: operator block size mismatch");
   std::vector<T> ot = to_t<T>(o);
   int rc = upload(s, s->lay.ops, ot.data(), ot.size() * sizeof(T));
+  if (rc) return rc;
+  rc = upload(s, s->lay.tcops, tc.data(), tc.size() * sizeof(uint32_t));
   if (rc) return rc;
   SWE_CUDA(cudaStreamSynchronize(s->stream));
   return SWE_OK;
@@ -416,7 +514,11 @@ int enqueue_substep_t(swe_solver* s, int j, KernelTimer* tm = nullptr) {
   p.perm = nullptr;
   int rc;
   if ((rc = timer_mark(s, tm, true, 0, nactive))) return rc;
-  SWE_CUDA(lt->stage(p, s->cfg, s->stream));
+  if (s->tc) {
+    SWE_CUDA(lt->stage_tc(p, s->cfg, s->stream));
+  } else {
+    SWE_CUDA(lt->stage(p, s->cfg, s->stream));
+  }
   if ((rc = timer_mark(s, tm, false, 0, 0))) return rc;
   int nl = 1;
   if (s->prm.limiter_mask & SWE_LIM_TVB) {
@@ -708,6 +810,7 @@ int swe_solver_create(const swe_mesh* mesh, const swe_params* params, void* dev_
   s->Np = s->ref.Np;
   s->NPP = npp_of(s->N);
   s->fp64 = params->precision == SWE_FP64;
+  s->tc = params->precision == SWE_FP32_TC;
   s->ts = s->fp64 ? 8 : 4;
   s->stream = reinterpret_cast<cudaStream_t>(stream);
   s->ws = reinterpret_cast<char*>(dev_workspace);
@@ -831,7 +934,11 @@ int swe_rhs(swe_solver* s, void* dev_R) {
     p.mode = 1;
     p.out = reinterpret_cast<float*>(dev_R);
     p.perm = reinterpret_cast<const int*>(s->ws + s->lay.perm);
-    SWE_CUDA(s->lf->stage(p, s->cfg, s->stream));
+    if (s->tc) {
+      SWE_CUDA(s->lf->stage_tc(p, s->cfg, s->stream));
+    } else {
+      SWE_CUDA(s->lf->stage(p, s->cfg, s->stream));
+    }
   }
   s->launches++;
   return SWE_OK;

@@ -20,6 +20,8 @@ def _prec_code(precision):
         return nat.SWE_FP64
     if p in ("fp32", "f32", "float"):
         return nat.SWE_FP32
+    if p in ("fp32tc", "fp32_tc", "tc", "bf16x3"):
+        return nat.SWE_FP32_TC
     raise ValueError(f"unknown precision {precision!r}")
 
 
