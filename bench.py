@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--batch-scenarios", type=int, default=64)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
     return ap.parse_args()
 
 
@@ -336,6 +340,13 @@ def run_ours(args):
                               "fp32_speedup": value / (d64 / (ms64 / 1e3))}
         del s64
 
+    # batched ensemble: uneven scenarios advanced by one graph launch per macro step
+    if rank == 0 and not args.no_batch:
+        result["batched"] = run_batched(args)
+    # served stream: Poisson arrivals, continuous batching under an HBM budget
+    if rank == 0 and not args.no_serve:
+        result["served"] = run_served(args)
+
     if rank == 0 and not args.no_cpu_baseline:
         v, dt, Ks, _ = oracle_sample(args, 1, 400, 100)
         cores, model = cpu_info()
@@ -347,6 +358,56 @@ def run_ours(args):
         print(json.dumps(result), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def run_batched(args, steps=5):
+    import torch
+    import paper_1403_1661_gb300 as P
+    from workloads import scenarios as sc
+    scns = sc.ensemble(n=args.batch_scenarios)
+    tuned = {N: P.tune(N, args.precision) for N in sorted({s.N for s in scns})}
+    solvers = []
+    for s in scns:
+        so = P.solver_from_scenario(s, precision=args.precision)
+        so.set_launch_config(tuned[s.N])
+        solvers.append(so)
+    b = P.Batch(solvers)
+    b.step(1)
+    torch.cuda.synchronize()
+    d0 = sum(so.stats()["dof_updates"] for so in solvers)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    b.step(steps)
+    e1.record(b.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    dofs = sum(so.stats()["dof_updates"] for so in solvers) - d0
+    out = {"value": dofs / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "scenarios": len(scns),
+           "triangles": int(sum(so.K for so in solvers)), "orders": sorted({s.N for s in scns}),
+           "autotuned_ctas_per_sm": {str(k): v for k, v in tuned.items()},
+           "step": "one graph launch = one macro step of every scenario (parallel graph branches)"}
+    b.close()
+    for so in solvers:
+        so.close()
+    return out
+
+
+def run_served(args):
+    import torch
+    from paper_1403_1661_gb300.serve import GpuFactory, Server, requests_from_stream
+    from workloads import scenarios as sc
+    stream = sc.served_stream(duration=args.serve_seconds)
+    reqs = requests_from_stream(stream, substeps=500)
+    srv = Server(budget_bytes=150e9, max_slots=64, macro_per_round=4, prep_workers=8,
+                 factory=GpuFactory(args.precision))
+    out = srv.run(reqs)
+    torch.cuda.synchronize()
+    return {"requests": out["requests"], "p50_s": out["p50_s"], "p99_s": out["p99_s"], "mean_s": out["mean_s"],
+            "aggregate_dof_per_s": out["aggregate_dof_per_s"], "wall_s": out["wall_s"],
+            "peak_running": out["peak_running"], "peak_gb": out["peak_bytes"] / 1e9,
+            "arrivals": f"Poisson 50/s for {args.serve_seconds:.0f} s, K log-uniform 2k-1M, N in {{2,3,4}}, "
+                        f"500 MRAB substeps each, HBM budget 150 GB"}
 
 
 def main():

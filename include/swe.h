@@ -196,6 +196,24 @@ int swe_set_full_state(swe_solver* solver, const void* host_buf, size_t bytes);
 /* Levels in use (L), elements per level (counts[0..L-1]) and dt_min. */
 int swe_level_info(const swe_solver* solver, int32_t* L, int32_t* counts, double* dt_min);
 
+/* ---- batched scenarios -------------------------------------------------- */
+typedef struct swe_batch swe_batch;
+
+/* Group n solvers (each on its own CUDA stream, level-synchronous) so that one
+ * graph launch on `stream` advances every one of them by one of its own macro
+ * steps: the graph holds each solver's substep kernels as a parallel branch, so
+ * uneven scenarios overlap on the GPU. The solvers stay usable on their own;
+ * work issued on their streams is ordered after a batch step. */
+int swe_batch_create(swe_solver* const* solvers, int32_t n, void* stream, swe_batch** out);
+/* n_macro graph launches (each advances every solver by one macro step). */
+int swe_batch_step(swe_batch* batch, int32_t n_macro);
+void swe_batch_destroy(swe_batch* batch);
+
+/* Launch shape of the stage and limiter kernels: at most ctas_per_sm CTAs per
+ * SM in their grid-stride loops (0 = as many as fit). Used by the autotuner;
+ * results do not depend on it. */
+int swe_set_launch_config(swe_solver* solver, int32_t ctas_per_sm);
+
 /* Advance n finest substeps like swe_substep, timing every kernel launch with CUDA
  * events on the solver's stream (synchronises at the end). out[0..5]: total ms of
  * the stage kernels (R + commit + positivity), of the TVB kernels, of the other

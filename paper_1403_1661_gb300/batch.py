@@ -1,0 +1,105 @@
+"""Batched scenarios (one graph launch advances many solvers) and the launch-shape
+autotuner. Argument marshalling only: the work runs in the native library."""
+from __future__ import annotations
+
+import ctypes as C
+import json
+import os
+import time
+
+import numpy as np
+
+from . import _native as nat
+from .build import BUILD
+
+
+class Batch:
+    """Many independent solvers advanced by one CUDA-graph launch per macro step."""
+
+    def __init__(self, solvers, stream=None):
+        import torch
+        self.solvers = list(solvers)
+        if not self.solvers:
+            raise ValueError("empty batch")
+        dev = self.solvers[0].device
+        with torch.cuda.device(dev):
+            self.stream = torch.cuda.Stream(dev) if stream is None else stream
+        handles = (C.c_void_p * len(self.solvers))(*[s.handle.value for s in self.solvers])
+        h = C.c_void_p()
+        with torch.cuda.device(dev):
+            nat.check(nat.lib().swe_batch_create(handles, len(self.solvers), C.c_void_p(self.stream.cuda_stream),
+                                                 C.byref(h)), "swe_batch_create")
+        self.handle = h
+
+    def step(self, n_macro=1):
+        nat.check(nat.lib().swe_batch_step(self.handle, int(n_macro)), "swe_batch_step")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            nat.lib().swe_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# autotuner: CTAs per SM of the grid-stride kernels, per (order, precision, GPU)
+
+CACHE = os.path.join(BUILD, "autotune.json")
+CANDIDATES = (1, 2, 3, 4, 0)
+
+
+def _gpu_key():
+    import torch
+    return torch.cuda.get_device_name().replace(" ", "_")
+
+
+def _load_cache():
+    try:
+        return json.load(open(CACHE))
+    except Exception:
+        return {}
+
+
+def tune(N, precision, candidates=CANDIDATES, reps=3, force=False, verbose=False):
+    """Time one macro step of a seeded sample problem of order N for every
+    candidate launch shape; cache and return the fastest (ctas_per_sm, 0 = max)."""
+    import torch
+    from workloads import scenarios as sc
+    from .solver import solver_from_scenario
+    key = f"{_gpu_key()}/N{N}/{precision}"
+    cache = _load_cache()
+    if key in cache and not force:
+        return cache[key]["ctas_per_sm"]
+    s = solver_from_scenario(sc.tsunami(nx=240, ny=60, N=N, nlevels=4), precision=precision)
+    timings = {}
+    for c in candidates:
+        s.set_launch_config(c)
+        s.step(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.step(reps)
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        timings[c] = e0.elapsed_time(e1) / reps
+    best = min(timings, key=timings.get)
+    cache[key] = {"ctas_per_sm": best, "ms_per_macro_step": timings, "when": time.time()}
+    os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+    json.dump(cache, open(CACHE, "w"), indent=1, default=str)
+    if verbose:
+        print(f"autotune {key}: {timings} -> {best}")
+    s.close()
+    return best
+
+
+def apply_tuning(solver, precision):
+    """Set the cached (or freshly tuned) launch shape on a solver."""
+    best = tune(solver.N, precision)
+    solver.set_launch_config(best)
+    return best

@@ -132,6 +132,17 @@ struct swe_solver {
   cudaGraphExec_t graph = nullptr;
   int graph_launches = 0;
   int64_t graph_dofs = 0;
+  swe::KernelCfg cfg_max;   // occupancy limits (set_launch_config caps below these)
+};
+
+struct swe_batch {
+  std::vector<swe_solver*> solvers;
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  cudaEvent_t fork = nullptr, done = nullptr;
+  std::vector<cudaEvent_t> join;
+  std::vector<int> launches;
+  std::vector<int64_t> dofs;
 };
 
 namespace {
@@ -826,6 +837,7 @@ int swe_solver_create(const swe_mesh* mesh, const swe_params* params, void* dev_
   if (bytes < s->lay.total) return fail(SWE_ENOMEM, "workspace smaller than swe_workspace_bytes()");
   cudaError_t ce = s->fp64 ? s->ld->prepare(&s->cfg) : s->lf->prepare(&s->cfg);
   if (ce != cudaSuccess) return fail(SWE_ECUDA, std::string("kernel setup: ") + cudaGetErrorString(ce));
+  s->cfg_max = s->cfg;
   // single level until levels are set up
   s->level.assign(s->K, 1);
   s->dt_min = 0.0;
@@ -1130,6 +1142,111 @@ int swe_level_info(const swe_solver* s, int32_t* L, int32_t* counts, double* dt_
     for (int l = 1; l <= s->L; ++l) counts[l - 1] = s->off[l] - s->off[l - 1];
   if (dt_min) *dt_min = s->dt_min;
   return SWE_OK;
+}
+
+int swe_set_launch_config(swe_solver* s, int32_t ctas_per_sm) {
+  if (!s || ctas_per_sm < 0) return fail(SWE_EINVAL, "bad arguments");
+  int dev = 0, nsm = 0;
+  SWE_CUDA(cudaGetDevice(&dev));
+  SWE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  auto cap = [&](int maxgrid) {
+    if (ctas_per_sm == 0) return maxgrid;
+    const int g = nsm * ctas_per_sm;
+    return g < maxgrid ? g : maxgrid;
+  };
+  s->cfg.grid_stage = cap(s->cfg_max.grid_stage);
+  s->cfg.grid_tc = cap(s->cfg_max.grid_tc);
+  s->cfg.grid_tvb = cap(s->cfg_max.grid_tvb);
+  s->cfg.grid_pos = cap(s->cfg_max.grid_pos);
+  invalidate_graph(s);
+  return SWE_OK;
+}
+
+int swe_batch_create(swe_solver* const* solvers, int32_t n, void* stream, swe_batch** out) {
+  if (!solvers || n < 1 || !out) return fail(SWE_EINVAL, "bad arguments");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    swe_solver* s = solvers[i];
+    if (!s || !s->have_state || !(s->dt_min > 0)) return fail(SWE_EINVAL, "every solver needs state and levels");
+    if (!synchronous(s)) return fail(SWE_EINVAL, "every solver must be level-synchronous");
+    if (!s->stream) return fail(SWE_EINVAL, "batched solvers need their own (non-default) streams");
+  }
+  std::unique_ptr<swe_batch> b(new (std::nothrow) swe_batch);
+  if (!b) return fail(SWE_ENOMEM, "host allocation failed");
+  b->solvers.assign(solvers, solvers + n);
+  b->stream = reinterpret_cast<cudaStream_t>(stream);
+  if (!b->stream) return fail(SWE_EINVAL, "the batch needs a non-default stream");
+  SWE_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+  SWE_CUDA(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming));
+  b->join.resize(n, nullptr);
+  for (int i = 0; i < n; ++i) SWE_CUDA(cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming));
+  b->launches.assign(n, 0);
+  b->dofs.assign(n, 0);
+  // one macro step of every solver, each on its own stream: parallel graph branches
+  cudaGraph_t g = nullptr;
+  SWE_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = SWE_OK;
+  cudaError_t ce = cudaEventRecord(b->fork, b->stream);
+  for (int i = 0; i < n && rc == SWE_OK && ce == cudaSuccess; ++i) {
+    swe_solver* s = b->solvers[i];
+    ce = cudaStreamWaitEvent(s->stream, b->fork, 0);
+    const int period = 1 << (s->L - 1);
+    for (int j = 0; j < period && ce == cudaSuccess; ++j) {
+      int nl = enqueue_substep(s, j);
+      if (nl < 0) { rc = nl; break; }
+      b->launches[i] += nl;
+      b->dofs[i] += substep_dofs(s, j);
+    }
+    if (rc == SWE_OK && ce == cudaSuccess) ce = cudaEventRecord(b->join[i], s->stream);
+    if (rc == SWE_OK && ce == cudaSuccess) ce = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+  }
+  cudaError_t ce2 = cudaStreamEndCapture(b->stream, &g);
+  if (rc != SWE_OK) { if (g) cudaGraphDestroy(g); swe_batch_destroy(b.release()); return rc; }
+  if (ce != cudaSuccess || ce2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    swe_batch_destroy(b.release());
+    return fail(SWE_ECUDA, std::string("batch capture: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
+  }
+  ce = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (ce != cudaSuccess) {
+    b->graph = nullptr;
+    swe_batch_destroy(b.release());
+    return fail(SWE_ECUDA, std::string("batch instantiate: ") + cudaGetErrorString(ce));
+  }
+  *out = b.release();
+  return SWE_OK;
+}
+
+int swe_batch_step(swe_batch* b, int32_t n_macro) {
+  if (!b || n_macro < 0) return fail(SWE_EINVAL, "bad arguments");
+  if (n_macro == 0) return SWE_OK;
+  // the batch stream waits for work already queued on the solvers' own streams
+  for (size_t i = 0; i < b->solvers.size(); ++i) {
+    SWE_CUDA(cudaEventRecord(b->join[i], b->solvers[i]->stream));
+    SWE_CUDA(cudaStreamWaitEvent(b->stream, b->join[i], 0));
+  }
+  for (int32_t r = 0; r < n_macro; ++r) SWE_CUDA(cudaGraphLaunch(b->graph, b->stream));
+  SWE_CUDA(cudaEventRecord(b->done, b->stream));
+  for (size_t i = 0; i < b->solvers.size(); ++i) {
+    swe_solver* s = b->solvers[i];
+    SWE_CUDA(cudaStreamWaitEvent(s->stream, b->done, 0));
+    s->k += (int64_t)n_macro << (s->L - 1);
+    s->dof_updates += b->dofs[i] * n_macro;
+    s->launches += (int64_t)b->launches[i] * n_macro;
+  }
+  return SWE_OK;
+}
+
+void swe_batch_destroy(swe_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->done) cudaEventDestroy(b->done);
+  for (cudaEvent_t e : b->join)
+    if (e) cudaEventDestroy(e);
+  delete b;
 }
 
 int swe_profile_substeps(swe_solver* s, int32_t n, double* out) {

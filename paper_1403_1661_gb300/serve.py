@@ -1,0 +1,190 @@
+"""Continuous-batching server for tsunami-scenario solves.
+
+Requests (a scenario and a number of finest MRAB substeps) arrive over time.
+Host-side preparation (mesh, connectivity, nodal inputs, level grouping) runs on
+a thread pool; a request is admitted, first come first served, as soon as its
+device workspace fits in the HBM budget and a slot is free. Every admitted solve
+keeps its state and Adams-Bashforth history resident in its own workspace and
+advances on its own CUDA stream a few macro steps at a time (graph replays), so
+the work of all running requests overlaps on the GPU. Finished requests return
+their state to the host and free their memory immediately, which admits the next
+ones. Latency is completion time minus arrival time.
+
+Solves never interact (no shared buffers, deterministic kernels), so a result
+does not depend on what else is running.
+"""
+from __future__ import annotations
+
+import collections
+import concurrent.futures as cf
+import dataclasses
+import math
+import time
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float                 # seconds after the start of the run
+    scenario: object
+    substeps: int = 500
+    admitted: float | None = None
+    finished: float | None = None
+    dof_updates: int = 0
+    bytes: int = 0
+    result: object = None
+
+
+class GpuFactory:
+    """Builds real solvers (used by the server; tests may pass a fake)."""
+
+    def __init__(self, precision="fp32tc", keep_state=False, tuned=None):
+        self.precision = precision
+        self.keep_state = keep_state
+        self.tuned = tuned or {}
+
+    def prepare(self, req):
+        from .solver import Mesh, scenario_inputs
+        from . import _native as nat
+        import ctypes as C
+        scn = req.scenario
+        vx, vy, E = scn.build_mesh()
+        mesh = Mesh(vx, vy, E)
+        B, h, hu, hv = scenario_inputs(scn, mesh)
+        lev, dtm = mesh.levels(scn.N, h, hu, hv, scn.g, scn.cfl, scn.nlevels)
+        prm = nat.swe_params(scn.g, scn.h0, 0.0, scn.tvb_M, scn.tvb_nu, scn.cfl, scn.N, scn.nlevels,
+                             {"fp64": 0, "fp32": 1, "fp32tc": 2}[self.precision], scn.limiter_mask,
+                             scn.dry_mode, 0)
+        nb = C.c_size_t()
+        nat.check(nat.lib().swe_workspace_bytes(mesh.handle, C.byref(prm), C.byref(nb)), "swe_workspace_bytes")
+        return {"mesh": mesh, "inputs": (B, h, hu, hv), "levels": (lev, dtm), "bytes": int(nb.value) + 256}
+
+    def bytes(self, prepared):
+        return prepared["bytes"]
+
+    def start(self, req, prepared):
+        return _GpuJob(self, req, prepared)
+
+
+class _GpuJob:
+    def __init__(self, factory, req, prepared):
+        import torch
+        from .solver import Solver
+        scn = req.scenario
+        self.factory = factory
+        self.s = Solver(prepared["mesh"], scn.N, g=scn.g, h0=scn.h0, cfl=scn.cfl, nlevels_max=scn.nlevels,
+                        precision=factory.precision, limiter_mask=scn.limiter_mask, tvb_M=scn.tvb_M,
+                        tvb_nu=scn.tvb_nu, dry_mode=scn.dry_mode)
+        if scn.N in factory.tuned:
+            self.s.set_launch_config(factory.tuned[scn.N])
+        B, h, hu, hv = prepared["inputs"]
+        lev, dtm = prepared["levels"]
+        self.s.set_bathymetry(B)
+        self.s.set_levels(lev, dtm)      # before the state: no re-ordering of uploaded data
+        self.s.set_state(h, hu, hv)
+        L = int(np.max(lev))
+        self.macro_period = 2 ** (L - 1)
+        self.event = torch.cuda.Event()
+        self.pending = False
+
+    def step(self, n):
+        self.s.step(n)
+        self.event.record(self.s.stream)
+        self.pending = True
+
+    def idle(self):
+        return (not self.pending) or self.event.query()
+
+    def finish(self):
+        st = self.s.stats()
+        out = self.s.get_state() if self.factory.keep_state else None
+        self.s.close()
+        return out, st["dof_updates"]
+
+
+class Server:
+    def __init__(self, budget_bytes=150e9, max_slots=64, macro_per_round=2, prep_workers=4, factory=None,
+                 clock=time.perf_counter, sleep=time.sleep):
+        self.budget = float(budget_bytes)
+        self.max_slots = int(max_slots)
+        self.macro_per_round = int(macro_per_round)
+        self.prep_workers = int(prep_workers)
+        self.factory = factory if factory is not None else GpuFactory()
+        self.clock = clock
+        self.sleep = sleep
+
+    def run(self, requests):
+        """Serve the requests (sorted by arrival); returns a summary dict."""
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        pending = collections.deque(reqs)
+        preparing = collections.deque()          # (req, future) in arrival order
+        ready = collections.deque()               # (req, prepared), FIFO
+        running = []                              # [req, job, remaining_macro]
+        used = 0.0
+        peak_used = 0.0
+        peak_running = 0
+        done = []
+        t0 = self.clock()
+        with cf.ThreadPoolExecutor(max_workers=self.prep_workers) as pool:
+            while pending or preparing or ready or running:
+                now = self.clock() - t0
+                progressed = False
+                while pending and pending[0].arrival <= now:
+                    r = pending.popleft()
+                    preparing.append((r, pool.submit(self.factory.prepare, r)))
+                    progressed = True
+                while preparing and preparing[0][1].done():
+                    r, fut = preparing.popleft()
+                    prep = fut.result()
+                    r.bytes = self.factory.bytes(prep)
+                    if r.bytes > self.budget:
+                        raise MemoryError(f"request {r.rid} needs {r.bytes} B, over the whole budget")
+                    ready.append((r, prep))
+                    progressed = True
+                # admission: first come first served, by budget and slots
+                while ready and len(running) < self.max_slots and used + ready[0][0].bytes <= self.budget:
+                    r, prep = ready.popleft()
+                    job = self.factory.start(r, prep)
+                    r.admitted = self.clock() - t0
+                    used += r.bytes
+                    peak_used = max(peak_used, used)
+                    running.append([r, job, int(math.ceil(r.substeps / job.macro_period))])
+                    progressed = True
+                peak_running = max(peak_running, len(running))
+                # issue work and retire finished solves
+                still = []
+                for item in running:
+                    r, job, rem = item
+                    if not job.idle():
+                        still.append(item)
+                        continue
+                    if rem > 0:
+                        n = min(rem, self.macro_per_round)
+                        job.step(n)
+                        item[2] = rem - n
+                        still.append(item)
+                        progressed = True
+                    else:
+                        r.result, r.dof_updates = job.finish()
+                        r.finished = self.clock() - t0
+                        used -= r.bytes
+                        done.append(r)
+                        progressed = True
+                running = still
+                if not progressed:
+                    nxt = pending[0].arrival - (self.clock() - t0) if pending else 0.0
+                    self.sleep(max(0.0002, min(nxt, 0.002)))
+        wall = self.clock() - t0
+        lat = np.array([r.finished - r.arrival for r in done]) if done else np.zeros(1)
+        dofs = sum(r.dof_updates for r in done)
+        return {"requests": len(done), "wall_s": wall, "p50_s": float(np.percentile(lat, 50)),
+                "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
+                "aggregate_dof_per_s": dofs / wall if wall > 0 else 0.0, "dof_updates": int(dofs),
+                "peak_running": peak_running, "peak_bytes": peak_used, "done": done}
+
+
+def requests_from_stream(stream, substeps=500):
+    """workloads.scenarios.served_stream() output -> Request list."""
+    return [Request(rid=i, arrival=t, scenario=scn, substeps=substeps) for i, (t, scn) in enumerate(stream)]

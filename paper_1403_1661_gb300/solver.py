@@ -219,6 +219,9 @@ class Solver:
         nat.check(nat.lib().swe_kernel_launches(self.handle, C.byref(n)), "swe_kernel_launches")
         return n.value
 
+    def set_launch_config(self, ctas_per_sm):
+        nat.check(nat.lib().swe_set_launch_config(self.handle, int(ctas_per_sm)), "swe_set_launch_config")
+
     def profile_substeps(self, n):
         """Run n substeps with CUDA events around every kernel; per-kernel totals."""
         out = np.zeros(6)
@@ -243,6 +246,7 @@ class Solver:
         if getattr(self, "handle", None):
             nat.lib().swe_solver_destroy(self.handle)
             self.handle = None
+            self.workspace = None
 
     def __del__(self):
         try:

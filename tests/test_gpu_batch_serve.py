@@ -1,0 +1,74 @@
+"""Batched and served forms on the GPU: a scenario's result is the same alone, in
+a batch graph, and in the server's mix (bit-identical: no cross-scenario
+interaction, deterministic kernels)."""
+import numpy as np
+import pytest
+
+from workloads import scenarios as sc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_1661_gb300 import build
+    build.build()
+
+
+def _mix():
+    return [sc.tsunami(nx=40, ny=10, N=3, nlevels=4, amp=1.5, src=(150e3, 40e3)),
+            sc.tsunami(nx=24, ny=8, N=4, nlevels=3, amp=3.0, src=(100e3, 60e3)),
+            sc.dam_break(nx=40, ny=4, N=3),
+            sc.hump_square(n=12, N=2)]
+
+
+@pytest.mark.parametrize("precision", ["fp32tc", "fp64"])
+def test_batch_graph_equals_solvers_alone(precision):
+    import paper_1403_1661_gb300 as P
+    alone = [P.solver_from_scenario(s, precision=precision) for s in _mix()]
+    mixed = [P.solver_from_scenario(s, precision=precision) for s in _mix()]
+    for s in alone:
+        s.step(3)
+    b = P.Batch(mixed)
+    b.step(3)
+    for a, m in zip(alone, mixed):
+        xa, xm = a.get_state(), m.get_state()
+        for u, v in zip(xa[:3], xm[:3]):
+            assert np.array_equal(u, v)
+        assert xa[3] == xm[3]
+        assert a.stats()["dof_updates"] == m.stats()["dof_updates"]
+    b.close()
+
+
+def test_served_results_equal_alone():
+    import paper_1403_1661_gb300 as P
+    from paper_1403_1661_gb300.serve import GpuFactory, Request, Server
+    scns = _mix()
+    reqs = [Request(rid=i, arrival=0.002 * i, scenario=s, substeps=24) for i, s in enumerate(scns)]
+    srv = Server(budget_bytes=2e9, max_slots=3, macro_per_round=1, factory=GpuFactory("fp32tc", keep_state=True))
+    out = srv.run(reqs)
+    assert out["requests"] == len(scns) and out["p99_s"] >= out["p50_s"] > 0
+    for r in out["done"]:
+        s = P.solver_from_scenario(r.scenario, precision="fp32tc")
+        L = s.level_info()[0]
+        s.step(-(-r.substeps // 2 ** (L - 1)))
+        ref = s.get_state()
+        for u, v in zip(ref[:3], r.result[:3]):
+            assert np.array_equal(u, v)
+
+
+def test_autotuner_and_launch_config_do_not_change_results():
+    import paper_1403_1661_gb300 as P
+    best = P.tune(3, "fp32tc", candidates=(1, 0), reps=1, force=True)
+    assert best in (1, 0)
+    scn = sc.tsunami(nx=40, ny=10, N=3, nlevels=4)
+    a = P.solver_from_scenario(scn, precision="fp32tc")
+    b = P.solver_from_scenario(scn, precision="fp32tc")
+    b.set_launch_config(1)
+    a.step(2)
+    b.step(2)
+    for u, v in zip(a.get_state()[:3], b.get_state()[:3]):
+        assert np.array_equal(u, v)
