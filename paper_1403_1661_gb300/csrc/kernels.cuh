@@ -90,6 +90,11 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 __device__ __forceinline__ float sqrt_nn(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
 __device__ __forceinline__ double sqrt_nn(double x) { return sqrt(x); }
 
+// Cache hints: start a line's trip from memory early, without holding registers.
+// Only addresses inside live buffers are ever passed.
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 template <typename T>
 __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 template <typename T>
@@ -271,6 +276,19 @@ __device__ __forceinline__ void surface_lift(const StageParams<T>& p, const T* _
   // ---- surface term (Section 7.2): traces, well-balanced flux, lift ----
   const int4 cn = __ldg(p.s.conn + e);
   const int nbs[3] = {cn.x, cn.y, cn.z};
+  // start all three neighbours' rows on their way before the first face needs them
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    const int nb = nbs[f];
+    if (nb >= 0) {
+      const long long an = k >> (level_of(sc, nb) - 1);
+      const T* qn = p.s.q + (size_t)(an & 1) * bstride + (size_t)nb * NPP;
+      prefetch_l1(qn);
+      prefetch_l1(qn + fstride);
+      prefetch_l1(qn + 2 * fstride);
+      prefetch_l1(p.s.B + (size_t)nb * NPP);
+    }
+  }
 #pragma unroll
   for (int f = 0; f < 3; ++f) {
     // outward normal times sJ/J from the affine factors
@@ -314,6 +332,16 @@ __device__ __forceinline__ void surface_lift(const StageParams<T>& p, const T* _
         }
       }
     }
+    // own face-node values, read once per face
+    T oe[NFP], ou[NFP], ov[NFP], oB[NFP];
+#pragma unroll
+    for (int m = 0; m < NFP; ++m) {
+      const int jn = face_node(N, f, m);
+      oe[m] = own(0, jn);
+      ou[m] = own(1, jn);
+      ov[m] = own(2, jn);
+      oB[m] = own(3, jn);
+    }
 #pragma unroll 1
     for (int gq = 0; gq < NG; ++gq) {
       T i1[D::NFPP];
@@ -321,11 +349,10 @@ __device__ __forceinline__ void surface_lift(const StageParams<T>& p, const T* _
       Trace<T> tm = {0, 0, 0, 0}, tp;
 #pragma unroll
       for (int m = 0; m < NFP; ++m) {
-        const int jn = face_node(N, f, m);
-        tm.eta += i1[m] * own(0, jn);
-        tm.hu += i1[m] * own(1, jn);
-        tm.hv += i1[m] * own(2, jn);
-        tm.B += i1[m] * own(3, jn);
+        tm.eta += i1[m] * oe[m];
+        tm.hu += i1[m] * ou[m];
+        tm.hv += i1[m] * ov[m];
+        tm.B += i1[m] * oB[m];
       }
       if (nb >= 0) {
         tp = {0, 0, 0, 0};
@@ -457,7 +484,7 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
   const Sched& sc = p.sc;
   const int K = sc.K;
   const long long k = (*p.s.macro) * (1LL << (sc.L - 1)) + p.j;
-  const T g = (T)p.ph.g, h0 = (T)p.ph.h0;
+  const T g = (T)p.ph.g, h0 = (T)p.ph.h0, hg = T(0.5) * g;
   double injected = 0.0;
 
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.nactive; e += gridDim.x * blockDim.x) {
@@ -498,13 +525,14 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
       const T hc = ec - bc;
       const T ih = hc > h0 ? recip(hc) : T(0);
       const T u = huc * ih, v = hvc * ih;
-      const T pr = T(0.5) * g * ec * (hc - bc);
-      const T F0 = huc, F1 = huc * u + pr, F2 = huc * v;
-      const T G0 = hvc, G1 = hvc * u, G2 = hvc * v + pr;
-      const T a0 = rx * F0 + ry * G0, a1 = rx * F1 + ry * G1, a2 = rx * F2 + ry * G2;   // cF1
-      const T b0 = sx * F0 + sy * G0, b1 = sx * F1 + sy * G1, b2 = sx * F2 + sy * G2;   // cF2
-      const T Bx = rx * brc + sx * bsc, By = ry * brc + sy * bsc;
-      const T S1 = -g * ec * Bx, S2 = -g * ec * By;
+      // cF1 = rx F + ry G and cF2 = sx F + sy G, with the momentum rows written
+      // through the mass row: rx (hu u + p) + ry hv u = u (rx hu + ry hv) + rx p
+      const T pr = hg * ec * (hc - bc);
+      const T a0 = rx * huc + ry * hvc, b0 = sx * huc + sy * hvc;
+      const T a1 = u * a0 + rx * pr, a2 = v * a0 + ry * pr;
+      const T b1 = u * b0 + sx * pr, b2 = v * b0 + sy * pr;
+      const T gm = -g * ec;
+      const T S1 = gm * (rx * brc + sx * bsc), S2 = gm * (ry * brc + sy * bsc);
       T prt[NPP], pst[NPP], pt[NPP];
       load_row<T, NPP>(sops + O::PRT + c * NPP, prt);
       load_row<T, NPP>(sops + O::PST + c * NPP, pst);

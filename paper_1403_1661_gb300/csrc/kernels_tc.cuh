@@ -48,16 +48,20 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
+// Per-warp shared tiles are node-major with the 32 elements of the warp
+// contiguous and a stride of LS = 36 words per node: one thread per element
+// reads a node of its own element without bank conflicts, and the mma fragment
+// reads (rows g, g+8, nodes 2t, 2t+1) land on 32 distinct banks.
+constexpr int LS = 36;
+
 template <int N>
 struct TcSmem {
   using D = Dims<N>;
   using C = TcDims<N>;
-  static constexpr int ROW = C::KP;                      // floats per state row (nodes, zero padded)
-  static constexpr int RROW = C::NPT;                    // floats per R row
-  // per warp: state [4 fields][32 el][ROW], R [3][32][RROW], geo [32][4]
+  // per warp: state [4 fields][KP nodes][LS], R [3][NPT][LS], geo [32][4]
   static constexpr int STATE = 0;
-  static constexpr int RT = STATE + 4 * 32 * ROW;
-  static constexpr int GEO = RT + 3 * 32 * RROW;
+  static constexpr int RT = STATE + 4 * C::KP * LS;
+  static constexpr int GEO = RT + 3 * C::NPT * LS;
   static constexpr int WARP = GEO + 32 * 4;              // floats per warp
   static constexpr int OPS = OpLayout<N>::TAIL;          // floats of per-element operators (staged first)
   static constexpr int BYTES = (OPS + kTcWarps * WARP) * 4;
@@ -92,7 +96,7 @@ __global__ void __launch_bounds__(kTcBlock, (N <= 4 ? 3 : 2)) k_stage_tc(StagePa
   const Sched& sc = p.sc;
   const int K = sc.K;
   const long long k = (*p.s.macro) * (1LL << (sc.L - 1)) + p.j;
-  const float gg = (float)p.ph.g, h0 = (float)p.ph.h0;
+  const float gg = (float)p.ph.g, h0 = (float)p.ph.h0, hg = 0.5f * gg;
   const size_t fstride = (size_t)K * NPP, bstride = 3 * fstride;
   double injected = 0.0;
   const int ntiles = (p.nactive + 31) / 32;
@@ -123,17 +127,32 @@ __global__ void __launch_bounds__(kTcBlock, (N <= 4 ? 3 : 2)) k_stage_tc(StagePa
         reinterpret_cast<float4*>(s_geo)[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
 #pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        float4* row = reinterpret_cast<float4*>(s_state + (f * 32 + lane) * KP);
+      for (int f = 0; f < 4; ++f)
 #pragma unroll
-        for (int i4 = 0; i4 < KP / 4; ++i4) {
-          const int i = 4 * i4;
-          row[i4] = make_float4(i < NPP ? q[f][i] : 0.f, i + 1 < NPP ? q[f][i + 1] : 0.f,
-                                i + 2 < NPP ? q[f][i + 2] : 0.f, i + 3 < NPP ? q[f][i + 3] : 0.f);
+        for (int i = 0; i < KP; ++i) s_state[(f * KP + i) * LS + lane] = i < NPP ? q[f][i] : 0.f;
+    }
+    __syncwarp();
+
+    // the next tile's rows and this element's older R slots start moving now
+    {
+      const int en = e + gridDim.x * kTcWarps * 32;
+      if (en < p.nactive) {
+        const long long an = k >> (level_of(sc, en) - 1);
+        const float* qn = p.s.q + (size_t)(an & 1) * bstride + (size_t)en * NPP;
+        prefetch_l2(qn);
+        prefetch_l2(qn + fstride);
+        prefetch_l2(qn + 2 * fstride);
+        prefetch_l2(p.s.B + (size_t)en * NPP);
+      }
+      if (valid && p.mode == 0) {
+        for (int s = 1; s < 3 && s <= a; ++s) {
+          const float* rs = p.s.ring + (size_t)((a - s) % 3) * bstride + (size_t)e * NPP;
+          prefetch_l2(rs);
+          prefetch_l2(rs + fstride);
+          prefetch_l2(rs + 2 * fstride);
         }
       }
     }
-    __syncwarp();
 
     // ---- volume term on tensor cores, one m-tile of 16 elements at a time ----
 #pragma unroll 1
@@ -145,12 +164,11 @@ __global__ void __launch_bounds__(kTcBlock, (N <= 4 ? 3 : 2)) k_stage_tc(StagePa
       for (int f = 0; f < 4; ++f)
 #pragma unroll
         for (int ks = 0; ks < KSTEP; ++ks) {
-          const float* s0 = s_state + (f * 32 + r0) * KP + 16 * ks;
-          const float* s1 = s_state + (f * 32 + r1) * KP + 16 * ks;
-          const float2 v00 = *reinterpret_cast<const float2*>(s0 + 2 * t);
-          const float2 v10 = *reinterpret_cast<const float2*>(s1 + 2 * t);
-          const float2 v01 = *reinterpret_cast<const float2*>(s0 + 2 * t + 8);
-          const float2 v11 = *reinterpret_cast<const float2*>(s1 + 2 * t + 8);
+          const float* sn = s_state + (f * KP + 16 * ks + 2 * t) * LS;   // node 16ks + 2t
+          const float2 v00 = make_float2(sn[r0], sn[LS + r0]);
+          const float2 v10 = make_float2(sn[r1], sn[LS + r1]);
+          const float2 v01 = make_float2(sn[8 * LS + r0], sn[9 * LS + r0]);
+          const float2 v11 = make_float2(sn[8 * LS + r1], sn[9 * LS + r1]);
           split2(v00.x, v00.y, ah[f][ks][0], al[f][ks][0]);
           split2(v10.x, v10.y, ah[f][ks][1], al[f][ks][1]);
           split2(v01.x, v01.y, ah[f][ks][2], al[f][ks][2]);
@@ -166,8 +184,28 @@ __global__ void __launch_bounds__(kTcBlock, (N <= 4 ? 3 : 2)) k_stage_tc(StagePa
 #pragma unroll
           for (int c = 0; c < 4; ++c) Racc[f][nt][c] = 0.f;
 
+      // interpolation fragments of the first cubature tile
+      uint2 ibh[3][KSTEP], ibl[3][KSTEP];
+#pragma unroll
+      for (int op = 0; op < 3; ++op)
+#pragma unroll
+        for (int ks = 0; ks < KSTEP; ++ks) {
+          const uint32_t* fb = stc + TL::INTERP + (((op * CT + 0) * KSTEP + ks) * 2) * 64 + lane * 2;
+          ibh[op][ks] = __ldg(reinterpret_cast<const uint2*>(fb));
+          ibl[op][ks] = __ldg(reinterpret_cast<const uint2*>(fb + 64));
+        }
 #pragma unroll 1
       for (int ct = 0; ct < CT; ++ct) {
+        // projection fragments of this tile: in flight during the interpolation and flux
+        uint32_t pbh[3][NT], pbl[3][NT];
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+          for (int op = 0; op < 3; ++op) {
+            const uint32_t* fb = stc + TL::PROJ + (((op * CT + ct) * NT + nt) * 2) * 32 + lane;
+            pbh[op][nt] = __ldg(fb);
+            pbl[op][nt] = __ldg(fb + 32);
+          }
         // interpolation: acc[0..3] = (eta, hu, hv, B) * Ic, acc[4] = B * Icr, acc[5] = B * Ics
         float acc[6][4];
 #pragma unroll
@@ -177,23 +215,28 @@ __global__ void __launch_bounds__(kTcBlock, (N <= 4 ? 3 : 2)) k_stage_tc(StagePa
 #pragma unroll
         for (int ks = 0; ks < KSTEP; ++ks) {
 #pragma unroll
-          for (int op = 0; op < 3; ++op) {
-            const uint32_t* fb = stc + TL::INTERP + (((op * CT + ct) * KSTEP + ks) * 2) * 64 + lane * 2;
-            const uint2 bh = __ldg(reinterpret_cast<const uint2*>(fb));
-            const uint2 bl = __ldg(reinterpret_cast<const uint2*>(fb + 64));
-            if (op == 0) {
-#pragma unroll
-              for (int f = 0; f < 4; ++f) {
-                mma_k16(acc[f], al[f][ks], bh.x, bh.y);
-                mma_k16(acc[f], ah[f][ks], bl.x, bl.y);
-                mma_k16(acc[f], ah[f][ks], bh.x, bh.y);
-              }
-            } else {
-              mma_k16(acc[3 + op], al[3][ks], bh.x, bh.y);
-              mma_k16(acc[3 + op], ah[3][ks], bl.x, bl.y);
-              mma_k16(acc[3 + op], ah[3][ks], bh.x, bh.y);
-            }
+          for (int f = 0; f < 4; ++f) {
+            mma_k16(acc[f], al[f][ks], ibh[0][ks].x, ibh[0][ks].y);
+            mma_k16(acc[f], ah[f][ks], ibl[0][ks].x, ibl[0][ks].y);
+            mma_k16(acc[f], ah[f][ks], ibh[0][ks].x, ibh[0][ks].y);
           }
+#pragma unroll
+          for (int op = 1; op < 3; ++op) {
+            mma_k16(acc[3 + op], al[3][ks], ibh[op][ks].x, ibh[op][ks].y);
+            mma_k16(acc[3 + op], ah[3][ks], ibl[op][ks].x, ibl[op][ks].y);
+            mma_k16(acc[3 + op], ah[3][ks], ibh[op][ks].x, ibh[op][ks].y);
+          }
+        }
+        // interpolation fragments of the next tile: in flight during the flux and projection
+        if (ct + 1 < CT) {
+#pragma unroll
+          for (int op = 0; op < 3; ++op)
+#pragma unroll
+            for (int ks = 0; ks < KSTEP; ++ks) {
+              const uint32_t* fb = stc + TL::INTERP + (((op * CT + ct + 1) * KSTEP + ks) * 2) * 64 + lane * 2;
+              ibh[op][ks] = __ldg(reinterpret_cast<const uint2*>(fb));
+              ibl[op][ks] = __ldg(reinterpret_cast<const uint2*>(fb + 64));
+            }
         }
         // flux and source at the lane's four points: (r0, 2t), (r0, 2t+1), (r1, 2t), (r1, 2t+1)
         float fl[8][4];
@@ -206,18 +249,18 @@ __global__ void __launch_bounds__(kTcBlock, (N <= 4 ? 3 : 2)) k_stage_tc(StagePa
           const float hc = ec - bc;
           const float ih = hc > h0 ? recip(hc) : 0.f;
           const float u = huc * ih, v = hvc * ih;
-          const float pr = 0.5f * gg * ec * (hc - bc);
-          const float F0 = huc, F1 = huc * u + pr, F2 = huc * v;
-          const float G0 = hvc, G1 = hvc * u, G2 = hvc * v + pr;
-          fl[0][c] = rx * F0 + ry * G0;
-          fl[1][c] = rx * F1 + ry * G1;
-          fl[2][c] = rx * F2 + ry * G2;
-          fl[3][c] = sx * F0 + sy * G0;
-          fl[4][c] = sx * F1 + sy * G1;
-          fl[5][c] = sx * F2 + sy * G2;
-          const float Bx = rx * brc + sx * bsc, By = ry * brc + sy * bsc;
-          fl[6][c] = -gg * ec * Bx;
-          fl[7][c] = -gg * ec * By;
+          // momentum rows of cF1, cF2 written through the mass row (see k_stage)
+          const float pr = hg * ec * (hc - bc);
+          const float a0 = rx * huc + ry * hvc, b0 = sx * huc + sy * hvc;
+          fl[0][c] = a0;
+          fl[1][c] = u * a0 + rx * pr;
+          fl[2][c] = v * a0 + ry * pr;
+          fl[3][c] = b0;
+          fl[4][c] = u * b0 + sx * pr;
+          fl[5][c] = v * b0 + sy * pr;
+          const float gm = -gg * ec;
+          fl[6][c] = gm * (rx * brc + sx * bsc);
+          fl[7][c] = gm * (ry * brc + sy * bsc);
         }
         // A fragments (m16n8k8): reg0 = row r0 (points 2t, 2t+1), reg1 = row r1
         uint32_t fh[8][2], flo[8][2];
@@ -229,13 +272,8 @@ __global__ void __launch_bounds__(kTcBlock, (N <= 4 ? 3 : 2)) k_stage_tc(StagePa
         // projection: R_h += cF1_h Pr + cF2_h Ps; R_m += cF1_m Pr + cF2_m Ps + cS_m P
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt) {
-          uint32_t bh[3], bl[3];
-#pragma unroll
-          for (int op = 0; op < 3; ++op) {
-            const uint32_t* fb = stc + TL::PROJ + (((op * CT + ct) * NT + nt) * 2) * 32 + lane;
-            bh[op] = __ldg(fb);
-            bl[op] = __ldg(fb + 32);
-          }
+          const uint32_t bh[3] = {pbh[0][nt], pbh[1][nt], pbh[2][nt]};
+          const uint32_t bl[3] = {pbl[0][nt], pbl[1][nt], pbl[2][nt]};
 #pragma unroll
           for (int f = 0; f < 3; ++f) {
             // cF1 (quantity f) with Pr, cF2 (3+f) with Ps, source (5+f, f>0) with P
@@ -258,10 +296,11 @@ __global__ void __launch_bounds__(kTcBlock, (N <= 4 ? 3 : 2)) k_stage_tc(StagePa
       for (int f = 0; f < 3; ++f)
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt) {
-          *reinterpret_cast<float2*>(s_R + (f * 32 + r0) * C::NPT + 8 * nt + 2 * t) =
-              make_float2(Racc[f][nt][0], Racc[f][nt][1]);
-          *reinterpret_cast<float2*>(s_R + (f * 32 + r1) * C::NPT + 8 * nt + 2 * t) =
-              make_float2(Racc[f][nt][2], Racc[f][nt][3]);
+          float* rn = s_R + (f * C::NPT + 8 * nt + 2 * t) * LS;
+          rn[r0] = Racc[f][nt][0];
+          rn[LS + r0] = Racc[f][nt][1];
+          rn[r1] = Racc[f][nt][2];
+          rn[LS + r1] = Racc[f][nt][3];
         }
     }
     __syncwarp();
@@ -271,22 +310,25 @@ __global__ void __launch_bounds__(kTcBlock, (N <= 4 ? 3 : 2)) k_stage_tc(StagePa
       float R0[NP], R1[NP], R2[NP];
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
-        R0[i] = s_R[(0 * 32 + lane) * C::NPT + i];
-        R1[i] = s_R[(1 * 32 + lane) * C::NPT + i];
-        R2[i] = s_R[(2 * 32 + lane) * C::NPT + i];
+        R0[i] = s_R[(0 * C::NPT + i) * LS + lane];
+        R1[i] = s_R[(1 * C::NPT + i) * LS + lane];
+        R2[i] = s_R[(2 * C::NPT + i) * LS + lane];
       }
       const float4 ge = reinterpret_cast<const float4*>(s_geo)[lane];
       // the per-element operators were staged at the start of shared memory with the
       // OpLayout offsets, so the shared epilogue indexes them directly; the own
       // state is read from the warp's shared tile when the surface term needs it
-      const float* my = s_state + lane * KP;
-      auto own = [&](int f, int jn) -> float { return my[f * 32 * KP + jn]; };
+      const float* my = s_state + lane;
+      auto own = [&](int f, int jn) -> float { return my[(f * KP + jn) * LS]; };
       surface_lift<float, N>(p, sops, e, k, own, ge.x, ge.y, ge.z, ge.w, R0, R1, R2);
       float eta[NPP], hu[NPP], hv[NPP], bb[NPP];
-      load_row<float, NPP>(my + 0 * 32 * KP, eta);
-      load_row<float, NPP>(my + 1 * 32 * KP, hu);
-      load_row<float, NPP>(my + 2 * 32 * KP, hv);
-      load_row<float, NPP>(my + 3 * 32 * KP, bb);
+#pragma unroll
+      for (int i = 0; i < NPP; ++i) {
+        eta[i] = my[(0 * KP + i) * LS];
+        hu[i] = my[(1 * KP + i) * LS];
+        hv[i] = my[(2 * KP + i) * LS];
+        bb[i] = my[(3 * KP + i) * LS];
+      }
       commit_and_limit<float, N>(p, sops, e, lev, a, eta, hu, hv, bb, ge.x, ge.y, ge.z, ge.w, R0, R1, R2,
                                  &injected);
     }
