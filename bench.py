@@ -315,10 +315,11 @@ def run_ours(args):
             out = s.get_state()
             de += s.stats()["dof_updates"] - d_before
         te = (time.perf_counter() - t0) / ne
-        npp = ((args.order + 1) * (args.order + 2) // 2 + 3) // 4 * 4
+        # device node planes: Np planes of KS = K rounded up to 32 elements per field
+        plane = (args.order + 1) * (args.order + 2) // 2 * ((s.K + 31) // 32 * 32)
         result["e2e"] = {"value": (de / ne) / te, "unit": UNIT,
-                         "h2d_bytes_per_step": 3 * s.K * npp * ts,
-                         "d2h_bytes_per_step": 2 * 3 * s.K * npp * ts + 64,
+                         "h2d_bytes_per_step": 3 * plane * ts,
+                         "d2h_bytes_per_step": 2 * 3 * plane * ts + 64,
                          "note": "swe_set_state (FP64 host arrays) + swe_step(1) + swe_get_state per step"}
 
     # the plain FP64 GPU form on the same workload (fewer steps: ~60x slower)

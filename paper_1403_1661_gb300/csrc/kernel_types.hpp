@@ -67,12 +67,15 @@ struct TcLayout {
   static constexpr int SIZE = PROJ + 3 * C::CT * C::NT * 2 * 32;
 };
 
-// Pointers into the caller-owned workspace.
+// Pointers into the caller-owned workspace. Nodal arrays are node-major
+// ("planes"): node i of element e is at plane[i * KS + e], KS = K rounded up to
+// a multiple of 32, so the threads of a warp, one element each, read and write
+// whole 128-byte lines.
 template <typename T>
 struct DevState {
-  T* q;                 // [2][3][K][NPP] double-buffered (eta, hu, hv)
-  T* ring;              // [3][3][K][NPP] Adams-Bashforth history of R
-  const T* B;           // [K][NPP]
+  T* q;                 // [2][3][NP][KS] double-buffered (eta, hu, hv)
+  T* ring;              // [3][3][NP][KS] Adams-Bashforth history of R
+  const T* B;           // [NP][KS]
   const T* geo;         // [K][4] rx, ry, sx, sy
   const int4* conn;     // [K] neighbour across faces 0,1,2 (-1: wall); .w packs faces/stencil
   const T* tvbg;        // [K][8] alpha_i, beta_i (i = 0..2)
@@ -88,6 +91,7 @@ struct DevState {
 
 struct Sched {
   int K;                     // elements
+  int KS;                    // element stride of the node planes (K rounded up to 32)
   int L;                     // levels in use
   int off[kMaxLevels + 1];   // level l (1-based) occupies [off[l-1], off[l])
   double dt_min;

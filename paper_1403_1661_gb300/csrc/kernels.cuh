@@ -2,9 +2,12 @@
 // Adams-Bashforth update and the limiters (CUDA, sm_103a).
 //
 // One thread owns one element (element-blocked SIMT): the element's nodal state
-// stays in registers from the coalesced 16-byte loads to the committed, limited
-// result, and the reference operators are staged once per CTA in shared memory,
-// where every warp reads them as broadcasts.
+// stays in registers from the loads to the committed, limited result, and the
+// reference operators are staged once per CTA in shared memory, where every warp
+// reads them as broadcasts. Nodal arrays are node-major planes (node i of element
+// e at plane[i * KS + e]), so a warp's loads and stores of one node cover
+// consecutive elements: whole lines, and nearly so for the neighbour traces of
+// a mesh numbered with locality.
 //
 // Formulation. The state is stored as (eta, hu, hv) with the free surface
 // eta = h + B. The momentum fluxes and the source are written about the datum
@@ -83,12 +86,29 @@ __device__ __forceinline__ void store_row_global(T* __restrict__ p, const T (&o)
   for (int k = 0; k < LEN / V::n; ++k) pv[k] = V::pack(&o[k * V::n]);
 }
 
+// Node-major element access: node i of the element at p is p[i * ks]. LEN >= NP
+// registers; the padding entries read as zero.
+template <typename T, int NP, int LEN>
+__device__ __forceinline__ void load_nodes(const T* __restrict__ p, size_t ks, T (&o)[LEN]) {
+#pragma unroll
+  for (int i = 0; i < LEN; ++i) o[i] = i < NP ? __ldg(p + i * ks) : T(0);
+}
+
+template <typename T, int NP, int LEN>
+__device__ __forceinline__ void store_nodes(T* __restrict__ p, size_t ks, const T (&o)[LEN]) {
+#pragma unroll
+  for (int i = 0; i < NP; ++i) p[i * ks] = o[i];
+}
+
 // Reciprocal and square root: hardware approximations in FP32 (about 1-2 ulp, no
 // slow-path branches), correctly rounded in FP64.
 __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
-__device__ __forceinline__ float sqrt_nn(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+// sqrt of x >= 0; the floor keeps x = 0 at 0 (0 * finite) instead of 0 * inf
+__device__ __forceinline__ float sqrt_nn(float x) { return x * rsqrtf(fmaxf(x, 1e-30f)); }
 __device__ __forceinline__ double sqrt_nn(double x) { return sqrt(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
 
 // Cache hints: start a line's trip from memory early, without holding registers.
 // Only addresses inside live buffers are ever passed.
@@ -154,22 +174,26 @@ struct Trace {
   T eta, hu, hv, B;
 };
 
+// (nx, ny) unit outward normal, (vx, vy) = (sJ/J) (nx, ny), hs = sJ/J / 2; the
+// returned fluxes are already scaled by sJ/J for the lift. hg = g/2, qg = g/4.
 template <typename T>
-__device__ __forceinline__ void wb_flux(const Trace<T>& m, const Trace<T>& p, T nx, T ny, T g, T h0,
-                                        T& f0, T& f1, T& f2) {
+__device__ __forceinline__ void wb_flux(const Trace<T>& m, const Trace<T>& p, T nx, T ny, T vx, T vy, T hs,
+                                        T g, T hg, T qg, T h0, T& f0, T& f1, T& f2) {
   const T hm = m.eta - m.B, hp = p.eta - p.B;
   const T im = hm > h0 ? recip(hm) : T(0), ip = hp > h0 ? recip(hp) : T(0);
   const T um = m.hu * im, vm = m.hv * im;
   const T up = p.hu * ip, vp = p.hv * ip;
   const T bmax = tmax(m.B, p.B);
+  // hydrostatically reconstructed depths and the normal mass fluxes they carry
   const T sm = tmax(T(0), m.eta - bmax), sp = tmax(T(0), p.eta - bmax);
   const T unm = um * nx + vm * ny, unp = up * nx + vp * ny;
   const T lam = tmax(fabs(unm) + sqrt_nn(g * sm), fabs(unp) + sqrt_nn(g * sp));
-  const T half = T(0.5);
-  f0 = half * (sm * unm + sp * unp) - half * lam * (sp - sm);
-  const T pres = half * g * m.eta * (hm - m.B) + T(0.25) * g * (sp - sm) * (sp + sm);
-  f1 = half * (sm * um * unm + sp * up * unp) - half * lam * (sp * up - sm * um) + pres * nx;
-  f2 = half * (sm * vm * unm + sp * vp * unp) - half * lam * (sp * vp - sm * vm) + pres * ny;
+  const T Fm = sm * unm, Fp = sp * unp;
+  const T ds = sp - sm;
+  const T pres = hg * m.eta * (hm - m.B) + qg * ds * (sp + sm);
+  f0 = hs * ((Fm + Fp) - lam * ds);
+  f1 = hs * ((Fm * um + Fp * up) - lam * (sp * up - sm * um)) + pres * vx;
+  f2 = hs * ((Fm * vm + Fp * vp) - lam * (sp * vp - sm * vm)) + pres * vy;
 }
 
 // --------------------------------------------------------------------------
@@ -259,8 +283,10 @@ __device__ __forceinline__ int positivity(T (&eta)[Dims<N>::NPP], T (&hu)[Dims<N
 // three faces, the well-balanced flux, and the lift subtracted from R (in
 // registers). own(f, j) returns the element's own field f (eta, hu, hv, B) at
 // node j, so the caller decides whether the state sits in registers or in
-// shared memory. Shared by the SIMT and the tensor-core stage kernels.
-template <typename T, int N, typename Own>
+// shared memory. Shared by the SIMT and the tensor-core stage kernels. With
+// kRolled the three faces run through one copy of the face code (own() must then
+// accept run-time node indices); otherwise the face loop is unrolled.
+template <typename T, int N, bool kRolled = false, typename Own>
 __device__ __forceinline__ void surface_lift(const StageParams<T>& p, const T* __restrict__ sops, int e,
                                              long long k, const Own& own, T rx, T ry, T sx, T sy,
                                              T (&R0)[Dims<N>::NP], T (&R1)[Dims<N>::NP],
@@ -269,50 +295,37 @@ __device__ __forceinline__ void surface_lift(const StageParams<T>& p, const T* _
   using O = OpLayout<N>;
   constexpr int NP = D::NP, NPP = D::NPP, NFP = D::NFP, NG = D::NG;
   const Sched& sc = p.sc;
-  const int K = sc.K;
-  const T g = (T)p.ph.g, h0 = (T)p.ph.h0;
-  const size_t fstride = (size_t)K * NPP;
+  const T g = (T)p.ph.g, h0 = (T)p.ph.h0, hg = T(0.5) * g, qg = T(0.25) * g;
+  const size_t ks = (size_t)sc.KS;
+  const size_t fstride = (size_t)NP * ks;
   const size_t bstride = 3 * fstride;
   // ---- surface term (Section 7.2): traces, well-balanced flux, lift ----
   const int4 cn = __ldg(p.s.conn + e);
-  const int nbs[3] = {cn.x, cn.y, cn.z};
-  // start all three neighbours' rows on their way before the first face needs them
-#pragma unroll
-  for (int f = 0; f < 3; ++f) {
-    const int nb = nbs[f];
-    if (nb >= 0) {
-      const long long an = k >> (level_of(sc, nb) - 1);
-      const T* qn = p.s.q + (size_t)(an & 1) * bstride + (size_t)nb * NPP;
-      prefetch_l1(qn);
-      prefetch_l1(qn + fstride);
-      prefetch_l1(qn + 2 * fstride);
-      prefetch_l1(p.s.B + (size_t)nb * NPP);
-    }
-  }
-#pragma unroll
+#pragma unroll (kRolled ? 1 : 3)
   for (int f = 0; f < 3; ++f) {
     // outward normal times sJ/J from the affine factors
     const T vxn = f == 0 ? -sx : (f == 1 ? rx + sx : -rx);
     const T vyn = f == 0 ? -sy : (f == 1 ? ry + sy : -ry);
-    const T scale = sqrt(vxn * vxn + vyn * vyn);
-    const T nx = vxn / scale, ny = vyn / scale;
+    const T v2 = vxn * vxn + vyn * vyn;
+    const T iv = rsqrt_t(v2);
+    const T nx = vxn * iv, ny = vyn * iv, hs = T(0.5) * v2 * iv;
     // neighbour face-node values, in this element's traversal order
     T ne[NFP], nu[NFP], nv[NFP], nB[NFP];
-    const int nb = nbs[f];
+    const int nb = f == 0 ? cn.x : (f == 1 ? cn.y : cn.z);
     if (nb >= 0) {
       const int fn = (cn.w >> (2 * f)) & 3;
       const int ln = level_of(sc, nb);
       const long long an = k >> (ln - 1);
       const long long pern = 1LL << (ln - 1);
       const long long phase = k & (pern - 1);
-      const T* qn = p.s.q + (size_t)(an & 1) * bstride;
+      const T* qn = p.s.q + (size_t)(an & 1) * bstride + nb;
 #pragma unroll
       for (int m = 0; m < NFP; ++m) {
-        const size_t idx = (size_t)nb * NPP + face_node_rt(N, fn, NFP - 1 - m);
+        const size_t idx = (size_t)face_node_rt(N, fn, NFP - 1 - m) * ks;
         ne[m] = __ldg(qn + idx);
         nu[m] = __ldg(qn + fstride + idx);
         nv[m] = __ldg(qn + 2 * fstride + idx);
-        nB[m] = __ldg(p.s.B + idx);
+        nB[m] = __ldg(p.s.B + nb + idx);
       }
       if (phase != 0) {  // neighbour between its steps: Adams-Bashforth polynomial at t_k
         const int depth = an + 1 < 3 ? (int)(an + 1) : 3;
@@ -321,10 +334,10 @@ __device__ __forceinline__ void surface_lift(const StageParams<T>& p, const T* _
         const T dtn = level_dt(sc, ln, T(0));
         for (int s = 0; s < depth; ++s) {
           const T ws = dtn * w[s];
-          const T* rs = p.s.ring + (size_t)((an - s) % 3) * bstride;
+          const T* rs = p.s.ring + (size_t)((an - s) % 3) * bstride + nb;
 #pragma unroll
           for (int m = 0; m < NFP; ++m) {
-            const size_t idx = (size_t)nb * NPP + face_node_rt(N, fn, NFP - 1 - m);
+            const size_t idx = (size_t)face_node_rt(N, fn, NFP - 1 - m) * ks;
             ne[m] += ws * __ldg(rs + idx);
             nu[m] += ws * __ldg(rs + fstride + idx);
             nv[m] += ws * __ldg(rs + 2 * fstride + idx);
@@ -368,8 +381,7 @@ __device__ __forceinline__ void surface_lift(const StageParams<T>& p, const T* _
         tp = {tm.eta, tm.hu - T(2) * mn * nx, tm.hv - T(2) * mn * ny, tm.B};
       }
       T f0, f1, f2;
-      wb_flux<T>(tm, tp, nx, ny, g, h0, f0, f1, f2);
-      f0 *= scale; f1 *= scale; f2 *= scale;
+      wb_flux<T>(tm, tp, nx, ny, vxn, vyn, hs, g, hg, qg, h0, f0, f1, f2);
       T lg[NPP];
       load_row<T, NPP>(sops + O::LGT + (f * NG + gq) * NPP, lg);
 #pragma unroll
@@ -396,7 +408,8 @@ __device__ __forceinline__ void commit_and_limit(const StageParams<T>& p, const 
   const Sched& sc = p.sc;
   const int K = sc.K;
   const int dst = (int)((a + 1) & 1);
-  const size_t fstride = (size_t)K * NPP;
+  const size_t ks = (size_t)sc.KS;
+  const size_t fstride = (size_t)NP * ks;
   const size_t bstride = 3 * fstride;
   double& injected = *injected_acc;
   if (p.mode == 1) {  // R only, caller layout
@@ -417,19 +430,10 @@ __device__ __forceinline__ void commit_and_limit(const StageParams<T>& p, const 
   const T dtl = level_dt(sc, lev, T(0));
   const T c0 = dtl * wab[0], c1 = dtl * wab[1], c2 = dtl * wab[2];
   T* ring = p.s.ring;
-  const size_t eo = (size_t)e * NPP;
-  {
-    T pad[NPP];
-#pragma unroll
-    for (int i = 0; i < NPP; ++i) pad[i] = i < NP ? R0[i] : T(0);
-    store_row_global<T, NPP>(ring + (size_t)(a % 3) * bstride + 0 * fstride + eo, pad);
-#pragma unroll
-    for (int i = 0; i < NPP; ++i) pad[i] = i < NP ? R1[i] : T(0);
-    store_row_global<T, NPP>(ring + (size_t)(a % 3) * bstride + 1 * fstride + eo, pad);
-#pragma unroll
-    for (int i = 0; i < NPP; ++i) pad[i] = i < NP ? R2[i] : T(0);
-    store_row_global<T, NPP>(ring + (size_t)(a % 3) * bstride + 2 * fstride + eo, pad);
-  }
+  const size_t eo = (size_t)e;
+  store_nodes<T, NP, NP>(ring + (size_t)(a % 3) * bstride + 0 * fstride + eo, ks, R0);
+  store_nodes<T, NP, NP>(ring + (size_t)(a % 3) * bstride + 1 * fstride + eo, ks, R1);
+  store_nodes<T, NP, NP>(ring + (size_t)(a % 3) * bstride + 2 * fstride + eo, ks, R2);
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
     eta[i] += c0 * R0[i];
@@ -439,16 +443,12 @@ __device__ __forceinline__ void commit_and_limit(const StageParams<T>& p, const 
   for (int s = 1; s < depth; ++s) {
     const T cs = s == 1 ? c1 : c2;
     const T* rs = ring + (size_t)((a - s) % 3) * bstride + eo;
-    T r[NPP];
-    load_row_global<T, NPP>(rs, r);
 #pragma unroll
-    for (int i = 0; i < NP; ++i) eta[i] += cs * r[i];
-    load_row_global<T, NPP>(rs + fstride, r);
-#pragma unroll
-    for (int i = 0; i < NP; ++i) hu[i] += cs * r[i];
-    load_row_global<T, NPP>(rs + 2 * fstride, r);
-#pragma unroll
-    for (int i = 0; i < NP; ++i) hv[i] += cs * r[i];
+    for (int i = 0; i < NP; ++i) {
+      eta[i] += cs * __ldg(rs + i * ks);
+      hu[i] += cs * __ldg(rs + fstride + i * ks);
+      hv[i] += cs * __ldg(rs + 2 * fstride + i * ks);
+    }
   }
 
   // ---- positivity limiter (Algorithm 3) and means ----
@@ -457,11 +457,9 @@ __device__ __forceinline__ void commit_and_limit(const StageParams<T>& p, const 
                                     &injected, mean);
   if (!(isfinite((double)mean[0]) && isfinite((double)mean[1]) && isfinite((double)mean[2])))
     atomicOr(p.s.flags, 1);
-#pragma unroll
-  for (int i = NP; i < NPP; ++i) { eta[i] = 0; hu[i] = 0; hv[i] = 0; }
-  store_row_global<T, NPP>(p.s.q + dst * bstride + 0 * fstride + eo, eta);
-  store_row_global<T, NPP>(p.s.q + dst * bstride + 1 * fstride + eo, hu);
-  store_row_global<T, NPP>(p.s.q + dst * bstride + 2 * fstride + eo, hv);
+  store_nodes<T, NP, NPP>(p.s.q + dst * bstride + 0 * fstride + eo, ks, eta);
+  store_nodes<T, NP, NPP>(p.s.q + dst * bstride + 1 * fstride + eo, ks, hu);
+  store_nodes<T, NP, NPP>(p.s.q + dst * bstride + 2 * fstride + eo, ks, hv);
   p.s.means[4 * (size_t)e + 0] = mean[0];
   p.s.means[4 * (size_t)e + 1] = mean[1];
   p.s.means[4 * (size_t)e + 2] = mean[2];
@@ -482,22 +480,22 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
   stage_ops<T, N>(sops, p.s.ops);
 
   const Sched& sc = p.sc;
-  const int K = sc.K;
   const long long k = (*p.s.macro) * (1LL << (sc.L - 1)) + p.j;
   const T g = (T)p.ph.g, h0 = (T)p.ph.h0, hg = T(0.5) * g;
+  const size_t ks = (size_t)sc.KS;
+  const size_t fstride = (size_t)NP * ks;            // between fields
+  const size_t bstride = 3 * fstride;                // between buffers
   double injected = 0.0;
 
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.nactive; e += gridDim.x * blockDim.x) {
     const int lev = level_of(sc, e);
     const long long a = k >> (lev - 1);
     const int src = (int)(a & 1);
-    const size_t fstride = (size_t)K * NPP;            // between fields
-    const size_t bstride = 3 * fstride;                // between buffers
     T eta[NPP], hu[NPP], hv[NPP], bb[NPP];
-    load_row_global<T, NPP>(p.s.q + src * bstride + 0 * fstride + (size_t)e * NPP, eta);
-    load_row_global<T, NPP>(p.s.q + src * bstride + 1 * fstride + (size_t)e * NPP, hu);
-    load_row_global<T, NPP>(p.s.q + src * bstride + 2 * fstride + (size_t)e * NPP, hv);
-    load_row_global<T, NPP>(p.s.B + (size_t)e * NPP, bb);
+    load_nodes<T, NP, NPP>(p.s.q + src * bstride + 0 * fstride + e, ks, eta);
+    load_nodes<T, NP, NPP>(p.s.q + src * bstride + 1 * fstride + e, ks, hu);
+    load_nodes<T, NP, NPP>(p.s.q + src * bstride + 2 * fstride + e, ks, hv);
+    load_nodes<T, NP, NPP>(p.s.B + e, ks, bb);
     const T rx = __ldg(p.s.geo + 4 * (size_t)e + 0), ry = __ldg(p.s.geo + 4 * (size_t)e + 1);
     const T sx = __ldg(p.s.geo + 4 * (size_t)e + 2), sy = __ldg(p.s.geo + 4 * (size_t)e + 3);
 
@@ -558,30 +556,31 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
 template <typename T, int N>
 __global__ void __launch_bounds__(kBlock) k_positivity(LimitParams<T> p) {
   using D = Dims<N>;
-  constexpr int NPP = D::NPP;
+  constexpr int NP = D::NP, NPP = D::NPP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sops = reinterpret_cast<T*>(smem_raw);
   stage_ops<T, N>(sops, p.s.ops);
   const Sched& sc = p.sc;
   const long long k = (*p.s.macro) * (1LL << (sc.L - 1)) + p.j;
+  const size_t ks = (size_t)sc.KS, fstride = (size_t)NP * ks, bstride = 3 * fstride;
   double injected = 0.0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.nactive; e += gridDim.x * blockDim.x) {
     const int lev = level_of(sc, e);
     const long long a = k >> (lev - 1);
     const int cur = (int)((a + p.post_stage) & 1);
-    const size_t fstride = (size_t)sc.K * NPP, bstride = 3 * fstride, eo = (size_t)e * NPP;
+    const size_t eo = (size_t)e;
     T* q = p.s.q + cur * bstride;
     T eta[NPP], hu[NPP], hv[NPP], bb[NPP];
-    load_row_global<T, NPP>(q + eo, eta);
-    load_row_global<T, NPP>(q + fstride + eo, hu);
-    load_row_global<T, NPP>(q + 2 * fstride + eo, hv);
-    load_row_global<T, NPP>(p.s.B + eo, bb);
+    load_nodes<T, NP, NPP>(q + eo, ks, eta);
+    load_nodes<T, NP, NPP>(q + fstride + eo, ks, hu);
+    load_nodes<T, NP, NPP>(q + 2 * fstride + eo, ks, hv);
+    load_nodes<T, NP, NPP>(p.s.B + eo, ks, bb);
     const T rx = p.s.geo[4 * e], ry = p.s.geo[4 * e + 1], sx = p.s.geo[4 * e + 2], sy = p.s.geo[4 * e + 3];
     T mean[3];
     const int dryf = positivity<T, N>(eta, hu, hv, bb, sops, p.s.Bbar[e], rx, ry, sx, sy, p.ph, &injected, mean);
-    store_row_global<T, NPP>(q + eo, eta);
-    store_row_global<T, NPP>(q + fstride + eo, hu);
-    store_row_global<T, NPP>(q + 2 * fstride + eo, hv);
+    store_nodes<T, NP, NPP>(q + eo, ks, eta);
+    store_nodes<T, NP, NPP>(q + fstride + eo, ks, hu);
+    store_nodes<T, NP, NPP>(q + 2 * fstride + eo, ks, hv);
     p.s.means[4 * (size_t)e + 0] = mean[0];
     p.s.means[4 * (size_t)e + 1] = mean[1];
     p.s.means[4 * (size_t)e + 2] = mean[2];
@@ -630,13 +629,13 @@ __global__ void __launch_bounds__(kBlock) k_tvb(LimitParams<T> p) {
     const int lev = level_of(sc, e);
     const long long a = k >> (lev - 1);
     const int cur = (int)((a + p.post_stage) & 1);
-    const size_t fstride = (size_t)sc.K * NPP, bstride = 3 * fstride, eo = (size_t)e * NPP;
+    const size_t ks = (size_t)sc.KS, fstride = (size_t)NP * ks, bstride = 3 * fstride, eo = (size_t)e;
     T* q = p.s.q + cur * bstride;
     T fld[3][NPP], bb[NPP];
-    load_row_global<T, NPP>(q + eo, fld[0]);
-    load_row_global<T, NPP>(q + fstride + eo, fld[1]);
-    load_row_global<T, NPP>(q + 2 * fstride + eo, fld[2]);
-    load_row_global<T, NPP>(p.s.B + eo, bb);
+    load_nodes<T, NP, NPP>(q + eo, ks, fld[0]);
+    load_nodes<T, NP, NPP>(q + fstride + eo, ks, fld[1]);
+    load_nodes<T, NP, NPP>(q + 2 * fstride + eo, ks, fld[2]);
+    load_nodes<T, NP, NPP>(p.s.B + eo, ks, bb);
     const T rx = p.s.geo[4 * e], ry = p.s.geo[4 * e + 1], sx = p.s.geo[4 * e + 2], sy = p.s.geo[4 * e + 3];
     // element means (eta, hu, hv) as stored by the positivity pass
     const T u0[3] = {p.s.means[4 * (size_t)e], p.s.means[4 * (size_t)e + 1], p.s.means[4 * (size_t)e + 2]};
@@ -773,9 +772,9 @@ __global__ void __launch_bounds__(kBlock) k_tvb(LimitParams<T> p) {
       fld[1][jn] = l0 * vu[0] + l1 * vu[1] + l2 * vu[2];
       fld[2][jn] = l0 * vv[0] + l1 * vv[1] + l2 * vv[2];
     }
-    store_row_global<T, NPP>(q + eo, fld[0]);
-    store_row_global<T, NPP>(q + fstride + eo, fld[1]);
-    store_row_global<T, NPP>(q + 2 * fstride + eo, fld[2]);
+    store_nodes<T, NP, NPP>(q + eo, ks, fld[0]);
+    store_nodes<T, NP, NPP>(q + fstride + eo, ks, fld[1]);
+    store_nodes<T, NP, NPP>(q + 2 * fstride + eo, ks, fld[2]);
   }
 }
 

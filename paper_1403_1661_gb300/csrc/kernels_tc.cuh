@@ -94,62 +94,59 @@ __global__ void __launch_bounds__(kTcBlock, (N <= 4 ? 3 : 2)) k_stage_tc(StagePa
   float* s_geo = sw + SM::GEO;
 
   const Sched& sc = p.sc;
-  const int K = sc.K;
   const long long k = (*p.s.macro) * (1LL << (sc.L - 1)) + p.j;
   const float gg = (float)p.ph.g, h0 = (float)p.ph.h0, hg = 0.5f * gg;
-  const size_t fstride = (size_t)K * NPP, bstride = 3 * fstride;
+  const size_t ks = (size_t)sc.KS, fstride = (size_t)NP * ks, bstride = 3 * fstride;
   double injected = 0.0;
   const int ntiles = (p.nactive + 31) / 32;
 
   for (int tile = blockIdx.x * kTcWarps + warp; tile < ntiles; tile += gridDim.x * kTcWarps) {
-    // ---- load: one element per lane into the warp's shared tiles ----
+    // ---- load: lane = element; each node plane is one coalesced 128-byte line ----
     const int e = tile * 32 + lane;
     const bool valid = e < p.nactive;
     int lev = 1;
     long long a = 0;
-    {
-      float q[4][NPP];
-      if (valid) {
-        lev = level_of(sc, e);
-        a = k >> (lev - 1);
-        const int src = (int)(a & 1);
-        load_row_global<float, NPP>(p.s.q + src * bstride + 0 * fstride + (size_t)e * NPP, q[0]);
-        load_row_global<float, NPP>(p.s.q + src * bstride + 1 * fstride + (size_t)e * NPP, q[1]);
-        load_row_global<float, NPP>(p.s.q + src * bstride + 2 * fstride + (size_t)e * NPP, q[2]);
-        load_row_global<float, NPP>(p.s.B + (size_t)e * NPP, q[3]);
-        const float4 gv = __ldg(reinterpret_cast<const float4*>(p.s.geo) + e);
-        reinterpret_cast<float4*>(s_geo)[lane] = gv;
-      } else {
+    if (valid) {
+      lev = level_of(sc, e);
+      a = k >> (lev - 1);
+      const float* qe = p.s.q + (size_t)(a & 1) * bstride + e;
 #pragma unroll
-        for (int f = 0; f < 4; ++f)
+      for (int f = 0; f < 3; ++f)
 #pragma unroll
-          for (int i = 0; i < NPP; ++i) q[f][i] = 0.f;
-        reinterpret_cast<float4*>(s_geo)[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
+        for (int i = 0; i < NP; ++i) s_state[(f * KP + i) * LS + lane] = __ldg(qe + f * fstride + i * ks);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) s_state[(3 * KP + i) * LS + lane] = __ldg(p.s.B + e + i * ks);
+      reinterpret_cast<float4*>(s_geo)[lane] = __ldg(reinterpret_cast<const float4*>(p.s.geo) + e);
+    } else {
 #pragma unroll
       for (int f = 0; f < 4; ++f)
 #pragma unroll
-        for (int i = 0; i < KP; ++i) s_state[(f * KP + i) * LS + lane] = i < NPP ? q[f][i] : 0.f;
+        for (int i = 0; i < NP; ++i) s_state[(f * KP + i) * LS + lane] = 0.f;
+      reinterpret_cast<float4*>(s_geo)[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int i = NP; i < KP; ++i) s_state[(f * KP + i) * LS + lane] = 0.f;
     __syncwarp();
 
-    // the next tile's rows and this element's older R slots start moving now
+    // the next tile's planes and this tile's older R slots start moving now: one
+    // 128-byte line per lane and plane (the parity of the first element stands for
+    // the tile; these are hints, every address lies inside its array)
     {
-      const int en = e + gridDim.x * kTcWarps * 32;
-      if (en < p.nactive) {
-        const long long an = k >> (level_of(sc, en) - 1);
-        const float* qn = p.s.q + (size_t)(an & 1) * bstride + (size_t)en * NPP;
-        prefetch_l2(qn);
-        prefetch_l2(qn + fstride);
-        prefetch_l2(qn + 2 * fstride);
-        prefetch_l2(p.s.B + (size_t)en * NPP);
+      const int e0n = (tile + gridDim.x * kTcWarps) * 32;
+      if (e0n < p.nactive) {
+        const long long an = k >> (level_of(sc, e0n) - 1);
+        const float* qn = p.s.q + (size_t)(an & 1) * bstride + e0n;
+        for (int pl = lane; pl < 4 * NP; pl += 32)
+          prefetch_l2(pl < 3 * NP ? qn + pl * ks : p.s.B + e0n + (pl - 3 * NP) * ks);
       }
-      if (valid && p.mode == 0) {
-        for (int s = 1; s < 3 && s <= a; ++s) {
-          const float* rs = p.s.ring + (size_t)((a - s) % 3) * bstride + (size_t)e * NPP;
-          prefetch_l2(rs);
-          prefetch_l2(rs + fstride);
-          prefetch_l2(rs + 2 * fstride);
+      const long long a0 = __shfl_sync(0xffffffffu, a, 0);
+      if (p.mode == 0) {
+        const int e0 = tile * 32;
+        for (int s = 1; s < 3 && s <= a0; ++s) {
+          const float* rs = p.s.ring + (size_t)((a0 - s) % 3) * bstride + e0;
+          for (int pl = lane; pl < 3 * NP; pl += 32) prefetch_l2(rs + pl * ks);
         }
       }
     }
@@ -320,7 +317,7 @@ __global__ void __launch_bounds__(kTcBlock, (N <= 4 ? 3 : 2)) k_stage_tc(StagePa
       // state is read from the warp's shared tile when the surface term needs it
       const float* my = s_state + lane;
       auto own = [&](int f, int jn) -> float { return my[(f * KP + jn) * LS]; };
-      surface_lift<float, N>(p, sops, e, k, own, ge.x, ge.y, ge.z, ge.w, R0, R1, R2);
+      surface_lift<float, N, true>(p, sops, e, k, own, ge.x, ge.y, ge.z, ge.w, R0, R1, R2);
       float eta[NPP], hu[NPP], hv[NPP], bb[NPP];
 #pragma unroll
       for (int i = 0; i < NPP; ++i) {

@@ -44,6 +44,11 @@ int npp_of(int N) {
   return (np + 3) / 4 * 4;
 }
 
+int np_of(int N) { return (N + 1) * (N + 2) / 2; }
+
+// element stride of the node-major planes: whole 128-byte lines per 32 elements
+int ks_of(int K) { return (K + 31) / 32 * 32; }
+
 struct Layout {
   size_t q, ring, B, geo, conn, tvbg, means, dry, Bbar, ops, tcops, perm, acc, flags, macro, partials, total;
   int nb_stats;
@@ -53,16 +58,16 @@ int tc_size_of(int N);
 
 Layout make_layout(int K, int N, size_t ts, int op_size) {
   Layout L;
-  const size_t npp = (size_t)npp_of(N);
+  const size_t plane = (size_t)np_of(N) * (size_t)ks_of(K);   // one field, all nodes
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
     off = align256(off + bytes);
     return o;
   };
-  L.q = take(2 * 3 * (size_t)K * npp * ts);
-  L.ring = take(3 * 3 * (size_t)K * npp * ts);
-  L.B = take((size_t)K * npp * ts);
+  L.q = take(2 * 3 * plane * ts);
+  L.ring = take(3 * 3 * plane * ts);
+  L.B = take(plane * ts);
   L.geo = take((size_t)K * 4 * ts);
   L.conn = take((size_t)K * 16);
   L.tvbg = take((size_t)K * 8 * ts);
@@ -105,6 +110,7 @@ struct swe_solver {
   swe_params prm;
   swe::RefElem ref;
   int N = 0, K = 0, Np = 0, NPP = 0;
+  int KS = 0;                    // element stride of the device node planes
   bool fp64 = false;
   bool tc = false;   // FP32 with tensor-core volume contractions
   size_t ts = 4;
@@ -172,6 +178,7 @@ swe::Sched sched_of(const swe_solver* s) {
   swe::Sched sc;
   std::memset(&sc, 0, sizeof(sc));
   sc.K = s->K;
+  sc.KS = s->KS;
   sc.L = s->L;
   for (int l = 0; l <= s->L; ++l) sc.off[l] = s->off[l];
   for (int l = s->L + 1; l <= swe::kMaxLevels; ++l) sc.off[l] = s->K;
@@ -341,7 +348,7 @@ int upload_ops_t(swe_solver* s) {
 // stencil, bathymetry, permutation).
 template <typename T>
 int upload_mesh_t(swe_solver* s) {
-  const int K = s->K, npp = s->NPP;
+  const int K = s->K, KS = s->KS;
   const swe::Mesh& m = s->mesh;
   std::vector<double> alpha, beta;
   std::vector<int32_t> jsel;
@@ -372,14 +379,14 @@ int upload_mesh_t(swe_solver* s) {
   if ((rc = upload(s, s->lay.tvbg, tvbg.data(), tvbg.size() * sizeof(T)))) return rc;
   if ((rc = upload(s, s->lay.perm, s->perm.data(), (size_t)K * 4))) return rc;
   if (s->have_B) {
-    std::vector<T> b((size_t)K * npp, T(0));
+    std::vector<T> b((size_t)s->Np * KS, T(0));
     std::vector<double> bbar(K, 0.0);
     for (int e = 0; e < K; ++e) {
       const int c = s->perm[e];
       double acc = 0.0;
       for (int j = 0; j < s->Np; ++j) {
         const T v = (T)s->B_in[(size_t)c * s->Np + j];
-        b[(size_t)e * npp + j] = v;
+        b[(size_t)j * KS + e] = v;
         acc += s->ref.mean_w[j] * (double)v;
       }
       bbar[e] = acc;
@@ -430,15 +437,16 @@ int reset_counters(swe_solver* s) {
 
 template <typename T>
 int upload_state_t(swe_solver* s, const double* h, const double* hu, const double* hv) {
-  const int K = s->K, npp = s->NPP, np = s->Np;
-  std::vector<T> q(3 * (size_t)K * npp, T(0));
+  const int K = s->K, KS = s->KS, np = s->Np;
+  const size_t fs = (size_t)np * KS;
+  std::vector<T> q(3 * fs, T(0));
   for (int e = 0; e < K; ++e) {
     const int c = s->perm[e];
     for (int j = 0; j < np; ++j) {
-      const size_t ci = (size_t)c * np + j;
-      q[(size_t)e * npp + j] = (T)(h[ci] + s->B_in[ci]);
-      q[(size_t)K * npp + (size_t)e * npp + j] = (T)hu[ci];
-      q[2 * (size_t)K * npp + (size_t)e * npp + j] = (T)hv[ci];
+      const size_t ci = (size_t)c * np + j, di = (size_t)j * KS + e;
+      q[di] = (T)(h[ci] + s->B_in[ci]);
+      q[fs + di] = (T)hu[ci];
+      q[2 * fs + di] = (T)hv[ci];
     }
   }
   int rc = upload(s, s->lay.q, q.data(), q.size() * sizeof(T));
@@ -567,19 +575,19 @@ bool synchronous(const swe_solver* s) { return (s->k % (1LL << (s->L - 1))) == 0
 
 template <typename T>
 int download_state_t(const swe_solver* s, double* h, double* hu, double* hv) {
-  const int K = s->K, npp = s->NPP, np = s->Np;
-  std::vector<T> q(2 * 3 * (size_t)K * npp);
+  const int K = s->K, KS = s->KS, np = s->Np;
+  const size_t fs = (size_t)np * KS, bs = 3 * fs;
+  std::vector<T> q(2 * bs);
   SWE_CUDA(cudaMemcpyAsync(q.data(), s->ws + s->lay.q, q.size() * sizeof(T), cudaMemcpyDeviceToHost,
                            s->stream));
   SWE_CUDA(cudaStreamSynchronize(s->stream));
-  const size_t fs = (size_t)K * npp, bs = 3 * fs;
   for (int e = 0; e < K; ++e) {
     const int c = s->perm[e];
     int l = 1;
     while (l < s->L && e >= s->off[l]) ++l;
     const int cur = (int)((s->k >> (l - 1)) & 1);
     for (int j = 0; j < np; ++j) {
-      const size_t ci = (size_t)c * np + j, di = (size_t)cur * bs + (size_t)e * npp + j;
+      const size_t ci = (size_t)c * np + j, di = (size_t)cur * bs + (size_t)j * KS + e;
       if (h) h[ci] = (double)q[di] - s->B_dev[ci];
       if (hu) hu[ci] = (double)q[di + fs];
       if (hv) hv[ci] = (double)q[di + 2 * fs];
@@ -592,39 +600,39 @@ int download_state(const swe_solver* s, double* h, double* hu, double* hv) {
   return s->fp64 ? download_state_t<double>(s, h, hu, hv) : download_state_t<float>(s, h, hu, hv);
 }
 
-// current state in device precision, caller order, [3][K][NPP] (no conversion)
+// current state in device precision, caller order, [3][K][Np] (no conversion)
 template <typename T>
 int download_raw_t(const swe_solver* s, std::vector<char>& raw) {
-  const int K = s->K, npp = s->NPP;
-  std::vector<T> q(2 * 3 * (size_t)K * npp);
+  const int K = s->K, KS = s->KS, np = s->Np;
+  const size_t fs = (size_t)np * KS, bs = 3 * fs, cs = (size_t)K * np;
+  std::vector<T> q(2 * bs);
   SWE_CUDA(cudaMemcpyAsync(q.data(), s->ws + s->lay.q, q.size() * sizeof(T), cudaMemcpyDeviceToHost,
                            s->stream));
   SWE_CUDA(cudaStreamSynchronize(s->stream));
-  raw.assign(3 * (size_t)K * npp * sizeof(T), 0);
+  raw.assign(3 * cs * sizeof(T), 0);
   T* out = reinterpret_cast<T*>(raw.data());
-  const size_t fs = (size_t)K * npp, bs = 3 * fs;
   for (int e = 0; e < K; ++e) {
     const int c = s->perm[e];
     int l = 1;
     while (l < s->L && e >= s->off[l]) ++l;
     const int cur = (int)((s->k >> (l - 1)) & 1);
     for (int f = 0; f < 3; ++f)
-      std::memcpy(out + f * fs + (size_t)c * npp, q.data() + cur * bs + f * fs + (size_t)e * npp,
-                  npp * sizeof(T));
+      for (int j = 0; j < np; ++j)
+        out[f * cs + (size_t)c * np + j] = q[cur * bs + f * fs + (size_t)j * KS + e];
   }
   return SWE_OK;
 }
 
 template <typename T>
 int upload_raw_t(swe_solver* s, const std::vector<char>& raw) {
-  const int K = s->K, npp = s->NPP;
+  const int K = s->K, KS = s->KS, np = s->Np;
   const T* in = reinterpret_cast<const T*>(raw.data());
-  std::vector<T> q(3 * (size_t)K * npp);
-  const size_t fs = (size_t)K * npp;
+  const size_t fs = (size_t)np * KS, cs = (size_t)K * np;
+  std::vector<T> q(3 * fs, T(0));
   for (int e = 0; e < K; ++e) {
     const int c = s->perm[e];
     for (int f = 0; f < 3; ++f)
-      std::memcpy(q.data() + f * fs + (size_t)e * npp, in + f * fs + (size_t)c * npp, npp * sizeof(T));
+      for (int j = 0; j < np; ++j) q[f * fs + (size_t)j * KS + e] = in[f * cs + (size_t)c * np + j];
   }
   int rc = upload(s, s->lay.q, q.data(), q.size() * sizeof(T));
   if (rc) return rc;
@@ -820,6 +828,7 @@ int swe_solver_create(const swe_mesh* mesh, const swe_params* params, void* dev_
   s->ref = swe::RefElem::build(s->N);
   s->Np = s->ref.Np;
   s->NPP = npp_of(s->N);
+  s->KS = ks_of(s->K);
   s->fp64 = params->precision == SWE_FP64;
   s->tc = params->precision == SWE_FP32_TC;
   s->ts = s->fp64 ? 8 : 4;
@@ -1070,7 +1079,7 @@ struct CkptHeader {
 
 int swe_full_state_bytes(const swe_solver* s, size_t* bytes) {
   if (!s || !bytes) return fail(SWE_EINVAL, "NULL argument");
-  const size_t qb = 2 * 3 * (size_t)s->K * s->NPP * s->ts, rb = 3 * qb / 2;
+  const size_t qb = 2 * 3 * (size_t)s->Np * s->KS * s->ts, rb = 3 * qb / 2;
   *bytes = sizeof(CkptHeader) + (size_t)s->K * 4 + qb + rb + (size_t)s->K * 4 * s->ts + s->K + 64 + 8;
   return SWE_OK;
 }
@@ -1086,7 +1095,7 @@ int swe_get_full_state(const swe_solver* s, void* host_buf, size_t bytes) {
   std::memcpy(h.magic, "SWEGB300", 8);
   h.K = s->K; h.N = s->N; h.precision = s->prm.precision; h.L = s->L;
   h.k = s->k; h.dof_updates = s->dof_updates; h.t0 = s->t0; h.dt_min = s->dt_min;
-  h.bytes_q = 2 * 3 * (uint64_t)s->K * s->NPP * s->ts;
+  h.bytes_q = 2 * 3 * (uint64_t)s->Np * s->KS * s->ts;
   h.bytes_ring = 3 * h.bytes_q / 2;
   h.bytes_means = (uint64_t)s->K * 4 * s->ts;
   h.bytes_dry = s->K;
