@@ -68,7 +68,7 @@ struct TcSmem {
 };
 
 template <int N>
-__global__ void __launch_bounds__(kTcBlock, (N <= 4 ? 3 : 2)) k_stage_tc(StageParams<float> p) {
+__global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) {
   using D = Dims<N>;
   using C = TcDims<N>;
   using TL = TcLayout<N>;
