@@ -75,9 +75,13 @@ template <typename T>
 struct DevState {
   T* q;                 // [2][3][NP][KS] double-buffered (eta, hu, hv)
   T* ring;              // [3][3][NP][KS] Adams-Bashforth history of R
+  T* qmid;              // [K][3][NPP] state at the middle of the element's current step,
+                        // element-major records (written only by elements with a finer
+                        // neighbour, so each writer fills whole sectors)
   const T* B;           // [NP][KS]
   const T* geo;         // [K][4] rx, ry, sx, sy
-  const int4* conn;     // [K] neighbour across faces 0,1,2 (-1: wall); .w packs faces/stencil
+  const int4* conn;     // [K] neighbour across faces 0,1,2 (-1: wall); .w packs neighbour faces
+                        // (bits 0-5), TVB stencil (6-11) and "has a finer neighbour" (12)
   const T* tvbg;        // [K][8] alpha_i, beta_i (i = 0..2)
   T* means;             // [K][4] element means (eta, hu, hv)
   uint8_t* dry;         // [K] dry flag of the latest positivity pass

@@ -318,16 +318,21 @@ __device__ __forceinline__ void surface_lift(const StageParams<T>& p, const T* _
       const long long an = k >> (ln - 1);
       const long long pern = 1LL << (ln - 1);
       const long long phase = k & (pern - 1);
-      const T* qn = p.s.q + (size_t)(an & 1) * bstride + nb;
+      // A neighbour one level coarser is always half-way through its step here; it
+      // wrote that half-step Adams-Bashforth state at its own commit.
+      const bool half = 2 * phase == pern;
+      const T* qn = half ? p.s.qmid + (size_t)nb * 3 * NPP : p.s.q + (size_t)(an & 1) * bstride + nb;
+      const size_t sn = half ? 1 : ks, sf = half ? (size_t)NPP : fstride;   // node, field strides
 #pragma unroll
       for (int m = 0; m < NFP; ++m) {
-        const size_t idx = (size_t)face_node_rt(N, fn, NFP - 1 - m) * ks;
+        const int jn = face_node_rt(N, fn, NFP - 1 - m);
+        const size_t idx = (size_t)jn * sn;
         ne[m] = __ldg(qn + idx);
-        nu[m] = __ldg(qn + fstride + idx);
-        nv[m] = __ldg(qn + 2 * fstride + idx);
-        nB[m] = __ldg(p.s.B + nb + idx);
+        nu[m] = __ldg(qn + sf + idx);
+        nv[m] = __ldg(qn + 2 * sf + idx);
+        nB[m] = __ldg(p.s.B + nb + (size_t)jn * ks);
       }
-      if (phase != 0) {  // neighbour between its steps: Adams-Bashforth polynomial at t_k
+      if (phase != 0 && !half) {  // other fractions: Adams-Bashforth polynomial at t_k
         const int depth = an + 1 < 3 ? (int)(an + 1) : 3;
         T w[3];
         ab_partial_weights<T>(depth, (T)phase / (T)pern, w);
@@ -434,21 +439,49 @@ __device__ __forceinline__ void commit_and_limit(const StageParams<T>& p, const 
   store_nodes<T, NP, NP>(ring + (size_t)(a % 3) * bstride + 0 * fstride + eo, ks, R0);
   store_nodes<T, NP, NP>(ring + (size_t)(a % 3) * bstride + 1 * fstride + eo, ks, R1);
   store_nodes<T, NP, NP>(ring + (size_t)(a % 3) * bstride + 2 * fstride + eo, ks, R2);
+  // The same pass over the older R slots also gives the Adams-Bashforth
+  // polynomial of this step at its middle, q(t_a + dt/2) = q + dt sum_s w_s(1/2)
+  // R^(a-s) (Section 4), which an element with a finer neighbour stores for that
+  // neighbour's next substep.
+  T wh[3];
+  ab_partial_weights<T>(depth, T(0.5), wh);
+  const T m0 = dtl * wh[0], m1 = dtl * wh[1], m2 = dtl * wh[2];
+  T x0[NP], x1[NP], x2[NP];
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
+    x0[i] = eta[i] + m0 * R0[i];
+    x1[i] = hu[i] + m0 * R1[i];
+    x2[i] = hv[i] + m0 * R2[i];
     eta[i] += c0 * R0[i];
     hu[i] += c0 * R1[i];
     hv[i] += c0 * R2[i];
   }
   for (int s = 1; s < depth; ++s) {
-    const T cs = s == 1 ? c1 : c2;
+    const T cs = s == 1 ? c1 : c2, ms = s == 1 ? m1 : m2;
     const T* rs = ring + (size_t)((a - s) % 3) * bstride + eo;
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-      eta[i] += cs * __ldg(rs + i * ks);
-      hu[i] += cs * __ldg(rs + fstride + i * ks);
-      hv[i] += cs * __ldg(rs + 2 * fstride + i * ks);
+      const T r0 = __ldg(rs + i * ks), r1 = __ldg(rs + fstride + i * ks), r2 = __ldg(rs + 2 * fstride + i * ks);
+      eta[i] += cs * r0;
+      hu[i] += cs * r1;
+      hv[i] += cs * r2;
+      x0[i] += ms * r0;
+      x1[i] += ms * r1;
+      x2[i] += ms * r2;
     }
+  }
+  if ((__ldg(reinterpret_cast<const int*>(p.s.conn + e) + 3) >> 12) & 1) {
+    T* qm = p.s.qmid + eo * 3 * NPP;
+    T row[NPP];
+#pragma unroll
+    for (int i = 0; i < NPP; ++i) row[i] = i < NP ? x0[i] : T(0);
+    store_row_global<T, NPP>(qm, row);
+#pragma unroll
+    for (int i = 0; i < NPP; ++i) row[i] = i < NP ? x1[i] : T(0);
+    store_row_global<T, NPP>(qm + NPP, row);
+#pragma unroll
+    for (int i = 0; i < NPP; ++i) row[i] = i < NP ? x2[i] : T(0);
+    store_row_global<T, NPP>(qm + 2 * NPP, row);
   }
 
   // ---- positivity limiter (Algorithm 3) and means ----

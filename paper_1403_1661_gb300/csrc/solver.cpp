@@ -50,7 +50,7 @@ int np_of(int N) { return (N + 1) * (N + 2) / 2; }
 int ks_of(int K) { return (K + 31) / 32 * 32; }
 
 struct Layout {
-  size_t q, ring, B, geo, conn, tvbg, means, dry, Bbar, ops, tcops, perm, acc, flags, macro, partials, total;
+  size_t q, ring, qmid, B, geo, conn, tvbg, means, dry, Bbar, ops, tcops, perm, acc, flags, macro, partials, total;
   int nb_stats;
 };
 
@@ -67,6 +67,7 @@ Layout make_layout(int K, int N, size_t ts, int op_size) {
   };
   L.q = take(2 * 3 * plane * ts);
   L.ring = take(3 * 3 * plane * ts);
+  L.qmid = take((size_t)K * 3 * npp_of(N) * ts);
   L.B = take(plane * ts);
   L.geo = take((size_t)K * 4 * ts);
   L.conn = take((size_t)K * 16);
@@ -159,6 +160,7 @@ swe::DevState<T> dev_state(swe_solver* s) {
   char* w = s->ws;
   d.q = reinterpret_cast<T*>(w + s->lay.q);
   d.ring = reinterpret_cast<T*>(w + s->lay.ring);
+  d.qmid = reinterpret_cast<T*>(w + s->lay.qmid);
   d.B = reinterpret_cast<const T*>(w + s->lay.B);
   d.geo = reinterpret_cast<const T*>(w + s->lay.geo);
   d.conn = reinterpret_cast<const int4*>(w + s->lay.conn);
@@ -364,6 +366,7 @@ int upload_mesh_t(swe_solver* s) {
     int w = 0;
     for (int f = 0; f < 3; ++f) {
       const int nb = m.EToE[3 * (size_t)c + f];
+      if (nb >= 0 && s->level[nb] < s->level[c]) w |= 1 << 12;   // a finer neighbour reads qmid
       conn[4 * (size_t)e + f] = nb >= 0 ? s->iperm[nb] : -1;
       const int fn = nb >= 0 ? m.EToF[3 * (size_t)c + f] : 0;
       w |= (fn & 3) << (2 * f);
@@ -1073,14 +1076,15 @@ struct CkptHeader {
   int32_t K, N, precision, L;
   int64_t k, dof_updates;
   double t0, dt_min;
-  uint64_t bytes_q, bytes_ring, bytes_means, bytes_dry;
+  uint64_t bytes_q, bytes_ring, bytes_qmid, bytes_means, bytes_dry;
 };
 }  // namespace
 
 int swe_full_state_bytes(const swe_solver* s, size_t* bytes) {
   if (!s || !bytes) return fail(SWE_EINVAL, "NULL argument");
   const size_t qb = 2 * 3 * (size_t)s->Np * s->KS * s->ts, rb = 3 * qb / 2;
-  *bytes = sizeof(CkptHeader) + (size_t)s->K * 4 + qb + rb + (size_t)s->K * 4 * s->ts + s->K + 64 + 8;
+  const size_t mb = (size_t)s->K * 3 * s->NPP * s->ts;
+  *bytes = sizeof(CkptHeader) + (size_t)s->K * 4 + qb + rb + mb + (size_t)s->K * 4 * s->ts + s->K + 64 + 8;
   return SWE_OK;
 }
 
@@ -1097,6 +1101,7 @@ int swe_get_full_state(const swe_solver* s, void* host_buf, size_t bytes) {
   h.k = s->k; h.dof_updates = s->dof_updates; h.t0 = s->t0; h.dt_min = s->dt_min;
   h.bytes_q = 2 * 3 * (uint64_t)s->Np * s->KS * s->ts;
   h.bytes_ring = 3 * h.bytes_q / 2;
+  h.bytes_qmid = (uint64_t)s->K * 3 * s->NPP * s->ts;
   h.bytes_means = (uint64_t)s->K * 4 * s->ts;
   h.bytes_dry = s->K;
   char* p = reinterpret_cast<char*>(host_buf);
@@ -1105,6 +1110,7 @@ int swe_get_full_state(const swe_solver* s, void* host_buf, size_t bytes) {
   cudaStream_t st = s->stream;
   SWE_CUDA(cudaMemcpyAsync(p, s->ws + s->lay.q, h.bytes_q, cudaMemcpyDeviceToHost, st)); p += h.bytes_q;
   SWE_CUDA(cudaMemcpyAsync(p, s->ws + s->lay.ring, h.bytes_ring, cudaMemcpyDeviceToHost, st)); p += h.bytes_ring;
+  SWE_CUDA(cudaMemcpyAsync(p, s->ws + s->lay.qmid, h.bytes_qmid, cudaMemcpyDeviceToHost, st)); p += h.bytes_qmid;
   SWE_CUDA(cudaMemcpyAsync(p, s->ws + s->lay.means, h.bytes_means, cudaMemcpyDeviceToHost, st)); p += h.bytes_means;
   SWE_CUDA(cudaMemcpyAsync(p, s->ws + s->lay.dry, h.bytes_dry, cudaMemcpyDeviceToHost, st)); p += h.bytes_dry;
   SWE_CUDA(cudaMemcpyAsync(p, s->ws + s->lay.acc, 64, cudaMemcpyDeviceToHost, st)); p += 64;
@@ -1131,6 +1137,7 @@ int swe_set_full_state(swe_solver* s, const void* host_buf, size_t bytes) {
   cudaStream_t st = s->stream;
   SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.q, p, h.bytes_q, cudaMemcpyHostToDevice, st)); p += h.bytes_q;
   SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.ring, p, h.bytes_ring, cudaMemcpyHostToDevice, st)); p += h.bytes_ring;
+  SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.qmid, p, h.bytes_qmid, cudaMemcpyHostToDevice, st)); p += h.bytes_qmid;
   SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.means, p, h.bytes_means, cudaMemcpyHostToDevice, st)); p += h.bytes_means;
   SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.dry, p, h.bytes_dry, cudaMemcpyHostToDevice, st)); p += h.bytes_dry;
   SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.acc, p, 64, cudaMemcpyHostToDevice, st)); p += 64;
