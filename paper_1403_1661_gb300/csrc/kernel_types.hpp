@@ -79,6 +79,8 @@ struct DevState {
                         // element-major records (written only by elements with a finer
                         // neighbour, so each writer fills whole sectors)
   const T* B;           // [NP][KS]
+  T* p1;                // [3][3][KS] vertex values of Pi1 (eta, hu, hv) after each commit
+  const T* vb;          // [3][KS] vertex values of Pi1 B (static)
   const T* geo;         // [K][4] rx, ry, sx, sy
   const int4* conn;     // [K] neighbour across faces 0,1,2 (-1: wall); .w packs neighbour faces
                         // (bits 0-5), TVB stencil (6-11) and "has a finer neighbour" (12)

@@ -279,6 +279,30 @@ __device__ __forceinline__ int positivity(T (&eta)[Dims<N>::NPP], T (&hu)[Dims<N
   return 0;
 }
 
+// Vertex values of Pi1 (eta, hu, hv) for the TVB limiter (Section 5.3), stored
+// as planes p1[(3 field + vertex) * KS + e] by whoever last committed the state.
+template <typename T, int N>
+__device__ __forceinline__ void store_p1(T* __restrict__ p1, size_t ks, const T* __restrict__ sops,
+                                         const T (&eta)[Dims<N>::NPP], const T (&hu)[Dims<N>::NPP],
+                                         const T (&hv)[Dims<N>::NPP]) {
+  using D = Dims<N>;
+  const T* t1 = sops + OpLayout<N>::T1;
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    T s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+    for (int jn = 0; jn < D::NP; ++jn) {
+      const T w = t1[v * D::NPP + jn];
+      s0 += w * eta[jn];
+      s1 += w * hu[jn];
+      s2 += w * hv[jn];
+    }
+    p1[(0 + v) * ks] = s0;
+    p1[(3 + v) * ks] = s1;
+    p1[(6 + v) * ks] = s2;
+  }
+}
+
 // Surface term (Section 7.2) for element e: traces at the Gauss points of its
 // three faces, the well-balanced flux, and the lift subtracted from R (in
 // registers). own(f, j) returns the element's own field f (eta, hu, hv, B) at
@@ -497,6 +521,7 @@ __device__ __forceinline__ void commit_and_limit(const StageParams<T>& p, const 
   p.s.means[4 * (size_t)e + 1] = mean[1];
   p.s.means[4 * (size_t)e + 2] = mean[2];
   p.s.dry[e] = (uint8_t)dryf;
+  store_p1<T, N>(p.s.p1 + eo, ks, sops, eta, hu, hv);
 }
 
 // --------------------------------------------------------------------------
@@ -614,6 +639,7 @@ __global__ void __launch_bounds__(kBlock) k_positivity(LimitParams<T> p) {
     store_nodes<T, NP, NPP>(q + eo, ks, eta);
     store_nodes<T, NP, NPP>(q + fstride + eo, ks, hu);
     store_nodes<T, NP, NPP>(q + 2 * fstride + eo, ks, hv);
+    store_p1<T, N>(p.s.p1 + eo, ks, sops, eta, hu, hv);
     p.s.means[4 * (size_t)e + 0] = mean[0];
     p.s.means[4 * (size_t)e + 1] = mean[1];
     p.s.means[4 * (size_t)e + 2] = mean[2];
@@ -664,29 +690,18 @@ __global__ void __launch_bounds__(kBlock) k_tvb(LimitParams<T> p) {
     const int cur = (int)((a + p.post_stage) & 1);
     const size_t ks = (size_t)sc.KS, fstride = (size_t)NP * ks, bstride = 3 * fstride, eo = (size_t)e;
     T* q = p.s.q + cur * bstride;
-    T fld[3][NPP], bb[NPP];
-    load_nodes<T, NP, NPP>(q + eo, ks, fld[0]);
-    load_nodes<T, NP, NPP>(q + fstride + eo, ks, fld[1]);
-    load_nodes<T, NP, NPP>(q + 2 * fstride + eo, ks, fld[2]);
-    load_nodes<T, NP, NPP>(p.s.B + eo, ks, bb);
     const T rx = p.s.geo[4 * e], ry = p.s.geo[4 * e + 1], sx = p.s.geo[4 * e + 2], sy = p.s.geo[4 * e + 3];
     // element means (eta, hu, hv) as stored by the positivity pass
     const T u0[3] = {p.s.means[4 * (size_t)e], p.s.means[4 * (size_t)e + 1], p.s.means[4 * (size_t)e + 2]};
-    // P1 part: vertex values of Pi1 q for eta, hu, hv and B
-    const T* t1 = sops + O::T1;
+    // P1 part: vertex values of Pi1 q for eta, hu, hv (stored with the committed
+    // state) and of Pi1 B (static)
     T vq[3][3], vb[3];
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
-      T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-#pragma unroll
-      for (int jn = 0; jn < NP; ++jn) {
-        const T w = t1[v * NPP + jn];
-        s0 += w * fld[0][jn];
-        s1 += w * fld[1][jn];
-        s2 += w * fld[2][jn];
-        s3 += w * bb[jn];
-      }
-      vq[0][v] = s0; vq[1][v] = s1; vq[2][v] = s2; vb[v] = s3;
+      vq[0][v] = p.s.p1[(0 + v) * ks + eo];
+      vq[1][v] = p.s.p1[(3 + v) * ks + eo];
+      vq[2][v] = p.s.p1[(6 + v) * ks + eo];
+      vb[v] = __ldg(p.s.vb + v * ks + eo);
     }
     // neighbour means; a wall face mirrors the normal momentum of the own mean
     T un[3][3];
@@ -798,6 +813,8 @@ __global__ void __launch_bounds__(kBlock) k_tvb(LimitParams<T> p) {
     vv[1] = u0[2] + dl[1][2] + dl[0][2] - dl[2][2];
     vv[2] = u0[2] + dl[2][2] + dl[1][2] - dl[0][2];
     const T* bary = sops + O::BARY;
+    T fld[3][NPP], bb[NPP];
+    load_nodes<T, NP, NPP>(p.s.B + eo, ks, bb);
 #pragma unroll
     for (int jn = 0; jn < NP; ++jn) {
       const T l0 = bary[4 * jn], l1 = bary[4 * jn + 1], l2 = bary[4 * jn + 2];

@@ -50,7 +50,7 @@ int np_of(int N) { return (N + 1) * (N + 2) / 2; }
 int ks_of(int K) { return (K + 31) / 32 * 32; }
 
 struct Layout {
-  size_t q, ring, qmid, B, geo, conn, tvbg, means, dry, Bbar, ops, tcops, perm, acc, flags, macro, partials, total;
+  size_t q, ring, qmid, B, p1, vb, geo, conn, tvbg, means, dry, Bbar, ops, tcops, perm, acc, flags, macro, partials, total;
   int nb_stats;
 };
 
@@ -69,6 +69,8 @@ Layout make_layout(int K, int N, size_t ts, int op_size) {
   L.ring = take(3 * 3 * plane * ts);
   L.qmid = take((size_t)K * 3 * npp_of(N) * ts);
   L.B = take(plane * ts);
+  L.p1 = take(9 * (size_t)ks_of(K) * ts);
+  L.vb = take(3 * (size_t)ks_of(K) * ts);
   L.geo = take((size_t)K * 4 * ts);
   L.conn = take((size_t)K * 16);
   L.tvbg = take((size_t)K * 8 * ts);
@@ -161,6 +163,8 @@ swe::DevState<T> dev_state(swe_solver* s) {
   d.q = reinterpret_cast<T*>(w + s->lay.q);
   d.ring = reinterpret_cast<T*>(w + s->lay.ring);
   d.qmid = reinterpret_cast<T*>(w + s->lay.qmid);
+  d.p1 = reinterpret_cast<T*>(w + s->lay.p1);
+  d.vb = reinterpret_cast<const T*>(w + s->lay.vb);
   d.B = reinterpret_cast<const T*>(w + s->lay.B);
   d.geo = reinterpret_cast<const T*>(w + s->lay.geo);
   d.conn = reinterpret_cast<const int4*>(w + s->lay.conn);
@@ -382,19 +386,22 @@ int upload_mesh_t(swe_solver* s) {
   if ((rc = upload(s, s->lay.tvbg, tvbg.data(), tvbg.size() * sizeof(T)))) return rc;
   if ((rc = upload(s, s->lay.perm, s->perm.data(), (size_t)K * 4))) return rc;
   if (s->have_B) {
-    std::vector<T> b((size_t)s->Np * KS, T(0));
+    std::vector<T> b((size_t)s->Np * KS, T(0)), vb(3 * (size_t)KS, T(0));
     std::vector<double> bbar(K, 0.0);
     for (int e = 0; e < K; ++e) {
       const int c = s->perm[e];
-      double acc = 0.0;
+      double acc = 0.0, v1[3] = {0.0, 0.0, 0.0};
       for (int j = 0; j < s->Np; ++j) {
         const T v = (T)s->B_in[(size_t)c * s->Np + j];
         b[(size_t)j * KS + e] = v;
         acc += s->ref.mean_w[j] * (double)v;
+        for (int t = 0; t < 3; ++t) v1[t] += s->ref.T1[(size_t)t * s->Np + j] * (double)v;
       }
       bbar[e] = acc;
+      for (int t = 0; t < 3; ++t) vb[(size_t)t * KS + e] = (T)v1[t];
     }
     if ((rc = upload(s, s->lay.B, b.data(), b.size() * sizeof(T)))) return rc;
+    if ((rc = upload(s, s->lay.vb, vb.data(), vb.size() * sizeof(T)))) return rc;
     if ((rc = upload(s, s->lay.Bbar, bbar.data(), bbar.size() * 8))) return rc;
     SWE_CUDA(cudaStreamSynchronize(s->stream));
   }
