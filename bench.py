@@ -124,10 +124,11 @@ class ClockSampler:
 def stage_bytes_per_element(N, ts):
     """Algorithmic HBM bytes one element moves in the stage kernel: read Q (3Np),
     B (Np), two older R slots (6Np), geometry (4) and connectivity (4 words);
-    write R (3Np), Q (3Np), means (3) and the dry byte. Neighbour traces are
-    counted as L2 hits."""
+    write R (3Np), Q (3Np), means (3), the P1 vertex values the TVB limiter reads
+    (9) and the dry byte. Neighbour traces are counted as L2 hits; the half-step
+    records of elements with a finer neighbour are not counted."""
     Np = (N + 1) * (N + 2) // 2
-    return (16 * Np + 4 + 3) * ts + 4 * 4 + 1
+    return (16 * Np + 4 + 3 + 9) * ts + 4 * 4 + 1
 
 
 def measured_peaks():
