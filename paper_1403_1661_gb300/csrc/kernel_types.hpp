@@ -45,7 +45,9 @@ struct OpLayout {
 // Tensor-core tiling of the volume contractions (mma.sync, bf16 operands).
 //   KP   node dimension padded to the k16 step of the interpolation
 //   CT   cubature points in tiles of 8 (n of the interpolation, k of the projection)
-//   NT   nodes in tiles of 8 (n of the projection)
+//   NT   nodes in tiles of 8 (n of the projection and of the lift)
+//   KF   the 3 Ng face Gauss points padded to the k8 step of the lift; KT = KF / 8
+//   FR   rows per field of the shared flux / R tile, max(KF, NPT)
 template <int N>
 struct TcDims {
   using D = Dims<N>;
@@ -54,17 +56,22 @@ struct TcDims {
   static constexpr int CT = (D::NCUB + 7) / 8;
   static constexpr int NT = (D::NP + 7) / 8;
   static constexpr int NPT = 8 * NT;
+  static constexpr int KF = (3 * D::NG + 7) / 8 * 8;
+  static constexpr int KT = KF / 8;
+  static constexpr int FR = KF > NPT ? KF : NPT;
 };
 
 // Operator fragments in register order (uint32 = two bf16), hi and lo parts.
 //   INTERP [3 ops Ic,Icr,Ics][CT][KSTEP][2 parts][32 lanes][2 regs]
 //   PROJ   [3 ops Pr,Ps,P][CT][NT][2 parts][32 lanes]
+//   LIFT   [KT][NT][2 parts][32 lanes], the B operand -L^g^T (face points x nodes)
 template <int N>
 struct TcLayout {
   using C = TcDims<N>;
   static constexpr int INTERP = 0;
   static constexpr int PROJ = INTERP + 3 * C::CT * C::KSTEP * 2 * 64;
-  static constexpr int SIZE = PROJ + 3 * C::CT * C::NT * 2 * 32;
+  static constexpr int LIFT = PROJ + 3 * C::CT * C::NT * 2 * 32;
+  static constexpr int SIZE = LIFT + C::KT * C::NT * 2 * 32;
 };
 
 // Pointers into the caller-owned workspace. Nodal arrays are node-major

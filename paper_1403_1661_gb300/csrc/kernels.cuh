@@ -303,18 +303,17 @@ __device__ __forceinline__ void store_p1(T* __restrict__ p1, size_t ks, const T*
   }
 }
 
-// Surface term (Section 7.2) for element e: traces at the Gauss points of its
-// three faces, the well-balanced flux, and the lift subtracted from R (in
-// registers). own(f, j) returns the element's own field f (eta, hu, hv, B) at
-// node j, so the caller decides whether the state sits in registers or in
-// shared memory. Shared by the SIMT and the tensor-core stage kernels. With
-// kRolled the three faces run through one copy of the face code (own() must then
-// accept run-time node indices); otherwise the face loop is unrolled.
-template <typename T, int N, bool kRolled = false, typename Own>
-__device__ __forceinline__ void surface_lift(const StageParams<T>& p, const T* __restrict__ sops, int e,
-                                             long long k, const Own& own, T rx, T ry, T sx, T sy,
-                                             T (&R0)[Dims<N>::NP], T (&R1)[Dims<N>::NP],
-                                             T (&R2)[Dims<N>::NP]) {
+// Surface fluxes (Section 7.2) of element e: traces at the Gauss points of its
+// three faces and the well-balanced flux, scaled by sJ/J; emit(f, gq, F0, F1, F2)
+// receives the flux at Gauss point gq of face f. own(f, j) returns the element's
+// own field f (eta, hu, hv, B) at node j, so the caller decides whether the state
+// sits in registers or in shared memory. With kRolled the three faces run
+// through one copy of the face code (own() must then accept run-time node
+// indices); otherwise the face loop is unrolled.
+template <typename T, int N, bool kRolled, typename Own, typename Emit>
+__device__ __forceinline__ void surface_fluxes(const StageParams<T>& p, const T* __restrict__ sops, int e,
+                                               long long k, const Own& own, T rx, T ry, T sx, T sy,
+                                               Emit&& emit) {
   using D = Dims<N>;
   using O = OpLayout<N>;
   constexpr int NP = D::NP, NPP = D::NPP, NFP = D::NFP, NG = D::NG;
@@ -323,7 +322,6 @@ __device__ __forceinline__ void surface_lift(const StageParams<T>& p, const T* _
   const size_t ks = (size_t)sc.KS;
   const size_t fstride = (size_t)NP * ks;
   const size_t bstride = 3 * fstride;
-  // ---- surface term (Section 7.2): traces, well-balanced flux, lift ----
   const int4 cn = __ldg(p.s.conn + e);
 #pragma unroll (kRolled ? 1 : 3)
   for (int f = 0; f < 3; ++f) {
@@ -411,16 +409,30 @@ __device__ __forceinline__ void surface_lift(const StageParams<T>& p, const T* _
       }
       T f0, f1, f2;
       wb_flux<T>(tm, tp, nx, ny, vxn, vyn, hs, g, hg, qg, h0, f0, f1, f2);
-      T lg[NPP];
-      load_row<T, NPP>(sops + O::LGT + (f * NG + gq) * NPP, lg);
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        R0[i] -= lg[i] * f0;
-        R1[i] -= lg[i] * f1;
-        R2[i] -= lg[i] * f2;
-      }
+      emit(f, gq, f0, f1, f2);
     }
   }
+}
+
+// Surface term with the lift R -= L^g F (Section 7.2) applied in registers, point
+// by point (the SIMT stage kernel).
+template <typename T, int N, bool kRolled = false, typename Own>
+__device__ __forceinline__ void surface_lift(const StageParams<T>& p, const T* __restrict__ sops, int e,
+                                             long long k, const Own& own, T rx, T ry, T sx, T sy,
+                                             T (&R0)[Dims<N>::NP], T (&R1)[Dims<N>::NP],
+                                             T (&R2)[Dims<N>::NP]) {
+  using D = Dims<N>;
+  constexpr int NP = D::NP, NPP = D::NPP, NG = D::NG;
+  surface_fluxes<T, N, kRolled>(p, sops, e, k, own, rx, ry, sx, sy, [&](int f, int gq, T f0, T f1, T f2) {
+    T lg[NPP];
+    load_row<T, NPP>(sops + OpLayout<N>::LGT + (f * NG + gq) * NPP, lg);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      R0[i] -= lg[i] * f0;
+      R1[i] -= lg[i] * f1;
+      R2[i] -= lg[i] * f2;
+    }
+  });
 }
 
 // Adams-Bashforth commit (Algorithm 1) and positivity limiter (Algorithm 3) of

@@ -1,20 +1,25 @@
-// Stage kernel with the volume contractions on tensor cores (FP32 tier with
-// split-BF16 products, Section 7.1's N(Q) = Pr cF1 + Ps cF2 + P cS).
+// Stage kernel with the volume contractions and the lift on tensor cores (FP32
+// tier with split-BF16 products, Section 7.1's N(Q) = Pr cF1 + Ps cF2 + P cS and
+// Section 7.2's R = N - L^g F).
 //
-// Each warp owns 32 elements (two 16-row m-tiles). Per m-tile and per tile of 8
-// cubature points:
+// Each warp owns 32 elements (two 16-row m-tiles). First one thread per element
+// computes the face traces and well-balanced fluxes at its 3 Ng Gauss points
+// (shared with the SIMT kernel) into the warp's shared flux tile. Then per m-tile
+// and per tile of 8 cubature points:
 //   interpolation  D[16 el x 8 pts] = State[16 el x Np] * Op^T  (mma m16n8k16),
 //                  for eta, hu, hv, B with Ic and for B with Icr, Ics;
 //   flux           evaluated in registers on the accumulator layout: lane (g, t)
 //                  holds elements g, g+8 at cubature points 2t, 2t+1, which is
 //                  exactly the A-fragment layout of the next product;
 //   projection     R[16 el x Np] += Flux[16 el x 8 pts] * Pr^T (Ps^T, P^T)
-//                  (mma m16n8k8), accumulated over all cubature tiles.
+//                  (mma m16n8k8), accumulated over all cubature tiles;
+// and, on the same accumulators, per tile of 8 face points
+//   lift           R[16 el x Np] -= SurfaceFlux[16 el x 8 pts] * L^g^T (m16n8k8).
 // Every product is split: a = a_hi + a_lo in bfloat16 (operators and data), and
 // a*b ~ a_hi*b_hi + a_hi*b_lo + a_lo*b_hi with FP32 accumulation (relative error
 // of order 2^-16 per product). The warp then hands R and the state to one thread
-// per element through shared memory for the surface term, the Adams-Bashforth
-// commit and the positivity limiter, which are shared with the SIMT kernel.
+// per element through shared memory for the Adams-Bashforth commit and the
+// positivity limiter, which are shared with the SIMT kernel.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -58,10 +63,11 @@ template <int N>
 struct TcSmem {
   using D = Dims<N>;
   using C = TcDims<N>;
-  // per warp: state [4 fields][KP nodes][LS], R [3][NPT][LS], geo [32][4]
+  // per warp: state [4 fields][KP nodes][LS]; surface fluxes [3][KF face points][LS],
+  // later R [3][NPT nodes][LS] in the same rows (field stride FR); geo [32][4]
   static constexpr int STATE = 0;
-  static constexpr int RT = STATE + 4 * C::KP * LS;
-  static constexpr int GEO = RT + 3 * C::NPT * LS;
+  static constexpr int FRT = STATE + 4 * C::KP * LS;
+  static constexpr int GEO = FRT + 3 * C::FR * LS;
   static constexpr int WARP = GEO + 32 * 4;              // floats per warp
   static constexpr int OPS = OpLayout<N>::TAIL;          // floats of per-element operators (staged first)
   static constexpr int BYTES = (OPS + kTcWarps * WARP) * 4;
@@ -74,6 +80,7 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
   using TL = TcLayout<N>;
   using SM = TcSmem<N>;
   constexpr int NP = D::NP, NPP = D::NPP, KP = C::KP, KSTEP = C::KSTEP, CT = C::CT, NT = C::NT;
+  constexpr int NG = D::NG, KT = C::KT, KF = C::KF, FR = C::FR;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sops = reinterpret_cast<float*>(smem_raw);                       // [0, OPS)
   float* swarp_all = sops + SM::OPS;
@@ -90,7 +97,7 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
   const int g = lane >> 2, t = lane & 3;
   float* sw = swarp_all + warp * SM::WARP;
   float* s_state = sw + SM::STATE;
-  float* s_R = sw + SM::RT;
+  float* s_FR = sw + SM::FRT;
   float* s_geo = sw + SM::GEO;
 
   const Sched& sc = p.sc;
@@ -151,7 +158,36 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
       }
     }
 
-    // ---- volume term on tensor cores, one m-tile of 16 elements at a time ----
+    // ---- surface fluxes, one thread per element, into the warp's flux tile ----
+    {
+      float* sf = s_FR + lane;
+      for (int q = 3 * NG; q < KF; ++q) {  // padding points: zero rows for the lift
+        sf[(0 * FR + q) * LS] = 0.f;
+        sf[(1 * FR + q) * LS] = 0.f;
+        sf[(2 * FR + q) * LS] = 0.f;
+      }
+      if (valid) {
+        const float4 ge = reinterpret_cast<const float4*>(s_geo)[lane];
+        const float* my = s_state + lane;
+        auto own = [&](int f, int jn) -> float { return my[(f * KP + jn) * LS]; };
+        surface_fluxes<float, N, true>(p, sops, e, k, own, ge.x, ge.y, ge.z, ge.w,
+                                       [&](int f, int gq, float f0, float f1, float f2) {
+                                         const int q = f * NG + gq;
+                                         sf[(0 * FR + q) * LS] = f0;
+                                         sf[(1 * FR + q) * LS] = f1;
+                                         sf[(2 * FR + q) * LS] = f2;
+                                       });
+      } else {
+        for (int q = 0; q < 3 * NG; ++q) {
+          sf[(0 * FR + q) * LS] = 0.f;
+          sf[(1 * FR + q) * LS] = 0.f;
+          sf[(2 * FR + q) * LS] = 0.f;
+        }
+      }
+    }
+    __syncwarp();
+
+    // ---- volume term and lift on tensor cores, one m-tile of 16 elements at a time ----
 #pragma unroll 1
     for (int mt = 0; mt < 2; ++mt) {
       const int r0 = 16 * mt + g, r1 = r0 + 8;
@@ -288,12 +324,39 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
           }
         }
       }
+      // lift: R -= Flux * L^g^T over the face points, k8 tiles of 8 points; the
+      // fluxes of rows r0, r1 at points 8kt + 2t, 2t + 1 form the A fragments
+#pragma unroll
+      for (int kt = 0; kt < KT; ++kt) {
+        uint32_t lbh[NT], lbl[NT];
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          const uint32_t* fb = stc + TL::LIFT + ((kt * NT + nt) * 2) * 32 + lane;
+          lbh[nt] = __ldg(fb);
+          lbl[nt] = __ldg(fb + 32);
+        }
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+          const float* fq = s_FR + (f * FR + 8 * kt + 2 * t) * LS;
+          uint32_t ah0, al0, ah1, al1;
+          split2(fq[r0], fq[LS + r0], ah0, al0);
+          split2(fq[r1], fq[LS + r1], ah1, al1);
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt) {
+            mma_k8(Racc[f][nt], al0, al1, lbh[nt]);
+            mma_k8(Racc[f][nt], ah0, ah1, lbl[nt]);
+            mma_k8(Racc[f][nt], ah0, ah1, lbh[nt]);
+          }
+        }
+      }
+      // every lane has read this m-tile's flux columns before R overwrites them
+      __syncwarp();
       // R of this m-tile to shared memory: rows r0, r1, nodes 8nt + {2t, 2t+1}
 #pragma unroll
       for (int f = 0; f < 3; ++f)
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt) {
-          float* rn = s_R + (f * C::NPT + 8 * nt + 2 * t) * LS;
+          float* rn = s_FR + (f * FR + 8 * nt + 2 * t) * LS;
           rn[r0] = Racc[f][nt][0];
           rn[LS + r0] = Racc[f][nt][1];
           rn[r1] = Racc[f][nt][2];
@@ -302,22 +365,19 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
     }
     __syncwarp();
 
-    // ---- one thread per element: surface term, commit, positivity ----
+    // ---- one thread per element: commit, positivity ----
     if (valid) {
       float R0[NP], R1[NP], R2[NP];
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
-        R0[i] = s_R[(0 * C::NPT + i) * LS + lane];
-        R1[i] = s_R[(1 * C::NPT + i) * LS + lane];
-        R2[i] = s_R[(2 * C::NPT + i) * LS + lane];
+        R0[i] = s_FR[(0 * FR + i) * LS + lane];
+        R1[i] = s_FR[(1 * FR + i) * LS + lane];
+        R2[i] = s_FR[(2 * FR + i) * LS + lane];
       }
       const float4 ge = reinterpret_cast<const float4*>(s_geo)[lane];
       // the per-element operators were staged at the start of shared memory with the
-      // OpLayout offsets, so the shared epilogue indexes them directly; the own
-      // state is read from the warp's shared tile when the surface term needs it
+      // OpLayout offsets, so the shared epilogue indexes them directly
       const float* my = s_state + lane;
-      auto own = [&](int f, int jn) -> float { return my[(f * KP + jn) * LS]; };
-      surface_lift<float, N, true>(p, sops, e, k, own, ge.x, ge.y, ge.z, ge.w, R0, R1, R2);
       float eta[NPP], hu[NPP], hv[NPP], bb[NPP];
 #pragma unroll
       for (int i = 0; i < NPP; ++i) {

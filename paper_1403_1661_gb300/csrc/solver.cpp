@@ -312,6 +312,22 @@ void pack_ops_n(const swe::RefElem& e, std::vector<double>& o, std::vector<uint3
           tc[TL::PROJ + base + 0 * 32 + lane] = pack2(h0, h1);
           tc[TL::PROJ + base + 1 * 32 + lane] = pack2(l0, l1);
         }
+  // lift: B[k][n] = -Lg[i = 8nt + n][q = 8kt + k], q = 3 Ng face points (Lg is np x 3ng)
+  for (int kt = 0; kt < C::KT; ++kt)
+    for (int nt = 0; nt < C::NT; ++nt)
+      for (int lane = 0; lane < 32; ++lane) {
+        const int g = lane / 4, t = lane % 4;
+        auto Bv = [&](int kk, int nn) {
+          const int i = 8 * nt + nn, q = 8 * kt + kk;
+          return (i < np && q < 3 * ng) ? -e.Lg[(size_t)i * 3 * ng + q] : 0.0;
+        };
+        uint16_t h0, l0, h1, l1;
+        bf16_split(Bv(2 * t, g), h0, l0);
+        bf16_split(Bv(2 * t + 1, g), h1, l1);
+        const size_t base = ((size_t)(kt * C::NT + nt) * 2) * 32;
+        tc[TL::LIFT + base + 0 * 32 + lane] = pack2(h0, h1);
+        tc[TL::LIFT + base + 1 * 32 + lane] = pack2(l0, l1);
+      }
 }
 
 void pack_ops(int N, const swe::RefElem& e, std::vector<double>& o, std::vector<uint32_t>& tc) {
