@@ -218,6 +218,19 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 
+def combine_ranks(ms, dofs, dist=None, device="cuda"):
+    """Whole-job numbers of independent replicas: the slowest rank's time and the
+    DOF updates of all ranks (one collective each, outside the timed region)."""
+    if dist is None:
+        return ms, float(dofs)
+    import torch
+    tmax = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    tsum = torch.tensor([float(dofs)], dtype=torch.float64, device=device)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[0])
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -266,14 +279,7 @@ def run_ours(args):
     st = s.stats()
     dofs = st["dof_updates"] - d0
     launches = s.kernel_launches() - launches0
-    if dist:
-        t = torch.tensor([ms, float(dofs)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        ms_all, dofs_all = float(tmax[0]), float(t[1])
-    else:
-        ms_all, dofs_all = ms, float(dofs)
+    ms_all, dofs_all = combine_ranks(ms, dofs, dist, "cuda")
     value = dofs_all / (ms_all / 1e3)
 
     # per-kernel timing of one more macro step (events around every launch)

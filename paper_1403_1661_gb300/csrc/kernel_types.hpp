@@ -32,7 +32,9 @@ struct OpLayout {
   static constexpr int MW = I1D + D::NG * D::NFPP;             // [NPP] mean weights
   static constexpr int T1 = MW + D::NPP;                       // [3][NPP] P1 vertex map
   static constexpr int BARY = T1 + 3 * D::NPP;                 // [NPP][4] barycentric
-  static constexpr int TAIL = BARY + 4 * D::NPP;
+  static constexpr int DR = BARY + 4 * D::NPP;                 // [NP][NPP] nodal d/dr
+  static constexpr int DS = DR + D::NP * D::NPP;               // [NP][NPP] nodal d/ds
+  static constexpr int TAIL = DS + D::NP * D::NPP;
   static constexpr int IC = TAIL;                              // [NCUB][NPP]
   static constexpr int ICR = IC + D::NCUB * D::NPP;            // [NCUB][NPP]
   static constexpr int ICS = ICR + D::NCUB * D::NPP;           // [NCUB][NPP]

@@ -22,6 +22,20 @@
 //   faces:   pressure term of the well-balanced flux (own side "-")
 //            g/2 eta^- (h^- - B^-) + g/4 (h*^+ - h*^-)(h*^+ + h*^-),
 //            h*^{+-} = max(0, eta^{+-} - max(B^+, B^-)).
+// Element reference split. With eta = eta0 + eta' and B = B0 + B' (eta0, B0 the
+// element's values at its node 0), the pressure g/2 eta (eta - 2B) is a constant
+// plus terms linear in eta' and B' with constant coefficients plus
+// p'' = g/2 eta' (eta' - 2B'). For a constant or such a linear term P (a
+// polynomial of degree N) the volume term plus the own-side face term is exactly
+// the strong derivative -dP/dx (integration by parts, exact integration); with the
+// source's -g eta0 grad B' the linear terms sum to -g h0 grad eta, h0 = eta0 - B0.
+// So both kernels take p'' in the volume and face pressures, the source
+// -g eta' grad B', and add -g h0 (r_x Dr + s_x Ds) eta (and the y analogue) once.
+// At ocean depths the pressure is ~1e5 where R is ~1, and on a beach a film of
+// millimetres sits on a bed metres above the datum: the rewrite removes both
+// cancellations, and a lake at rest at any level gives R = 0 exactly. Where both
+// sides of a face are wet the jump h*^+ - h*^- is computed as eta^+ - eta^-,
+// which it equals, instead of as a difference of two large depths.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -176,9 +190,11 @@ struct Trace {
 
 // (nx, ny) unit outward normal, (vx, vy) = (sJ/J) (nx, ny), hs = sJ/J / 2; the
 // returned fluxes are already scaled by sJ/J for the lift. hg = g/2, qg = g/4.
+// epm, epp, bpm: eta^-, eta^+ and B^- relative to the element's eta0, B0; the
+// own-side pressure is p'' (element reference split above).
 template <typename T>
-__device__ __forceinline__ void wb_flux(const Trace<T>& m, const Trace<T>& p, T nx, T ny, T vx, T vy, T hs,
-                                        T g, T hg, T qg, T h0, T& f0, T& f1, T& f2) {
+__device__ __forceinline__ void wb_flux(const Trace<T>& m, const Trace<T>& p, T epm, T epp, T bpm, T nx, T ny,
+                                        T vx, T vy, T hs, T g, T hg, T qg, T h0, T& f0, T& f1, T& f2) {
   const T hm = m.eta - m.B, hp = p.eta - p.B;
   const T im = hm > h0 ? recip(hm) : T(0), ip = hp > h0 ? recip(hp) : T(0);
   const T um = m.hu * im, vm = m.hv * im;
@@ -189,8 +205,8 @@ __device__ __forceinline__ void wb_flux(const Trace<T>& m, const Trace<T>& p, T 
   const T unm = um * nx + vm * ny, unp = up * nx + vp * ny;
   const T lam = tmax(fabs(unm) + sqrt_nn(g * sm), fabs(unp) + sqrt_nn(g * sp));
   const T Fm = sm * unm, Fp = sp * unp;
-  const T ds = sp - sm;
-  const T pres = hg * m.eta * (hm - m.B) + qg * ds * (sp + sm);
+  const T ds = (sm > T(0) && sp > T(0)) ? epp - epm : sp - sm;
+  const T pres = hg * epm * (epm - T(2) * bpm) + qg * ds * (sp + sm);
   f0 = hs * ((Fm + Fp) - lam * ds);
   f1 = hs * ((Fm * um + Fp * up) - lam * (sp * up - sm * um)) + pres * vx;
   f2 = hs * ((Fm * vm + Fp * vp) - lam * (sp * vp - sm * vm)) + pres * vy;
@@ -323,6 +339,7 @@ __device__ __forceinline__ void surface_fluxes(const StageParams<T>& p, const T*
   const size_t fstride = (size_t)NP * ks;
   const size_t bstride = 3 * fstride;
   const int4 cn = __ldg(p.s.conn + e);
+  const T E0 = own(0, 0), B0 = own(3, 0);
 #pragma unroll (kRolled ? 1 : 3)
   for (int f = 0; f < 3; ++f) {
     // outward normal times sJ/J from the affine factors
@@ -349,10 +366,10 @@ __device__ __forceinline__ void surface_fluxes(const StageParams<T>& p, const T*
       for (int m = 0; m < NFP; ++m) {
         const int jn = face_node_rt(N, fn, NFP - 1 - m);
         const size_t idx = (size_t)jn * sn;
-        ne[m] = __ldg(qn + idx);
+        ne[m] = __ldg(qn + idx) - E0;   // relative to the own E0, like oe
         nu[m] = __ldg(qn + sf + idx);
         nv[m] = __ldg(qn + 2 * sf + idx);
-        nB[m] = __ldg(p.s.B + nb + (size_t)jn * ks);
+        nB[m] = __ldg(p.s.B + nb + (size_t)jn * ks) - B0;   // relative to the own B0, like oB
       }
       if (phase != 0 && !half) {  // other fractions: Adams-Bashforth polynomial at t_k
         const int depth = an + 1 < 3 ? (int)(an + 1) : 3;
@@ -365,35 +382,38 @@ __device__ __forceinline__ void surface_fluxes(const StageParams<T>& p, const T*
 #pragma unroll
           for (int m = 0; m < NFP; ++m) {
             const size_t idx = (size_t)face_node_rt(N, fn, NFP - 1 - m) * ks;
-            ne[m] += ws * __ldg(rs + idx);
+            ne[m] += ws * __ldg(rs + idx);   // (ne keeps its E0 offset: R carries none)
             nu[m] += ws * __ldg(rs + fstride + idx);
             nv[m] += ws * __ldg(rs + 2 * fstride + idx);
           }
         }
       }
     }
-    // own face-node values, read once per face
+    // own face-node values, read once per face; surface and bed relative to E0, B0
     T oe[NFP], ou[NFP], ov[NFP], oB[NFP];
 #pragma unroll
     for (int m = 0; m < NFP; ++m) {
       const int jn = face_node(N, f, m);
-      oe[m] = own(0, jn);
+      oe[m] = own(0, jn) - E0;
       ou[m] = own(1, jn);
       ov[m] = own(2, jn);
-      oB[m] = own(3, jn);
+      oB[m] = own(3, jn) - B0;
     }
 #pragma unroll 1
     for (int gq = 0; gq < NG; ++gq) {
       T i1[D::NFPP];
       load_row<T, D::NFPP>(sops + O::I1D + gq * D::NFPP, i1);
       Trace<T> tm = {0, 0, 0, 0}, tp;
+      T epm = 0, bpm = 0, epp;
 #pragma unroll
       for (int m = 0; m < NFP; ++m) {
-        tm.eta += i1[m] * oe[m];
+        epm += i1[m] * oe[m];
         tm.hu += i1[m] * ou[m];
         tm.hv += i1[m] * ov[m];
-        tm.B += i1[m] * oB[m];
+        bpm += i1[m] * oB[m];
       }
+      tm.eta = E0 + epm;
+      tm.B = B0 + bpm;
       if (nb >= 0) {
         tp = {0, 0, 0, 0};
 #pragma unroll
@@ -403,12 +423,16 @@ __device__ __forceinline__ void surface_fluxes(const StageParams<T>& p, const T*
           tp.hv += i1[m] * nv[m];
           tp.B += i1[m] * nB[m];
         }
+        epp = tp.eta;
+        tp.eta += E0;
+        tp.B += B0;
       } else {  // reflecting wall: mirror the normal momentum
         const T mn = tm.hu * nx + tm.hv * ny;
         tp = {tm.eta, tm.hu - T(2) * mn * nx, tm.hv - T(2) * mn * ny, tm.B};
+        epp = epm;
       }
       T f0, f1, f2;
-      wb_flux<T>(tm, tp, nx, ny, vxn, vyn, hs, g, hg, qg, h0, f0, f1, f2);
+      wb_flux<T>(tm, tp, epm, epp, bpm, nx, ny, vxn, vyn, hs, g, hg, qg, h0, f0, f1, f2);
       emit(f, gq, f0, f1, f2);
     }
   }
@@ -433,6 +457,36 @@ __device__ __forceinline__ void surface_lift(const StageParams<T>& p, const T* _
       R2[i] -= lg[i] * f2;
     }
   });
+}
+
+// The reference part of the pressure and source in strong form (element
+// reference split above): R_hu -= g h0 (r_x Dr + s_x Ds)(eta - eta0),
+// R_hv -= g h0 (r_y Dr + s_y Ds)(eta - eta0), h0 = eta0 - B0 the depth at node 0.
+template <typename T, int N>
+__device__ __forceinline__ void add_reference_pressure(const T* __restrict__ sops, const T (&eta)[Dims<N>::NPP],
+                                                       const T (&bb)[Dims<N>::NPP], T g, T rx, T ry, T sx,
+                                                       T sy, T (&R1)[Dims<N>::NP], T (&R2)[Dims<N>::NP]) {
+  using D = Dims<N>;
+  using O = OpLayout<N>;
+  constexpr int NP = D::NP, NPP = D::NPP;
+  T d[NPP];
+#pragma unroll
+  for (int j = 0; j < NPP; ++j) d[j] = j < NP ? eta[j] - eta[0] : T(0);
+  const T gb = -g * (eta[0] - bb[0]);
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    T dr[NPP], ds[NPP];
+    load_row<T, NPP>(sops + O::DR + i * NPP, dr);
+    load_row<T, NPP>(sops + O::DS + i * NPP, ds);
+    T er = 0, es = 0;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      er += dr[j] * d[j];
+      es += ds[j] * d[j];
+    }
+    R1[i] += gb * (rx * er + sx * es);
+    R2[i] += gb * (ry * er + sy * es);
+  }
 }
 
 // Adams-Bashforth commit (Algorithm 1) and positivity limiter (Algorithm 3) of
@@ -580,22 +634,25 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
       load_row<T, NPP>(sops + O::IC + c * NPP, ic);
       load_row<T, NPP>(sops + O::ICR + c * NPP, icr);
       load_row<T, NPP>(sops + O::ICS + c * NPP, ics);
+      // ec, bc, brc, bsc: of eta - eta0 and B - B0 (element reference split)
       T ec = 0, huc = 0, hvc = 0, bc = 0, brc = 0, bsc = 0;
 #pragma unroll
       for (int jn = 0; jn < NP; ++jn) {
-        ec += ic[jn] * eta[jn];
+        const T ep = eta[jn] - eta[0], bp = bb[jn] - bb[0];
+        ec += ic[jn] * ep;
         huc += ic[jn] * hu[jn];
         hvc += ic[jn] * hv[jn];
-        bc += ic[jn] * bb[jn];
-        brc += icr[jn] * bb[jn];
-        bsc += ics[jn] * bb[jn];
+        bc += ic[jn] * bp;
+        brc += icr[jn] * bp;
+        bsc += ics[jn] * bp;
       }
-      const T hc = ec - bc;
+      const T hc = (eta[0] - bb[0]) + (ec - bc);
       const T ih = hc > h0 ? recip(hc) : T(0);
       const T u = huc * ih, v = hvc * ih;
       // cF1 = rx F + ry G and cF2 = sx F + sy G, with the momentum rows written
-      // through the mass row: rx (hu u + p) + ry hv u = u (rx hu + ry hv) + rx p
-      const T pr = hg * ec * (hc - bc);
+      // through the mass row: rx (hu u + p) + ry hv u = u (rx hu + ry hv) + rx p;
+      // p = p'' (element reference split)
+      const T pr = hg * ec * (ec - T(2) * bc);
       const T a0 = rx * huc + ry * hvc, b0 = sx * huc + sy * hvc;
       const T a1 = u * a0 + rx * pr, a2 = v * a0 + ry * pr;
       const T b1 = u * b0 + sx * pr, b2 = v * b0 + sy * pr;
@@ -615,6 +672,7 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
 
     auto own = [&](int f, int jn) -> T { return f == 0 ? eta[jn] : (f == 1 ? hu[jn] : (f == 2 ? hv[jn] : bb[jn])); };
     surface_lift<T, N>(p, sops, e, k, own, rx, ry, sx, sy, R0, R1, R2);
+    add_reference_pressure<T, N>(sops, eta, bb, g, rx, ry, sx, sy, R1, R2);
     commit_and_limit<T, N>(p, sops, e, lev, a, eta, hu, hv, bb, rx, ry, sx, sy, R0, R1, R2, &injected);
   }
   if (injected != 0.0) atomicAdd(p.s.acc, injected);

@@ -191,17 +191,25 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
 #pragma unroll 1
     for (int mt = 0; mt < 2; ++mt) {
       const int r0 = 16 * mt + g, r1 = r0 + 8;
-      // state A fragments (rows r0, r1; nodes 16ks + {2t, 2t+1, 2t+8, 2t+9}), hi and lo
+      // State A fragments (rows r0, r1; nodes 16ks + {2t, 2t+1, 2t+8, 2t+9}), hi and
+      // lo. The surface and the bed enter relative to their values at node 0 of the
+      // element (eta0, B0): the interpolation of a constant is exact and its
+      // derivatives vanish (Ic B = B0 + Ic (B - B0), Icr B = Icr (B - B0)), so only
+      // the within-element variation carries the split-product error, whether the
+      // bed is thousands of metres deep or the water a millimetre thin.
+      const float cE0 = s_state[r0], cE1 = s_state[r1];
+      const float cB0 = s_state[(3 * KP) * LS + r0], cB1 = s_state[(3 * KP) * LS + r1];
       uint32_t ah[4][KSTEP][4], al[4][KSTEP][4];
 #pragma unroll
       for (int f = 0; f < 4; ++f)
 #pragma unroll
         for (int ks = 0; ks < KSTEP; ++ks) {
           const float* sn = s_state + (f * KP + 16 * ks + 2 * t) * LS;   // node 16ks + 2t
-          const float2 v00 = make_float2(sn[r0], sn[LS + r0]);
-          const float2 v10 = make_float2(sn[r1], sn[LS + r1]);
-          const float2 v01 = make_float2(sn[8 * LS + r0], sn[9 * LS + r0]);
-          const float2 v11 = make_float2(sn[8 * LS + r1], sn[9 * LS + r1]);
+          const float d0 = f == 3 ? cB0 : (f == 0 ? cE0 : 0.f), d1 = f == 3 ? cB1 : (f == 0 ? cE1 : 0.f);
+          const float2 v00 = make_float2(sn[r0] - d0, sn[LS + r0] - d0);
+          const float2 v10 = make_float2(sn[r1] - d1, sn[LS + r1] - d1);
+          const float2 v01 = make_float2(sn[8 * LS + r0] - d0, sn[9 * LS + r0] - d0);
+          const float2 v11 = make_float2(sn[8 * LS + r1] - d1, sn[9 * LS + r1] - d1);
           split2(v00.x, v00.y, ah[f][ks][0], al[f][ks][0]);
           split2(v10.x, v10.y, ah[f][ks][1], al[f][ks][1]);
           split2(v01.x, v01.y, ah[f][ks][2], al[f][ks][2]);
@@ -277,13 +285,16 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
         for (int c = 0; c < 4; ++c) {
           const float4 ge = c < 2 ? ge0 : ge1;
           const float rx = ge.x, ry = ge.y, sx = ge.z, sy = ge.w;
-          const float ec = acc[0][c], huc = acc[1][c], hvc = acc[2][c], bc = acc[3][c];
+          // eta - eta0 and B - B0 at the point (element reference split)
+          const float ec = acc[0][c], huc = acc[1][c], hvc = acc[2][c];
+          const float bpc = acc[3][c];
           const float brc = acc[4][c], bsc = acc[5][c];
-          const float hc = ec - bc;
+          const float hc = (c < 2 ? cE0 - cB0 : cE1 - cB1) + (ec - bpc);
           const float ih = hc > h0 ? recip(hc) : 0.f;
           const float u = huc * ih, v = hvc * ih;
-          // momentum rows of cF1, cF2 written through the mass row (see k_stage)
-          const float pr = hg * ec * (hc - bc);
+          // momentum rows of cF1, cF2 written through the mass row; p'' (the
+          // reference part is added in strong form before the commit)
+          const float pr = hg * ec * (ec - 2.f * bpc);
           const float a0 = rx * huc + ry * hvc, b0 = sx * huc + sy * hvc;
           fl[0][c] = a0;
           fl[1][c] = u * a0 + rx * pr;
@@ -386,6 +397,7 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
         hv[i] = my[(2 * KP + i) * LS];
         bb[i] = my[(3 * KP + i) * LS];
       }
+      add_reference_pressure<float, N>(sops, eta, bb, gg, ge.x, ge.y, ge.z, ge.w, R1, R2);
       commit_and_limit<float, N>(p, sops, e, lev, a, eta, hu, hv, bb, ge.x, ge.y, ge.z, ge.w, R0, R1, R2,
                                  &injected);
     }
