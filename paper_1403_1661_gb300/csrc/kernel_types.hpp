@@ -32,16 +32,16 @@ struct OpLayout {
   static constexpr int MW = I1D + D::NG * D::NFPP;             // [NPP] mean weights
   static constexpr int T1 = MW + D::NPP;                       // [3][NPP] P1 vertex map
   static constexpr int BARY = T1 + 3 * D::NPP;                 // [NPP][4] barycentric
-  static constexpr int DR = BARY + 4 * D::NPP;                 // [NP][NPP] nodal d/dr
-  static constexpr int DS = DR + D::NP * D::NPP;               // [NP][NPP] nodal d/ds
-  static constexpr int TAIL = DS + D::NP * D::NPP;
+  static constexpr int TAIL = BARY + 4 * D::NPP;
   static constexpr int IC = TAIL;                              // [NCUB][NPP]
   static constexpr int ICR = IC + D::NCUB * D::NPP;            // [NCUB][NPP]
   static constexpr int ICS = ICR + D::NCUB * D::NPP;           // [NCUB][NPP]
   static constexpr int PRT = ICS + D::NCUB * D::NPP;           // [NCUB][NPP], Pr^T
   static constexpr int PST = PRT + D::NCUB * D::NPP;           // [NCUB][NPP], Ps^T
   static constexpr int PT = PST + D::NCUB * D::NPP;            // [NCUB][NPP], P^T
-  static constexpr int SIZE = PT + D::NCUB * D::NPP;
+  static constexpr int DR = PT + D::NCUB * D::NPP;             // [NP][NPP] nodal d/dr
+  static constexpr int DS = DR + D::NP * D::NPP;               // [NP][NPP] nodal d/ds
+  static constexpr int SIZE = DS + D::NP * D::NPP;
 };
 
 // Tensor-core tiling of the volume contractions (mma.sync, bf16 operands).
@@ -67,13 +67,16 @@ struct TcDims {
 //   INTERP [3 ops Ic,Icr,Ics][CT][KSTEP][2 parts][32 lanes][2 regs]
 //   PROJ   [3 ops Pr,Ps,P][CT][NT][2 parts][32 lanes]
 //   LIFT   [KT][NT][2 parts][32 lanes], the B operand -L^g^T (face points x nodes)
+//   DIFF   [2 ops Dr,Ds][KP/8][NT][2 parts][32 lanes][2 regs], TF32 B operands
+//          Dr^T, Ds^T (nodes x nodes) of m16n8k8.tf32
 template <int N>
 struct TcLayout {
   using C = TcDims<N>;
   static constexpr int INTERP = 0;
   static constexpr int PROJ = INTERP + 3 * C::CT * C::KSTEP * 2 * 64;
   static constexpr int LIFT = PROJ + 3 * C::CT * C::NT * 2 * 32;
-  static constexpr int SIZE = LIFT + C::KT * C::NT * 2 * 32;
+  static constexpr int DIFF = LIFT + C::KT * C::NT * 2 * 32;
+  static constexpr int SIZE = DIFF + 2 * (C::KP / 8) * C::NT * 2 * 64;
 };
 
 // Pointers into the caller-owned workspace. Nodal arrays are node-major

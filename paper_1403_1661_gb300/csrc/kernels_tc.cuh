@@ -44,6 +44,19 @@ __device__ __forceinline__ void mma_k8(float (&d)[4], uint32_t a0, uint32_t a1, 
       : "r"(a0), "r"(a1), "r"(b0));
 }
 
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// float -> (hi, lo) TF32 pair: hi rounded to 10 mantissa bits, lo the remainder
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
+  lo = __float_as_uint(x - __uint_as_float(hi));
+}
+
 // two floats -> (hi, lo) bf16x2 pairs; the first float goes to the low half
 __device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
@@ -360,6 +373,48 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
           }
         }
       }
+      // strong-form reference pressure (element reference split, see kernels.cuh):
+      // R_hu -= g h0 (rx Dr + sx Ds)(eta - eta0), R_hv -= g h0 (ry Dr + sy Ds)(eta - eta0).
+      // The leading term of R at depth, so TF32 split products (2^-21 per product).
+      {
+        float Dacc[2][NT][4];
+#pragma unroll
+        for (int op = 0; op < 2; ++op)
+#pragma unroll
+          for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) Dacc[op][nt][c] = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < KP / 8; ++kk) {
+          const float* sn = s_state + (8 * kk + t) * LS;   // eta at node 8kk + t
+          uint32_t eh[4], el[4];
+          split_tf32(sn[r0] - cE0, eh[0], el[0]);
+          split_tf32(sn[r1] - cE1, eh[1], el[1]);
+          split_tf32(sn[4 * LS + r0] - cE0, eh[2], el[2]);
+          split_tf32(sn[4 * LS + r1] - cE1, eh[3], el[3]);
+#pragma unroll
+          for (int op = 0; op < 2; ++op)
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+              const uint32_t* fb = stc + TL::DIFF + (((op * (KP / 8) + kk) * NT + nt) * 2) * 64 + lane * 2;
+              const uint2 bh = __ldg(reinterpret_cast<const uint2*>(fb));
+              const uint2 bl = __ldg(reinterpret_cast<const uint2*>(fb + 64));
+              mma_tf32(Dacc[op][nt], el, bh.x, bh.y);
+              mma_tf32(Dacc[op][nt], eh, bl.x, bl.y);
+              mma_tf32(Dacc[op][nt], eh, bh.x, bh.y);
+            }
+        }
+        const float gh0 = -gg * (cE0 - cB0), gh1 = -gg * (cE1 - cB1);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float4 ge = c < 2 ? ge0 : ge1;
+            const float gh = c < 2 ? gh0 : gh1;
+            Racc[1][nt][c] += gh * (ge.x * Dacc[0][nt][c] + ge.z * Dacc[1][nt][c]);
+            Racc[2][nt][c] += gh * (ge.y * Dacc[0][nt][c] + ge.w * Dacc[1][nt][c]);
+          }
+      }
       // every lane has read this m-tile's flux columns before R overwrites them
       __syncwarp();
       // R of this m-tile to shared memory: rows r0, r1, nodes 8nt + {2t, 2t+1}
@@ -397,7 +452,6 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
         hv[i] = my[(2 * KP + i) * LS];
         bb[i] = my[(3 * KP + i) * LS];
       }
-      add_reference_pressure<float, N>(sops, eta, bb, gg, ge.x, ge.y, ge.z, ge.w, R1, R2);
       commit_and_limit<float, N>(p, sops, e, lev, a, eta, hu, hv, bb, ge.x, ge.y, ge.z, ge.w, R0, R1, R2,
                                  &injected);
     }

@@ -233,6 +233,21 @@ float bf16_value(uint16_t b) {
   std::memcpy(&f, &u, 4);
   return f;
 }
+// hi/lo TF32 split of an operator entry: hi rounded to 10 mantissa bits (to
+// nearest, ties away), lo = the single-precision remainder (the tensor core reads
+// its top 10 mantissa bits)
+void tf32_split(double v, uint32_t& hi, uint32_t& lo) {
+  const float vf = (float)v;
+  uint32_t u;
+  std::memcpy(&u, &vf, 4);
+  u = (u + 0x1000u) & 0xFFFFE000u;
+  float h;
+  std::memcpy(&h, &u, 4);
+  const float l = vf - h;
+  hi = u;
+  std::memcpy(&lo, &l, 4);
+}
+
 // hi/lo bf16 split of a single-precision operator entry
 void bf16_split(double v, uint16_t& hi, uint16_t& lo) {
   const float vf = (float)v;
@@ -323,6 +338,26 @@ void pack_ops_n(const swe::RefElem& e, std::vector<double>& o, std::vector<uint3
           const size_t base = (((size_t)(op * C::CT + ct) * C::NT + nt) * 2) * 32;
           tc[TL::PROJ + base + 0 * 32 + lane] = pack2(h0, h1);
           tc[TL::PROJ + base + 1 * 32 + lane] = pack2(l0, l1);
+        }
+  // nodal differentiation for the strong-form pressure term: TF32 m16n8k8 B
+  // operands, B[k][n] = D[i = 8nt + n][j = 8kk + k]; lane (g, t) holds k = t, t + 4
+  for (int op = 0; op < 2; ++op)
+    for (int kk = 0; kk < C::KP / 8; ++kk)
+      for (int nt = 0; nt < C::NT; ++nt)
+        for (int lane = 0; lane < 32; ++lane) {
+          const int g = lane / 4, t = lane % 4;
+          auto Bv = [&](int k, int n) {
+            const int i = 8 * nt + n, j = 8 * kk + k;
+            return (i < np && j < np) ? o[(op == 0 ? O::DR : O::DS) + (size_t)i * npp + j] : 0.0;
+          };
+          uint32_t h0, l0, h1, l1;
+          tf32_split(Bv(t, g), h0, l0);
+          tf32_split(Bv(t + 4, g), h1, l1);
+          const size_t base = TL::DIFF + ((((size_t)op * (C::KP / 8) + kk) * C::NT + nt) * 2) * 64;
+          tc[base + 0 * 64 + lane * 2 + 0] = h0;
+          tc[base + 0 * 64 + lane * 2 + 1] = h1;
+          tc[base + 1 * 64 + lane * 2 + 0] = l0;
+          tc[base + 1 * 64 + lane * 2 + 1] = l1;
         }
   // lift: B[k][n] = -Lg[i = 8nt + n][q = 8kt + k], q = 3 Ng face points (Lg is np x 3ng)
   for (int kt = 0; kt < C::KT; ++kt)
