@@ -141,7 +141,11 @@ int swe_set_bathymetry(swe_solver* solver, const double* B);
 
 /* Initial state (K x Np each, host, FP64): interpolated nodal values (the caller
  * does Pi_H). Applies the limiters of the mask to it (Algorithm 2, first line),
- * clears the Adams-Bashforth history and sets t = 0. */
+ * clears the Adams-Bashforth history and sets t = 0. The arrays are copied to the
+ * device as they are (page-locked host memory transfers fastest); the check for
+ * non-finite values, the reordering and the precision conversion run there.
+ * SWE_EINVAL for a non-finite value, with the previous state left in place.
+ * Synchronises the stream. */
 int swe_set_state(swe_solver* solver, const double* h, const double* hu, const double* hv);
 
 /* Group elements into MRAB levels from the current state (Eq. cfl, Section 4):
@@ -175,7 +179,9 @@ int swe_step(swe_solver* solver, int32_t n_macro);
 int swe_limit(swe_solver* solver, int32_t mask);
 
 /* Copy the current state to the host (K x Np each, FP64, caller order) and the
- * simulated time t. Requires a level-synchronous state. Synchronises the stream. */
+ * simulated time t. The conversion to the caller's layout runs on the device,
+ * then one copy per array; any of h, hu, hv, t may be NULL (not copied).
+ * Requires a level-synchronous state. Synchronises the stream. */
 int swe_get_state(const swe_solver* solver, double* h, double* hu, double* hv, double* t);
 
 /* Diagnostics (synchronises): mass = sum_k |D^k| mean(h), injected mass of dry

@@ -33,6 +33,19 @@ template <typename T>
 const Launchers<T>* launchers_for(int N);
 
 cudaError_t launch_advance(long long* macro, cudaStream_t st);
+
+// State transfer between the caller's layout ([3][K][Np] FP64, caller element
+// order, depth h) and the device planes (eta = h + B in device precision, level
+// order). x: staging copy of the caller arrays in device memory; Bc: the bed in
+// caller order (FP64); iperm: caller index -> device index.
+cudaError_t launch_check_finite(const double* x, size_t n, int* flag, cudaStream_t st);
+template <typename T>
+cudaError_t launch_pack_state(const double* x, const double* Bc, const int* iperm, int K, int KS, int Np,
+                              T* q, cudaStream_t st);
+// Reverse: each element's current buffer from its level, h = eta - (device-precision B).
+template <typename T>
+cudaError_t launch_unpack_state(const T* q, const double* Bc, const int* iperm, const Sched& sc,
+                                long long k, int Np, double* x, cudaStream_t st);
 cudaError_t launch_stats_finalize(const double* partials, int nblocks, double* out, cudaStream_t st);
 
 }  // namespace swe

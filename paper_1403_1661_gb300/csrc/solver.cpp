@@ -50,7 +50,7 @@ int np_of(int N) { return (N + 1) * (N + 2) / 2; }
 int ks_of(int K) { return (K + 31) / 32 * 32; }
 
 struct Layout {
-  size_t q, ring, qmid, B, p1, vb, geo, conn, tvbg, means, dry, Bbar, ops, tcops, perm, acc, flags, macro, partials, total;
+  size_t q, ring, qmid, B, p1, vb, xfer, bcaller, iperm, xflag, geo, conn, tvbg, means, dry, Bbar, ops, tcops, perm, acc, flags, macro, partials, total;
   int nb_stats;
 };
 
@@ -71,6 +71,10 @@ Layout make_layout(int K, int N, size_t ts, int op_size) {
   L.B = take(plane * ts);
   L.p1 = take(9 * (size_t)ks_of(K) * ts);
   L.vb = take(3 * (size_t)ks_of(K) * ts);
+  L.xfer = take(3 * (size_t)K * np_of(N) * 8);      // caller-layout FP64 staging of the state
+  L.bcaller = take((size_t)K * np_of(N) * 8);       // the bed in caller order, FP64
+  L.iperm = take((size_t)K * 4);
+  L.xflag = take(16);
   L.geo = take((size_t)K * 4 * ts);
   L.conn = take((size_t)K * 16);
   L.tvbg = take((size_t)K * 8 * ts);
@@ -448,6 +452,7 @@ int upload_mesh_t(swe_solver* s) {
   if ((rc = upload(s, s->lay.conn, conn.data(), conn.size() * 4))) return rc;
   if ((rc = upload(s, s->lay.tvbg, tvbg.data(), tvbg.size() * sizeof(T)))) return rc;
   if ((rc = upload(s, s->lay.perm, s->perm.data(), (size_t)K * 4))) return rc;
+  if ((rc = upload(s, s->lay.iperm, s->iperm.data(), (size_t)K * 4))) return rc;
   if (s->have_B) {
     std::vector<T> b((size_t)s->Np * KS, T(0)), vb(3 * (size_t)KS, T(0));
     std::vector<double> bbar(K, 0.0);
@@ -465,6 +470,7 @@ int upload_mesh_t(swe_solver* s) {
     }
     if ((rc = upload(s, s->lay.B, b.data(), b.size() * sizeof(T)))) return rc;
     if ((rc = upload(s, s->lay.vb, vb.data(), vb.size() * sizeof(T)))) return rc;
+    if ((rc = upload(s, s->lay.bcaller, s->B_in.data(), s->B_in.size() * 8))) return rc;
     if ((rc = upload(s, s->lay.Bbar, bbar.data(), bbar.size() * 8))) return rc;
     SWE_CUDA(cudaStreamSynchronize(s->stream));
   }
@@ -505,26 +511,6 @@ int invalidate_graph(swe_solver* s) {
 int reset_counters(swe_solver* s) {
   s->k = 0;
   SWE_CUDA(cudaMemsetAsync(s->ws + s->lay.macro, 0, 8, s->stream));
-  return SWE_OK;
-}
-
-template <typename T>
-int upload_state_t(swe_solver* s, const double* h, const double* hu, const double* hv) {
-  const int K = s->K, KS = s->KS, np = s->Np;
-  const size_t fs = (size_t)np * KS;
-  std::vector<T> q(3 * fs, T(0));
-  for (int e = 0; e < K; ++e) {
-    const int c = s->perm[e];
-    for (int j = 0; j < np; ++j) {
-      const size_t ci = (size_t)c * np + j, di = (size_t)j * KS + e;
-      q[di] = (T)(h[ci] + s->B_in[ci]);
-      q[fs + di] = (T)hu[ci];
-      q[2 * fs + di] = (T)hv[ci];
-    }
-  }
-  int rc = upload(s, s->lay.q, q.data(), q.size() * sizeof(T));
-  if (rc) return rc;
-  SWE_CUDA(cudaStreamSynchronize(s->stream));
   return SWE_OK;
 }
 
@@ -646,31 +632,28 @@ int64_t substep_dofs(const swe_solver* s, int j) {
 
 bool synchronous(const swe_solver* s) { return (s->k % (1LL << (s->L - 1))) == 0; }
 
-template <typename T>
-int download_state_t(const swe_solver* s, double* h, double* hu, double* hv) {
-  const int K = s->K, KS = s->KS, np = s->Np;
-  const size_t fs = (size_t)np * KS, bs = 3 * fs;
-  std::vector<T> q(2 * bs);
-  SWE_CUDA(cudaMemcpyAsync(q.data(), s->ws + s->lay.q, q.size() * sizeof(T), cudaMemcpyDeviceToHost,
-                           s->stream));
+// Current state in the caller's layout ([K][Np] FP64 arrays, depth h): unpacked
+// on the device into the staging region, then one copy per array (any of h, hu,
+// hv may be NULL).
+int download_state(const swe_solver* cs, double* h, double* hu, double* hv) {
+  swe_solver* s = const_cast<swe_solver*>(cs);
+  const size_t n = (size_t)s->K * s->Np;
+  double* x = reinterpret_cast<double*>(s->ws + s->lay.xfer);
+  const double* bc = reinterpret_cast<const double*>(s->ws + s->lay.bcaller);
+  const int* ip = reinterpret_cast<const int*>(s->ws + s->lay.iperm);
+  const swe::Sched sc = sched_of(s);
+  cudaError_t ce = s->fp64
+      ? swe::launch_unpack_state<double>(reinterpret_cast<const double*>(s->ws + s->lay.q), bc, ip, sc, s->k,
+                                         s->Np, x, s->stream)
+      : swe::launch_unpack_state<float>(reinterpret_cast<const float*>(s->ws + s->lay.q), bc, ip, sc, s->k,
+                                        s->Np, x, s->stream);
+  if (ce != cudaSuccess) return fail(SWE_ECUDA, std::string("state unpack: ") + cudaGetErrorString(ce));
+  s->launches++;
+  if (h) SWE_CUDA(cudaMemcpyAsync(h, x, n * 8, cudaMemcpyDeviceToHost, s->stream));
+  if (hu) SWE_CUDA(cudaMemcpyAsync(hu, x + n, n * 8, cudaMemcpyDeviceToHost, s->stream));
+  if (hv) SWE_CUDA(cudaMemcpyAsync(hv, x + 2 * n, n * 8, cudaMemcpyDeviceToHost, s->stream));
   SWE_CUDA(cudaStreamSynchronize(s->stream));
-  for (int e = 0; e < K; ++e) {
-    const int c = s->perm[e];
-    int l = 1;
-    while (l < s->L && e >= s->off[l]) ++l;
-    const int cur = (int)((s->k >> (l - 1)) & 1);
-    for (int j = 0; j < np; ++j) {
-      const size_t ci = (size_t)c * np + j, di = (size_t)cur * bs + (size_t)j * KS + e;
-      if (h) h[ci] = (double)q[di] - s->B_dev[ci];
-      if (hu) hu[ci] = (double)q[di + fs];
-      if (hv) hv[ci] = (double)q[di + 2 * fs];
-    }
-  }
   return SWE_OK;
-}
-
-int download_state(const swe_solver* s, double* h, double* hu, double* hv) {
-  return s->fp64 ? download_state_t<double>(s, h, hu, hv) : download_state_t<float>(s, h, hu, hv);
 }
 
 // current state in device precision, caller order, [3][K][Np] (no conversion)
@@ -957,12 +940,31 @@ int swe_set_bathymetry(swe_solver* s, const double* B) {
 int swe_set_state(swe_solver* s, const double* h, const double* hu, const double* hv) {
   if (!s || !h || !hu || !hv) return fail(SWE_EINVAL, "NULL argument");
   if (!s->have_B) return fail(SWE_EINVAL, "swe_set_bathymetry must come first");
+  // the caller's arrays go to the device as they are; the finiteness check, the
+  // level-order permutation, eta = h + B and the precision conversion run there
   const size_t n = (size_t)s->K * s->Np;
-  for (size_t i = 0; i < n; ++i)
-    if (!std::isfinite(h[i]) || !std::isfinite(hu[i]) || !std::isfinite(hv[i]))
-      return fail(SWE_EINVAL, "non-finite state");
-  int rc = s->fp64 ? upload_state_t<double>(s, h, hu, hv) : upload_state_t<float>(s, h, hu, hv);
-  if (rc) return rc;
+  double* x = reinterpret_cast<double*>(s->ws + s->lay.xfer);
+  int* flag = reinterpret_cast<int*>(s->ws + s->lay.xflag);
+  SWE_CUDA(cudaMemcpyAsync(x, h, n * 8, cudaMemcpyHostToDevice, s->stream));
+  SWE_CUDA(cudaMemcpyAsync(x + n, hu, n * 8, cudaMemcpyHostToDevice, s->stream));
+  SWE_CUDA(cudaMemcpyAsync(x + 2 * n, hv, n * 8, cudaMemcpyHostToDevice, s->stream));
+  SWE_CUDA(cudaMemsetAsync(flag, 0, 4, s->stream));
+  SWE_CUDA(swe::launch_check_finite(x, 3 * n, flag, s->stream));
+  int bad = 0;
+  SWE_CUDA(cudaMemcpyAsync(&bad, flag, 4, cudaMemcpyDeviceToHost, s->stream));
+  SWE_CUDA(cudaStreamSynchronize(s->stream));
+  s->launches++;
+  if (bad) return fail(SWE_EINVAL, "non-finite state");
+  const double* bc = reinterpret_cast<const double*>(s->ws + s->lay.bcaller);
+  const int* ip = reinterpret_cast<const int*>(s->ws + s->lay.iperm);
+  cudaError_t ce = s->fp64
+      ? swe::launch_pack_state<double>(x, bc, ip, s->K, s->KS, s->Np, reinterpret_cast<double*>(s->ws + s->lay.q),
+                                       s->stream)
+      : swe::launch_pack_state<float>(x, bc, ip, s->K, s->KS, s->Np, reinterpret_cast<float*>(s->ws + s->lay.q),
+                                      s->stream);
+  if (ce != cudaSuccess) return fail(SWE_ECUDA, std::string("state pack: ") + cudaGetErrorString(ce));
+  s->launches++;
+  int rc;
   if ((rc = reset_counters(s))) return rc;
   s->t0 = 0.0;
   s->dof_updates = 0;

@@ -187,10 +187,18 @@ class Solver:
         nat.check(nat.lib().swe_limit(self.handle, int(mask)), "swe_limit")
 
     # -- outputs ------------------------------------------------------------
-    def get_state(self):
-        h = np.zeros((self.K, self.Np))
-        hu = np.zeros_like(h)
-        hv = np.zeros_like(h)
+    def get_state(self, out=None):
+        """(h, hu, hv, t); out = three preallocated (K, Np) float64 C-contiguous arrays
+        (for example views of page-locked memory) to fill instead of new ones."""
+        if out is None:
+            h = np.zeros((self.K, self.Np))
+            hu = np.zeros_like(h)
+            hv = np.zeros_like(h)
+        else:
+            h, hu, hv = out
+            for a in out:
+                if a.dtype != np.float64 or a.shape != (self.K, self.Np) or not a.flags.c_contiguous:
+                    raise ValueError("out arrays must be C-contiguous float64 of shape (K, Np)")
         t = C.c_double()
         nat.check(nat.lib().swe_get_state(self.handle, nat.dptr(h), nat.dptr(hu), nat.dptr(hv), C.byref(t)),
                   "swe_get_state")

@@ -212,3 +212,26 @@ def test_mass_conservation_and_stats():
     _report("mass fp64", drift=abs(st["mass"] - m0) / m0)
     assert abs(st["mass"] - m0) < 1e-13 * m0 * 50
     assert st["dof_updates"] == 50 * integ.model.mesh.K * 10 * 3 and not st["nonfinite"]
+
+
+def test_set_state_rejects_nonfinite_and_keeps_state():
+    import paper_1403_1661_gb300 as P
+    from paper_1403_1661_gb300 import _native as nat
+    scn = sc.tsunami(nx=24, ny=6, N=3, nlevels=3)
+    s = P.solver_from_scenario(scn, precision="fp32tc")
+    s.step(1)
+    before = s.get_state()
+    h, hu, hv = (np.array(a) for a in before[:3])
+    hu[3, 2] = np.nan
+    with pytest.raises(nat.SWEError) as ei:
+        s.set_state(h, hu, hv)
+    assert ei.value.code == nat.SWE_EINVAL
+    after = s.get_state()
+    for x, y in zip(before[:3], after[:3]):
+        assert np.array_equal(x, y)
+    # pinned output buffers give the same values
+    import torch
+    outs = tuple(torch.empty((s.K, s.Np), dtype=torch.float64, pin_memory=True).numpy() for _ in range(3))
+    got = s.get_state(out=outs)
+    for x, y in zip(before[:3], got[:3]):
+        assert np.array_equal(x, y)
