@@ -36,6 +36,13 @@
 // cancellations, and a lake at rest at any level gives R = 0 exactly. Where both
 // sides of a face are wet the jump h*^+ - h*^- is computed as eta^+ - eta^-,
 // which it equals, instead of as a difference of two large depths.
+// Dry elements (the positivity pass's flag) take the depth form instead:
+// p_d = g/2 h'^2 and source -g h' grad B', h' = eta' - B'. It differs from
+// p'', -g eta' grad B' by the static pair -g/2 B'^2, -g B' grad B', whose volume,
+// own-side face and source terms cancel exactly; with it a uniform film on a
+// slope (h' = 0) has no cancelling terms left, as a lake at rest (eta' = 0) has
+// none in the surface form. With md = 1 for the depth form, 0 for the surface
+// form: p = g/2 (eta' - md B')(eta' - (2 - md) B'), source -g (eta' - md B') grad B'.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -183,30 +190,34 @@ __device__ __forceinline__ void stage_ops(T* sops, const T* __restrict__ gops) {
 // --------------------------------------------------------------------------
 // the well-balanced local Lax-Friedrichs flux (pre-balanced form), own side "-"
 
+// Traces at a face point relative to the face's reference point (Ef, Bf): surface
+// e = eta - Ef, bed b = B - Bf, and the momenta.
 template <typename T>
 struct Trace {
-  T eta, hu, hv, B;
+  T e, hu, hv, b;
 };
 
 // (nx, ny) unit outward normal, (vx, vy) = (sJ/J) (nx, ny), hs = sJ/J / 2; the
 // returned fluxes are already scaled by sJ/J for the lift. hg = g/2, qg = g/4.
-// epm, epp, bpm: eta^-, eta^+ and B^- relative to the element's eta0, B0; the
-// own-side pressure is p'' (element reference split above).
+// hf = Ef - Bf, the depth at the face's reference point, so depths are
+// hf + (e - b) without cancelling two large values. epm, bpm: eta^- and B^-
+// relative to the element's own eta0, B0; the own-side pressure is p'' or p_d by
+// md (element reference split above).
 template <typename T>
-__device__ __forceinline__ void wb_flux(const Trace<T>& m, const Trace<T>& p, T epm, T epp, T bpm, T nx, T ny,
-                                        T vx, T vy, T hs, T g, T hg, T qg, T h0, T& f0, T& f1, T& f2) {
-  const T hm = m.eta - m.B, hp = p.eta - p.B;
+__device__ __forceinline__ void wb_flux(const Trace<T>& m, const Trace<T>& p, T hf, T epm, T bpm, T md, T nx,
+                                        T ny, T vx, T vy, T hs, T g, T hg, T qg, T h0, T& f0, T& f1, T& f2) {
+  const T hm = hf + (m.e - m.b), hp = hf + (p.e - p.b);
   const T im = hm > h0 ? recip(hm) : T(0), ip = hp > h0 ? recip(hp) : T(0);
   const T um = m.hu * im, vm = m.hv * im;
   const T up = p.hu * ip, vp = p.hv * ip;
-  const T bmax = tmax(m.B, p.B);
+  const T bmax = tmax(m.b, p.b);
   // hydrostatically reconstructed depths and the normal mass fluxes they carry
-  const T sm = tmax(T(0), m.eta - bmax), sp = tmax(T(0), p.eta - bmax);
+  const T sm = tmax(T(0), hf + (m.e - bmax)), sp = tmax(T(0), hf + (p.e - bmax));
   const T unm = um * nx + vm * ny, unp = up * nx + vp * ny;
   const T lam = tmax(fabs(unm) + sqrt_nn(g * sm), fabs(unp) + sqrt_nn(g * sp));
   const T Fm = sm * unm, Fp = sp * unp;
-  const T ds = (sm > T(0) && sp > T(0)) ? epp - epm : sp - sm;
-  const T pres = hg * epm * (epm - T(2) * bpm) + qg * ds * (sp + sm);
+  const T ds = (sm > T(0) && sp > T(0)) ? p.e - m.e : sp - sm;
+  const T pres = hg * (epm - md * bpm) * (epm - (T(2) - md) * bpm) + qg * ds * (sp + sm);
   f0 = hs * ((Fm + Fp) - lam * ds);
   f1 = hs * ((Fm * um + Fp * up) - lam * (sp * up - sm * um)) + pres * vx;
   f2 = hs * ((Fm * vm + Fp * vp) - lam * (sp * vp - sm * vm)) + pres * vy;
@@ -320,15 +331,15 @@ __device__ __forceinline__ void store_p1(T* __restrict__ p1, size_t ks, const T*
 }
 
 // Surface fluxes (Section 7.2) of element e: traces at the Gauss points of its
-// three faces and the well-balanced flux, scaled by sJ/J; emit(f, gq, F0, F1, F2)
-// receives the flux at Gauss point gq of face f. own(f, j) returns the element's
+// three faces and the well-balanced flux, scaled by sJ/J; emit(f, gq, F0, F1, F2,
+// vx, vy) receives the flux at Gauss point gq of face f and the face's (sJ/J) n. own(f, j) returns the element's
 // own field f (eta, hu, hv, B) at node j, so the caller decides whether the state
 // sits in registers or in shared memory. With kRolled the three faces run
 // through one copy of the face code (own() must then accept run-time node
 // indices); otherwise the face loop is unrolled.
 template <typename T, int N, bool kRolled, typename Own, typename Emit>
 __device__ __forceinline__ void surface_fluxes(const StageParams<T>& p, const T* __restrict__ sops, int e,
-                                               long long k, const Own& own, T rx, T ry, T sx, T sy,
+                                               long long k, const Own& own, T rx, T ry, T sx, T sy, T md,
                                                Emit&& emit) {
   using D = Dims<N>;
   using O = OpLayout<N>;
@@ -348,8 +359,14 @@ __device__ __forceinline__ void surface_fluxes(const StageParams<T>& p, const T*
     const T v2 = vxn * vxn + vyn * vyn;
     const T iv = rsqrt_t(v2);
     const T nx = vxn * iv, ny = vyn * iv, hs = T(0.5) * v2 * iv;
-    // neighbour face-node values, in this element's traversal order
+    // Neighbour face-node values in the NEIGHBOUR's own order: its trace at this
+    // element's Gauss point gq is its own point NG-1-gq, evaluated below with the
+    // same operands in the same order as the neighbour evaluates it, relative to
+    // the same face reference (node 0 of the lower-numbered element of the pair),
+    // so both sides of a face see bit-identical traces and take the same wet/dry
+    // and velocity decisions (the mass flux stays exactly antisymmetric).
     T ne[NFP], nu[NFP], nv[NFP], nB[NFP];
+    T Ef = E0, Bf = B0;   // face reference: the own node 0 unless the neighbour is lower
     const int nb = f == 0 ? cn.x : (f == 1 ? cn.y : cn.z);
     if (nb >= 0) {
       const int fn = (cn.w >> (2 * f)) & 3;
@@ -364,12 +381,16 @@ __device__ __forceinline__ void surface_fluxes(const StageParams<T>& p, const T*
       const size_t sn = half ? 1 : ks, sf = half ? (size_t)NPP : fstride;   // node, field strides
 #pragma unroll
       for (int m = 0; m < NFP; ++m) {
-        const int jn = face_node_rt(N, fn, NFP - 1 - m);
+        const int jn = face_node_rt(N, fn, m);
         const size_t idx = (size_t)jn * sn;
-        ne[m] = __ldg(qn + idx) - E0;   // relative to the own E0, like oe
+        ne[m] = __ldg(qn + idx);
         nu[m] = __ldg(qn + sf + idx);
         nv[m] = __ldg(qn + 2 * sf + idx);
-        nB[m] = __ldg(p.s.B + nb + (size_t)jn * ks) - B0;   // relative to the own B0, like oB
+        nB[m] = __ldg(p.s.B + nb + (size_t)jn * ks);
+      }
+      if (phase == 0 && nb < e) {   // an active neighbour numbered lower: its node 0
+        Ef = __ldg(qn);
+        Bf = __ldg(p.s.B + nb);
       }
       if (phase != 0 && !half) {  // other fractions: Adams-Bashforth polynomial at t_k
         const int depth = an + 1 < 3 ? (int)(an + 1) : 3;
@@ -381,59 +402,62 @@ __device__ __forceinline__ void surface_fluxes(const StageParams<T>& p, const T*
           const T* rs = p.s.ring + (size_t)((an - s) % 3) * bstride + nb;
 #pragma unroll
           for (int m = 0; m < NFP; ++m) {
-            const size_t idx = (size_t)face_node_rt(N, fn, NFP - 1 - m) * ks;
-            ne[m] += ws * __ldg(rs + idx);   // (ne keeps its E0 offset: R carries none)
+            const size_t idx = (size_t)face_node_rt(N, fn, m) * ks;
+            ne[m] += ws * __ldg(rs + idx);
             nu[m] += ws * __ldg(rs + fstride + idx);
             nv[m] += ws * __ldg(rs + 2 * fstride + idx);
           }
         }
       }
     }
-    // own face-node values, read once per face; surface and bed relative to E0, B0
+    // own face-node values relative to the face reference, read once per face
     T oe[NFP], ou[NFP], ov[NFP], oB[NFP];
 #pragma unroll
     for (int m = 0; m < NFP; ++m) {
       const int jn = face_node(N, f, m);
-      oe[m] = own(0, jn) - E0;
+      oe[m] = own(0, jn) - Ef;
       ou[m] = own(1, jn);
       ov[m] = own(2, jn);
-      oB[m] = own(3, jn) - B0;
+      oB[m] = own(3, jn) - Bf;
     }
-#pragma unroll 1
-    for (int gq = 0; gq < NG; ++gq) {
-      T i1[D::NFPP];
-      load_row<T, D::NFPP>(sops + O::I1D + gq * D::NFPP, i1);
-      Trace<T> tm = {0, 0, 0, 0}, tp;
-      T epm = 0, bpm = 0, epp;
+    if (nb >= 0) {
 #pragma unroll
       for (int m = 0; m < NFP; ++m) {
-        epm += i1[m] * oe[m];
+        ne[m] -= Ef;
+        nB[m] -= Bf;
+      }
+    }
+    const T hf = Ef - Bf;               // depth at the face reference
+    const T dE = Ef - E0, dB = Bf - B0; // face reference relative to the element's own
+#pragma unroll 1
+    for (int gq = 0; gq < NG; ++gq) {
+      T i1[D::NFPP], i1n[D::NFPP];
+      load_row<T, D::NFPP>(sops + O::I1D + gq * D::NFPP, i1);
+      load_row<T, D::NFPP>(sops + O::I1D + (NG - 1 - gq) * D::NFPP, i1n);
+      Trace<T> tm = {0, 0, 0, 0}, tp;
+#pragma unroll
+      for (int m = 0; m < NFP; ++m) {
+        tm.e += i1[m] * oe[m];
         tm.hu += i1[m] * ou[m];
         tm.hv += i1[m] * ov[m];
-        bpm += i1[m] * oB[m];
+        tm.b += i1[m] * oB[m];
       }
-      tm.eta = E0 + epm;
-      tm.B = B0 + bpm;
       if (nb >= 0) {
         tp = {0, 0, 0, 0};
 #pragma unroll
         for (int m = 0; m < NFP; ++m) {
-          tp.eta += i1[m] * ne[m];
-          tp.hu += i1[m] * nu[m];
-          tp.hv += i1[m] * nv[m];
-          tp.B += i1[m] * nB[m];
+          tp.e += i1n[m] * ne[m];
+          tp.hu += i1n[m] * nu[m];
+          tp.hv += i1n[m] * nv[m];
+          tp.b += i1n[m] * nB[m];
         }
-        epp = tp.eta;
-        tp.eta += E0;
-        tp.B += B0;
       } else {  // reflecting wall: mirror the normal momentum
         const T mn = tm.hu * nx + tm.hv * ny;
-        tp = {tm.eta, tm.hu - T(2) * mn * nx, tm.hv - T(2) * mn * ny, tm.B};
-        epp = epm;
+        tp = {tm.e, tm.hu - T(2) * mn * nx, tm.hv - T(2) * mn * ny, tm.b};
       }
       T f0, f1, f2;
-      wb_flux<T>(tm, tp, epm, epp, bpm, nx, ny, vxn, vyn, hs, g, hg, qg, h0, f0, f1, f2);
-      emit(f, gq, f0, f1, f2);
+      wb_flux<T>(tm, tp, hf, tm.e + dE, tm.b + dB, md, nx, ny, vxn, vyn, hs, g, hg, qg, h0, f0, f1, f2);
+      emit(f, gq, f0, f1, f2, vxn, vyn);
     }
   }
 }
@@ -442,12 +466,12 @@ __device__ __forceinline__ void surface_fluxes(const StageParams<T>& p, const T*
 // by point (the SIMT stage kernel).
 template <typename T, int N, bool kRolled = false, typename Own>
 __device__ __forceinline__ void surface_lift(const StageParams<T>& p, const T* __restrict__ sops, int e,
-                                             long long k, const Own& own, T rx, T ry, T sx, T sy,
+                                             long long k, const Own& own, T rx, T ry, T sx, T sy, T md,
                                              T (&R0)[Dims<N>::NP], T (&R1)[Dims<N>::NP],
                                              T (&R2)[Dims<N>::NP]) {
   using D = Dims<N>;
   constexpr int NP = D::NP, NPP = D::NPP, NG = D::NG;
-  surface_fluxes<T, N, kRolled>(p, sops, e, k, own, rx, ry, sx, sy, [&](int f, int gq, T f0, T f1, T f2) {
+  surface_fluxes<T, N, kRolled>(p, sops, e, k, own, rx, ry, sx, sy, md, [&](int f, int gq, T f0, T f1, T f2, T, T) {
     T lg[NPP];
     load_row<T, NPP>(sops + OpLayout<N>::LGT + (f * NG + gq) * NPP, lg);
 #pragma unroll
@@ -622,6 +646,7 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
     load_nodes<T, NP, NPP>(p.s.B + e, ks, bb);
     const T rx = __ldg(p.s.geo + 4 * (size_t)e + 0), ry = __ldg(p.s.geo + 4 * (size_t)e + 1);
     const T sx = __ldg(p.s.geo + 4 * (size_t)e + 2), sy = __ldg(p.s.geo + 4 * (size_t)e + 3);
+    const T md = p.s.dry[e] ? T(1) : T(0);   // depth form of the pressure for dry elements
 
     T R0[NP], R1[NP], R2[NP];
 #pragma unroll
@@ -652,11 +677,12 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
       // cF1 = rx F + ry G and cF2 = sx F + sy G, with the momentum rows written
       // through the mass row: rx (hu u + p) + ry hv u = u (rx hu + ry hv) + rx p;
       // p = p'' (element reference split)
-      const T pr = hg * ec * (ec - T(2) * bc);
+      const T ep = ec - md * bc;
+      const T pr = hg * ep * (ec - (T(2) - md) * bc);
       const T a0 = rx * huc + ry * hvc, b0 = sx * huc + sy * hvc;
       const T a1 = u * a0 + rx * pr, a2 = v * a0 + ry * pr;
       const T b1 = u * b0 + sx * pr, b2 = v * b0 + sy * pr;
-      const T gm = -g * ec;
+      const T gm = -g * ep;
       const T S1 = gm * (rx * brc + sx * bsc), S2 = gm * (ry * brc + sy * bsc);
       T prt[NPP], pst[NPP], pt[NPP];
       load_row<T, NPP>(sops + O::PRT + c * NPP, prt);
@@ -671,7 +697,7 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
     }
 
     auto own = [&](int f, int jn) -> T { return f == 0 ? eta[jn] : (f == 1 ? hu[jn] : (f == 2 ? hv[jn] : bb[jn])); };
-    surface_lift<T, N>(p, sops, e, k, own, rx, ry, sx, sy, R0, R1, R2);
+    surface_lift<T, N>(p, sops, e, k, own, rx, ry, sx, sy, md, R0, R1, R2);
     add_reference_pressure<T, N>(sops, eta, bb, g, rx, ry, sx, sy, R1, R2);
     commit_and_limit<T, N>(p, sops, e, lev, a, eta, hu, hv, bb, rx, ry, sx, sy, R0, R1, R2, &injected);
   }

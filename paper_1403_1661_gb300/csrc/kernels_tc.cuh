@@ -77,11 +77,13 @@ struct TcSmem {
   using D = Dims<N>;
   using C = TcDims<N>;
   // per warp: state [4 fields][KP nodes][LS]; surface fluxes [3][KF face points][LS],
-  // later R [3][NPT nodes][LS] in the same rows (field stride FR); geo [32][4]
+  // later R [3][NPT nodes][LS] in the same rows (field stride FR); geo [32][4];
+  // pressure form md [32]
   static constexpr int STATE = 0;
   static constexpr int FRT = STATE + 4 * C::KP * LS;
   static constexpr int GEO = FRT + 3 * C::FR * LS;
-  static constexpr int WARP = GEO + 32 * 4;              // floats per warp
+  static constexpr int MD = GEO + 32 * 4;
+  static constexpr int WARP = MD + 32;                   // floats per warp
   static constexpr int OPS = OpLayout<N>::TAIL;          // floats of per-element operators (staged first)
   static constexpr int BYTES = (OPS + kTcWarps * WARP) * 4;
 };
@@ -112,6 +114,7 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
   float* s_state = sw + SM::STATE;
   float* s_FR = sw + SM::FRT;
   float* s_geo = sw + SM::GEO;
+  float* s_md = sw + SM::MD;
 
   const Sched& sc = p.sc;
   const long long k = (*p.s.macro) * (1LL << (sc.L - 1)) + p.j;
@@ -137,7 +140,9 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
 #pragma unroll
       for (int i = 0; i < NP; ++i) s_state[(3 * KP + i) * LS + lane] = __ldg(p.s.B + e + i * ks);
       reinterpret_cast<float4*>(s_geo)[lane] = __ldg(reinterpret_cast<const float4*>(p.s.geo) + e);
+      s_md[lane] = p.s.dry[e] ? 1.f : 0.f;   // depth form of the pressure for dry elements
     } else {
+      s_md[lane] = 0.f;
 #pragma unroll
       for (int f = 0; f < 4; ++f)
 #pragma unroll
@@ -183,12 +188,18 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
         const float4 ge = reinterpret_cast<const float4*>(s_geo)[lane];
         const float* my = s_state + lane;
         auto own = [&](int f, int jn) -> float { return my[(f * KP + jn) * LS]; };
-        surface_fluxes<float, N, true>(p, sops, e, k, own, ge.x, ge.y, ge.z, ge.w,
-                                       [&](int f, int gq, float f0, float f1, float f2) {
+        // the element's node-0 flux, subtracted here and from the volume fluxes (see
+        // the reference flux below): constant fluxes contribute nothing to R
+        const float hu0 = my[(1 * KP) * LS], hv0 = my[(2 * KP) * LS], d0 = my[0] - my[(3 * KP) * LS];
+        const float id0 = d0 > h0 ? recip(d0) : 0.f;
+        const float u0 = hu0 * id0, v0 = hv0 * id0;
+        surface_fluxes<float, N, true>(p, sops, e, k, own, ge.x, ge.y, ge.z, ge.w, s_md[lane],
+                                       [&](int f, int gq, float f0, float f1, float f2, float vx, float vy) {
                                          const int q = f * NG + gq;
-                                         sf[(0 * FR + q) * LS] = f0;
-                                         sf[(1 * FR + q) * LS] = f1;
-                                         sf[(2 * FR + q) * LS] = f2;
+                                         const float fr = hu0 * vx + hv0 * vy;
+                                         sf[(0 * FR + q) * LS] = f0 - fr;
+                                         sf[(1 * FR + q) * LS] = f1 - u0 * fr;
+                                         sf[(2 * FR + q) * LS] = f2 - v0 * fr;
                                        });
       } else {
         for (int q = 0; q < 3 * NG; ++q) {
@@ -210,15 +221,21 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
       // derivatives vanish (Ic B = B0 + Ic (B - B0), Icr B = Icr (B - B0)), so only
       // the within-element variation carries the split-product error, whether the
       // bed is thousands of metres deep or the water a millimetre thin.
-      const float cE0 = s_state[r0], cE1 = s_state[r1];
-      const float cB0 = s_state[(3 * KP) * LS + r0], cB1 = s_state[(3 * KP) * LS + r1];
+      // All four fields enter relative to their node-0 values (c0 for row r0, c1 for r1).
+      float c0[4], c1[4];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        c0[f] = s_state[(f * KP) * LS + r0];
+        c1[f] = s_state[(f * KP) * LS + r1];
+      }
+      const float cE0 = c0[0], cE1 = c1[0], cB0 = c0[3], cB1 = c1[3];
       uint32_t ah[4][KSTEP][4], al[4][KSTEP][4];
 #pragma unroll
       for (int f = 0; f < 4; ++f)
 #pragma unroll
         for (int ks = 0; ks < KSTEP; ++ks) {
           const float* sn = s_state + (f * KP + 16 * ks + 2 * t) * LS;   // node 16ks + 2t
-          const float d0 = f == 3 ? cB0 : (f == 0 ? cE0 : 0.f), d1 = f == 3 ? cB1 : (f == 0 ? cE1 : 0.f);
+          const float d0 = c0[f], d1 = c1[f];
           const float2 v00 = make_float2(sn[r0] - d0, sn[LS + r0] - d0);
           const float2 v10 = make_float2(sn[r1] - d1, sn[LS + r1] - d1);
           const float2 v01 = make_float2(sn[8 * LS + r0] - d0, sn[9 * LS + r0] - d0);
@@ -230,6 +247,21 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
         }
       const float4 ge0 = reinterpret_cast<const float4*>(s_geo)[r0];
       const float4 ge1 = reinterpret_cast<const float4*>(s_geo)[r1];
+      // Reference flux: the volume fluxes cF1, cF2 of each row's node-0 state. A
+      // constant flux adds nothing to R (its volume term and its own-side lift
+      // cancel exactly), so it is subtracted here and from the surface fluxes and
+      // the split products see only the flux's variation over the element (the
+      // pressure p'' vanishes at node 0).
+      float fr0[6], fr1[6];
+      {
+        const float d0 = cE0 - cB0, d1 = cE1 - cB1;
+        const float i0 = d0 > h0 ? recip(d0) : 0.f, i1v = d1 > h0 ? recip(d1) : 0.f;
+        const float u0 = c0[1] * i0, v0 = c0[2] * i0, u1 = c1[1] * i1v, v1 = c1[2] * i1v;
+        const float a0r = ge0.x * c0[1] + ge0.y * c0[2], b0r = ge0.z * c0[1] + ge0.w * c0[2];
+        const float a1r = ge1.x * c1[1] + ge1.y * c1[2], b1r = ge1.z * c1[1] + ge1.w * c1[2];
+        fr0[0] = a0r; fr0[1] = u0 * a0r; fr0[2] = v0 * a0r; fr0[3] = b0r; fr0[4] = u0 * b0r; fr0[5] = v0 * b0r;
+        fr1[0] = a1r; fr1[1] = u1 * a1r; fr1[2] = v1 * a1r; fr1[3] = b1r; fr1[4] = u1 * b1r; fr1[5] = v1 * b1r;
+      }
       float Racc[3][NT][4];
 #pragma unroll
       for (int f = 0; f < 3; ++f)
@@ -299,7 +331,8 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
           const float4 ge = c < 2 ? ge0 : ge1;
           const float rx = ge.x, ry = ge.y, sx = ge.z, sy = ge.w;
           // eta - eta0 and B - B0 at the point (element reference split)
-          const float ec = acc[0][c], huc = acc[1][c], hvc = acc[2][c];
+          const float ec = acc[0][c];
+          const float huc = (c < 2 ? c0[1] : c1[1]) + acc[1][c], hvc = (c < 2 ? c0[2] : c1[2]) + acc[2][c];
           const float bpc = acc[3][c];
           const float brc = acc[4][c], bsc = acc[5][c];
           const float hc = (c < 2 ? cE0 - cB0 : cE1 - cB1) + (ec - bpc);
@@ -307,15 +340,18 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
           const float u = huc * ih, v = hvc * ih;
           // momentum rows of cF1, cF2 written through the mass row; p'' (the
           // reference part is added in strong form before the commit)
-          const float pr = hg * ec * (ec - 2.f * bpc);
+          const float md = c < 2 ? s_md[r0] : s_md[r1];
+          const float ep = ec - md * bpc;
+          const float pr = hg * ep * (ec - (2.f - md) * bpc);
           const float a0 = rx * huc + ry * hvc, b0 = sx * huc + sy * hvc;
-          fl[0][c] = a0;
-          fl[1][c] = u * a0 + rx * pr;
-          fl[2][c] = v * a0 + ry * pr;
-          fl[3][c] = b0;
-          fl[4][c] = u * b0 + sx * pr;
-          fl[5][c] = v * b0 + sy * pr;
-          const float gm = -gg * ec;
+          const float* fr = c < 2 ? fr0 : fr1;
+          fl[0][c] = a0 - fr[0];
+          fl[1][c] = (u * a0 + rx * pr) - fr[1];
+          fl[2][c] = (v * a0 + ry * pr) - fr[2];
+          fl[3][c] = b0 - fr[3];
+          fl[4][c] = (u * b0 + sx * pr) - fr[4];
+          fl[5][c] = (v * b0 + sy * pr) - fr[5];
+          const float gm = -gg * ep;
           fl[6][c] = gm * (rx * brc + sx * bsc);
           fl[7][c] = gm * (ry * brc + sy * bsc);
         }

@@ -283,6 +283,7 @@ void pack_ops_n(const swe::RefElem& e, std::vector<double>& o, std::vector<uint3
     for (int j = 0; j < np; ++j) o[O::T1 + (size_t)v * npp + j] = e.T1[(size_t)v * np + j];
   for (int j = 0; j < np; ++j)
     for (int v = 0; v < 3; ++v) o[O::BARY + (size_t)j * 4 + v] = e.bary[(size_t)j * 3 + v];
+
   // nodal differentiation: d/dr of the interpolant has degree N-1, so projecting
   // its cubature values back onto P_N (P = M^-1 Ic^T W) recovers it: Dr = P Icr
   for (int i = 0; i < np; ++i)
