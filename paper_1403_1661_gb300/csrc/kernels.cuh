@@ -176,10 +176,11 @@ __host__ __device__ constexpr int face_node(int N, int f, int m) {
 
 __device__ __forceinline__ int face_node_rt(int N, int f, int m) { return face_node(N, f, m); }
 
-// Stage the operator block into shared memory (all threads of the CTA).
-template <typename T, int N>
+// Stage the first S entries of the operator block into shared memory (all threads
+// of the CTA): the whole block for the SIMT stage kernel, the per-element
+// operators [0, TAIL) for the limiter kernels.
+template <typename T, int N, int S = OpLayout<N>::SIZE>
 __device__ __forceinline__ void stage_ops(T* sops, const T* __restrict__ gops) {
-  constexpr int S = OpLayout<N>::SIZE;
   using V = Vec16<T>;
   const typename V::type* src = reinterpret_cast<const typename V::type*>(gops);
   typename V::type* dst = reinterpret_cast<typename V::type*>(sops);
@@ -713,7 +714,7 @@ __global__ void __launch_bounds__(kBlock) k_positivity(LimitParams<T> p) {
   constexpr int NP = D::NP, NPP = D::NPP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sops = reinterpret_cast<T*>(smem_raw);
-  stage_ops<T, N>(sops, p.s.ops);
+  stage_ops<T, N, OpLayout<N>::TAIL>(sops, p.s.ops);
   const Sched& sc = p.sc;
   const long long k = (*p.s.macro) * (1LL << (sc.L - 1)) + p.j;
   const size_t ks = (size_t)sc.KS, fstride = (size_t)NP * ks, bstride = 3 * fstride;
@@ -768,7 +769,7 @@ __global__ void __launch_bounds__(kBlock) k_tvb(LimitParams<T> p) {
   constexpr int NP = D::NP, NPP = D::NPP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sops = reinterpret_cast<T*>(smem_raw);
-  stage_ops<T, N>(sops, p.s.ops);
+  stage_ops<T, N, OpLayout<N>::TAIL>(sops, p.s.ops);
   const Sched& sc = p.sc;
   const long long k = (*p.s.macro) * (1LL << (sc.L - 1)) + p.j;
   const T g = (T)p.ph.g, h0 = (T)p.ph.h0;

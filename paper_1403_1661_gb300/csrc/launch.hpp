@@ -11,7 +11,8 @@ namespace swe {
 // Per (precision, order) kernel configuration: shared-memory bytes of the
 // operator block and the number of CTAs that fill the GPU once.
 struct KernelCfg {
-  int smem_bytes = 0;
+  int smem_bytes = 0;      // the whole operator block (SIMT stage kernel)
+  int smem_lim = 0;        // the per-element operators (limiter kernels)
   int grid_stage = 0, grid_pos = 0, grid_tvb = 0, grid_stats = 0;
   int smem_tc = 0, grid_tc = 0;   // tensor-core stage kernel (FP32 only)
 };
