@@ -787,9 +787,13 @@ __global__ void __launch_bounds__(kBlock) k_tvb(LimitParams<T> p) {
     const int cur = (int)((a + p.post_stage) & 1);
     const size_t ks = (size_t)sc.KS, fstride = (size_t)NP * ks, bstride = 3 * fstride, eo = (size_t)e;
     T* q = p.s.q + cur * bstride;
-    const T rx = p.s.geo[4 * e], ry = p.s.geo[4 * e + 1], sx = p.s.geo[4 * e + 2], sy = p.s.geo[4 * e + 3];
-    // element means (eta, hu, hv) as stored by the positivity pass
-    const T u0[3] = {p.s.means[4 * (size_t)e], p.s.means[4 * (size_t)e + 1], p.s.means[4 * (size_t)e + 2]};
+    // 16-byte rows: geometry, element means (eta, hu, hv, -) as stored by the
+    // positivity pass, the neighbour-mean weights
+    T gm[4], u0[4], tg[8];
+    load_row_global<T, 4>(p.s.geo + 4 * eo, gm);
+    load_row_global<T, 4>(p.s.means + 4 * eo, u0);
+    load_row_global<T, 8>(p.s.tvbg + 8 * eo, tg);
+    const T rx = gm[0], ry = gm[1], sx = gm[2], sy = gm[3];
     // P1 part: vertex values of Pi1 q for eta, hu, hv (stored with the committed
     // state) and of Pi1 B (static)
     T vq[3][3], vb[3];
@@ -801,14 +805,12 @@ __global__ void __launch_bounds__(kBlock) k_tvb(LimitParams<T> p) {
       vb[v] = __ldg(p.s.vb + v * ks + eo);
     }
     // neighbour means; a wall face mirrors the normal momentum of the own mean
-    T un[3][3];
+    T un[3][4];
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
       const int nb = nbs[f];
       if (nb >= 0) {
-        un[f][0] = p.s.means[4 * (size_t)nb];
-        un[f][1] = p.s.means[4 * (size_t)nb + 1];
-        un[f][2] = p.s.means[4 * (size_t)nb + 2];
+        load_row_global<T, 4>(p.s.means + 4 * (size_t)nb, un[f]);
       } else {
         const T vxn = f == 0 ? -sx : (f == 1 ? rx + sx : -rx);
         const T vyn = f == 0 ? -sy : (f == 1 ? ry + sy : -ry);
@@ -835,12 +837,13 @@ __global__ void __launch_bounds__(kBlock) k_tvb(LimitParams<T> p) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const int jj = (cn.w >> (6 + 2 * i)) & 3;
-      const T al = p.s.tvbg[8 * (size_t)e + 2 * i], be = p.s.tvbg[8 * (size_t)e + 2 * i + 1];
+      const T al = tg[2 * i], be = tg[2 * i + 1];
       T dt_[3], dn[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         dt_[c] = T(0.5) * (vq[c][i] + vq[c][(i + 1) % 3]) - u0[c];
-        dn[c] = al * (un[i][c] - u0[c]) + be * (un[jj][c] - u0[c]);
+        const T uj = jj == 0 ? un[0][c] : (jj == 1 ? un[1][c] : un[2][c]);   // selects, no local array
+        dn[c] = al * (un[i][c] - u0[c]) + be * (uj - u0[c]);
       }
       const T mx = xr * dr[i] + xs * ds[i], my = yr * dr[i] + ys * ds[i];
       const T dist = sqrt(mx * mx + my * my);
