@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-ablation", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-scenarios", type=int, default=64)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
@@ -361,6 +362,11 @@ def run_ours(args):
                               "fp32_speedup": value / (d64 / (ms64 / 1e3))}
         del s64
 
+    # kernel-structure ablation (Section 7): one R evaluation of the whole mesh by the
+    # fused kernels and by the paper's three-kernel split with stored face traces
+    if rank == 0 and not args.no_ablation:
+        result["kernel_structure"] = run_ablation(s, P)
+
     # batched ensemble: uneven scenarios advanced by one graph launch per macro step
     if rank == 0 and not args.no_batch:
         result["batched"] = run_batched(args)
@@ -379,6 +385,46 @@ def run_ours(args):
         print(json.dumps(result), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def run_ablation(s, P, reps=10):
+    """ms per R evaluation (all elements, level-synchronous state) of each kernel
+    structure; L2 flushed (256 MB written) before every timed launch."""
+    import torch
+    from paper_1403_1661_gb300 import _native as nat
+    variants = [("fused_tc" if s.precision == nat.SWE_FP32_TC else "fused", nat.SWE_RHS_FUSED),
+                ("fused_simt_ops_in_smem", nat.SWE_RHS_FUSED_SIMT),
+                ("fused_simt_ops_in_global", nat.SWE_RHS_GLOBAL_OPS),
+                ("split_3_kernels_stored_traces", nat.SWE_RHS_SPLIT)]
+    if s.precision != nat.SWE_FP32_TC:
+        variants.pop(1)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=s.device)
+    dofs = 3 * s.K * s.Np
+    out = {"unit": "ms per R evaluation", "elements": s.K, "reps": reps, "l2": "flushed before each launch"}
+    base = None
+    for name, v in variants:
+        nbytes = s.rhs_scratch_bytes(v)
+        scratch = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=s.device) if nbytes else None
+        for _ in range(3):
+            s.rhs_variant(v, scratch)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(reps):
+            with torch.cuda.stream(s.stream):
+                flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s.stream)
+            s.rhs_variant(v, scratch)
+            e1.record(s.stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        ms = tot / reps
+        base = base or ms
+        out[name] = {"ms": ms, "dof_per_s": dofs / (ms / 1e3), "vs_first": ms / base,
+                     "scratch_mb": nbytes / 1e6}
+        del scratch
+    return out
 
 
 def run_batched(args, steps=5):

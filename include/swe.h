@@ -165,6 +165,37 @@ int swe_set_levels(swe_solver* solver, const int32_t* level, double dt_min);
  * the solver's stream. */
 int swe_rhs(swe_solver* solver, void* dev_R);
 
+/* ---- kernel-structure ablations of swe_rhs (Section 7) ------------------
+ * The same R(Q) as swe_rhs, computed by another kernel structure, for timing
+ * the design choices of Section 7 against the fused stage kernel:
+ *   SWE_RHS_FUSED       the solver's own kernel (identical to swe_rhs)
+ *   SWE_RHS_FUSED_SIMT  the fused kernel without tensor cores, operators in
+ *                       shared memory (the solver's kernel unless SWE_FP32_TC)
+ *   SWE_RHS_GLOBAL_OPS  the same, operators read from global memory through
+ *                       the L1 cache (the operator placement of Section 7.4)
+ *   SWE_RHS_SPLIT       three kernels as in Sections 7.1-7.3: traces at the
+ *                       face Gauss points (Q^g) stored in device memory, the
+ *                       volume term, the surface term from the stored traces
+ *                       of both sides
+ * Results agree with swe_rhs up to rounding (the split adds the volume and
+ * surface sums in another order); SWE_RHS_FUSED_SIMT and SWE_RHS_GLOBAL_OPS
+ * equal it bit for bit unless the solver uses SWE_FP32_TC. */
+#define SWE_RHS_FUSED 0
+#define SWE_RHS_FUSED_SIMT 1
+#define SWE_RHS_GLOBAL_OPS 2
+#define SWE_RHS_SPLIT 3
+
+/* Device scratch a variant needs: 0 except for SWE_RHS_SPLIT, whose traces
+ * (3 Ng x 4 values + 6 face references per element) and volume term (3 Np per
+ * element) live there. SWE_EINVAL for an unknown variant. */
+int swe_rhs_scratch_bytes(const swe_solver* solver, int variant, size_t* bytes);
+
+/* R(Q) by the given variant into dev_R (layout and precision as swe_rhs).
+ * dev_scratch: caller-owned device memory of at least
+ * swe_rhs_scratch_bytes() bytes, 256-byte aligned (NULL when that is 0);
+ * SWE_ENOMEM if it is smaller. Enqueued on the solver's stream. */
+int swe_rhs_variant(swe_solver* solver, int variant, void* dev_R, void* dev_scratch, size_t scratch_bytes);
+
 /* Advance n finest substeps of the multirate schedule (Algorithm 2). At every
  * substep k, the levels l with k mod 2^{l-1} = 0 evaluate R, take one
  * Adams-Bashforth step of 2^{l-1} dt_min and are limited. */

@@ -24,6 +24,11 @@ SWE_EUNSUPPORTED = -6
 SWE_FP64 = 0
 SWE_FP32 = 1
 SWE_FP32_TC = 2
+
+SWE_RHS_FUSED = 0
+SWE_RHS_FUSED_SIMT = 1
+SWE_RHS_GLOBAL_OPS = 2
+SWE_RHS_SPLIT = 3
 SWE_LIM_PP = 1
 SWE_LIM_TVB = 2
 
@@ -63,6 +68,8 @@ SIGNATURES = {
     "swe_setup_levels": (C.c_int, [_vp, _ip, _dp]),
     "swe_set_levels": (C.c_int, [_vp, _ip, C.c_double]),
     "swe_rhs": (C.c_int, [_vp, _vp]),
+    "swe_rhs_scratch_bytes": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_size_t)]),
+    "swe_rhs_variant": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_size_t]),
     "swe_substep": (C.c_int, [_vp, C.c_int32]),
     "swe_step": (C.c_int, [_vp, C.c_int32]),
     "swe_limit": (C.c_int, [_vp, C.c_int32]),

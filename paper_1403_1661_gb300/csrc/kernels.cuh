@@ -619,18 +619,80 @@ __device__ __forceinline__ void commit_and_limit(const StageParams<T>& p, const 
 // the stage kernel: R(Q) for one element (volume + surface + lift), then the
 // Adams-Bashforth commit and the positivity limiter (mode 0) or R only (mode 1)
 
+// Volume term N(Q) (Section 7.1) of one element, accumulated into R: interpolate
+// to the cubature points, volume flux and source there, project back.
 template <typename T, int N>
-__global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
+__device__ __forceinline__ void volume_term(const T* __restrict__ sops, const T (&eta)[Dims<N>::NPP],
+                                            const T (&hu)[Dims<N>::NPP], const T (&hv)[Dims<N>::NPP],
+                                            const T (&bb)[Dims<N>::NPP], T rx, T ry, T sx, T sy, T md, T g,
+                                            T h0, T (&R0)[Dims<N>::NP], T (&R1)[Dims<N>::NP],
+                                            T (&R2)[Dims<N>::NP]) {
   using D = Dims<N>;
   using O = OpLayout<N>;
   constexpr int NP = D::NP, NPP = D::NPP, NCUB = D::NCUB;
+  const T hg = T(0.5) * g;
+#pragma unroll 1
+  for (int c = 0; c < NCUB; ++c) {
+    T ic[NPP], icr[NPP], ics[NPP];
+    load_row<T, NPP>(sops + O::IC + c * NPP, ic);
+    load_row<T, NPP>(sops + O::ICR + c * NPP, icr);
+    load_row<T, NPP>(sops + O::ICS + c * NPP, ics);
+    // ec, bc, brc, bsc: of eta - eta0 and B - B0 (element reference split)
+    T ec = 0, huc = 0, hvc = 0, bc = 0, brc = 0, bsc = 0;
+#pragma unroll
+    for (int jn = 0; jn < NP; ++jn) {
+      const T ep = eta[jn] - eta[0], bp = bb[jn] - bb[0];
+      ec += ic[jn] * ep;
+      huc += ic[jn] * hu[jn];
+      hvc += ic[jn] * hv[jn];
+      bc += ic[jn] * bp;
+      brc += icr[jn] * bp;
+      bsc += ics[jn] * bp;
+    }
+    const T hc = (eta[0] - bb[0]) + (ec - bc);
+    const T ih = hc > h0 ? recip(hc) : T(0);
+    const T u = huc * ih, v = hvc * ih;
+    // cF1 = rx F + ry G and cF2 = sx F + sy G, with the momentum rows written
+    // through the mass row: rx (hu u + p) + ry hv u = u (rx hu + ry hv) + rx p;
+    // p = p'' (element reference split)
+    const T ep = ec - md * bc;
+    const T pr = hg * ep * (ec - (T(2) - md) * bc);
+    const T a0 = rx * huc + ry * hvc, b0 = sx * huc + sy * hvc;
+    const T a1 = u * a0 + rx * pr, a2 = v * a0 + ry * pr;
+    const T b1 = u * b0 + sx * pr, b2 = v * b0 + sy * pr;
+    const T gm = -g * ep;
+    const T S1 = gm * (rx * brc + sx * bsc), S2 = gm * (ry * brc + sy * bsc);
+    T prt[NPP], pst[NPP], pt[NPP];
+    load_row<T, NPP>(sops + O::PRT + c * NPP, prt);
+    load_row<T, NPP>(sops + O::PST + c * NPP, pst);
+    load_row<T, NPP>(sops + O::PT + c * NPP, pt);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      R0[i] += prt[i] * a0 + pst[i] * b0;
+      R1[i] += prt[i] * a1 + pst[i] * b1 + pt[i] * S1;
+      R2[i] += prt[i] * a2 + pst[i] * b2 + pt[i] * S2;
+    }
+  }
+}
+
+// kGlobalOps: the operators are read from global memory (through L1) instead of
+// the block's shared-memory copy (the operator-placement comparison of Section 7.4).
+template <typename T, int N, bool kGlobalOps = false>
+__global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
+  using D = Dims<N>;
+  constexpr int NP = D::NP, NPP = D::NPP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sops = reinterpret_cast<T*>(smem_raw);
-  stage_ops<T, N>(sops, p.s.ops);
+  const T* sops;
+  if constexpr (kGlobalOps) {
+    sops = p.s.ops;
+  } else {
+    stage_ops<T, N>(reinterpret_cast<T*>(smem_raw), p.s.ops);
+    sops = reinterpret_cast<const T*>(smem_raw);
+  }
 
   const Sched& sc = p.sc;
   const long long k = (*p.s.macro) * (1LL << (sc.L - 1)) + p.j;
-  const T g = (T)p.ph.g, h0 = (T)p.ph.h0, hg = T(0.5) * g;
+  const T g = (T)p.ph.g, h0 = (T)p.ph.h0;
   const size_t ks = (size_t)sc.KS;
   const size_t fstride = (size_t)NP * ks;            // between fields
   const size_t bstride = 3 * fstride;                // between buffers
@@ -654,48 +716,7 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
     for (int i = 0; i < NP; ++i) { R0[i] = 0; R1[i] = 0; R2[i] = 0; }
 
     // ---- volume term (Section 7.1): interpolate, flux + source, project ----
-#pragma unroll 1
-    for (int c = 0; c < NCUB; ++c) {
-      T ic[NPP], icr[NPP], ics[NPP];
-      load_row<T, NPP>(sops + O::IC + c * NPP, ic);
-      load_row<T, NPP>(sops + O::ICR + c * NPP, icr);
-      load_row<T, NPP>(sops + O::ICS + c * NPP, ics);
-      // ec, bc, brc, bsc: of eta - eta0 and B - B0 (element reference split)
-      T ec = 0, huc = 0, hvc = 0, bc = 0, brc = 0, bsc = 0;
-#pragma unroll
-      for (int jn = 0; jn < NP; ++jn) {
-        const T ep = eta[jn] - eta[0], bp = bb[jn] - bb[0];
-        ec += ic[jn] * ep;
-        huc += ic[jn] * hu[jn];
-        hvc += ic[jn] * hv[jn];
-        bc += ic[jn] * bp;
-        brc += icr[jn] * bp;
-        bsc += ics[jn] * bp;
-      }
-      const T hc = (eta[0] - bb[0]) + (ec - bc);
-      const T ih = hc > h0 ? recip(hc) : T(0);
-      const T u = huc * ih, v = hvc * ih;
-      // cF1 = rx F + ry G and cF2 = sx F + sy G, with the momentum rows written
-      // through the mass row: rx (hu u + p) + ry hv u = u (rx hu + ry hv) + rx p;
-      // p = p'' (element reference split)
-      const T ep = ec - md * bc;
-      const T pr = hg * ep * (ec - (T(2) - md) * bc);
-      const T a0 = rx * huc + ry * hvc, b0 = sx * huc + sy * hvc;
-      const T a1 = u * a0 + rx * pr, a2 = v * a0 + ry * pr;
-      const T b1 = u * b0 + sx * pr, b2 = v * b0 + sy * pr;
-      const T gm = -g * ep;
-      const T S1 = gm * (rx * brc + sx * bsc), S2 = gm * (ry * brc + sy * bsc);
-      T prt[NPP], pst[NPP], pt[NPP];
-      load_row<T, NPP>(sops + O::PRT + c * NPP, prt);
-      load_row<T, NPP>(sops + O::PST + c * NPP, pst);
-      load_row<T, NPP>(sops + O::PT + c * NPP, pt);
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        R0[i] += prt[i] * a0 + pst[i] * b0;
-        R1[i] += prt[i] * a1 + pst[i] * b1 + pt[i] * S1;
-        R2[i] += prt[i] * a2 + pst[i] * b2 + pt[i] * S2;
-      }
-    }
+    volume_term<T, N>(sops, eta, hu, hv, bb, rx, ry, sx, sy, md, g, h0, R0, R1, R2);
 
     auto own = [&](int f, int jn) -> T { return f == 0 ? eta[jn] : (f == 1 ? hu[jn] : (f == 2 ? hv[jn] : bb[jn])); };
     surface_lift<T, N>(p, sops, e, k, own, rx, ry, sx, sy, md, R0, R1, R2);

@@ -15,6 +15,8 @@ struct KernelCfg {
   int smem_lim = 0;        // the per-element operators (limiter kernels)
   int grid_stage = 0, grid_pos = 0, grid_tvb = 0, grid_stats = 0;
   int smem_tc = 0, grid_tc = 0;   // tensor-core stage kernel (FP32 only)
+  int grid_stage_g = 0;           // stage kernel with the operators in global memory
+  int grid_split_t = 0, grid_split_v = 0, grid_split_s = 0;   // kernel-split ablation
 };
 
 template <typename T>
@@ -27,6 +29,12 @@ struct Launchers {
   cudaError_t (*stats)(const DevState<T>&, const Sched&, int nblocks, double* partials,
                        cudaStream_t);
   int op_size;  // elements of the operator block
+  // Ablations of the fused stage kernel (R only, mode 1): the operators read from
+  // global memory; the three-kernel split with stored face traces. qg holds
+  // split_planes planes and rg 3 NP planes, each of stride KS.
+  cudaError_t (*stage_global_ops)(const StageParams<T>&, const KernelCfg&, cudaStream_t);
+  cudaError_t (*split_rhs)(const StageParams<T>&, T* qg, T* rg, const KernelCfg&, cudaStream_t);
+  int split_planes;
 };
 
 // Registered per order by kernels_n*.cu; nullptr when the order is not built.

@@ -1041,6 +1041,74 @@ int swe_rhs(swe_solver* s, void* dev_R) {
   return SWE_OK;
 }
 
+int swe_rhs_scratch_bytes(const swe_solver* s, int variant, size_t* bytes) {
+  if (!s || !bytes) return fail(SWE_EINVAL, "NULL argument");
+  if (variant < SWE_RHS_FUSED || variant > SWE_RHS_SPLIT) return fail(SWE_EINVAL, "unknown variant");
+  *bytes = 0;
+  if (variant == SWE_RHS_SPLIT) {
+    const int planes = s->fp64 ? s->ld->split_planes : s->lf->split_planes;
+    const size_t plane = (size_t)s->KS * s->ts;
+    *bytes = ((plane * planes + 255) / 256) * 256 + plane * 3 * s->Np;
+  }
+  return SWE_OK;
+}
+
+extern "C++" {
+namespace {
+
+template <typename T>
+int rhs_variant_t(swe_solver* s, const swe::Launchers<T>* lt, int variant, T* R, char* scratch) {
+  swe::StageParams<T> p;
+  p.s = dev_state<T>(s);
+  p.sc = sched_of(s);
+  p.ph = phys_of(s, s->prm.limiter_mask);
+  p.j = 0;
+  p.nactive = s->K;
+  p.mode = 1;
+  p.out = R;
+  p.perm = reinterpret_cast<const int*>(s->ws + s->lay.perm);
+  if (variant == SWE_RHS_FUSED) {
+    if (s->tc) {
+      SWE_CUDA(lt->stage_tc(p, s->cfg, s->stream));
+    } else {
+      SWE_CUDA(lt->stage(p, s->cfg, s->stream));
+    }
+    s->launches += 1;
+  } else if (variant == SWE_RHS_FUSED_SIMT) {
+    SWE_CUDA(lt->stage(p, s->cfg, s->stream));
+    s->launches += 1;
+  } else if (variant == SWE_RHS_GLOBAL_OPS) {
+    SWE_CUDA(lt->stage_global_ops(p, s->cfg, s->stream));
+    s->launches += 1;
+  } else {
+    const size_t plane = (size_t)s->KS * sizeof(T);
+    T* qg = reinterpret_cast<T*>(scratch);
+    T* rg = reinterpret_cast<T*>(scratch + ((plane * lt->split_planes + 255) / 256) * 256);
+    SWE_CUDA(lt->split_rhs(p, qg, rg, s->cfg, s->stream));
+    s->launches += 3;
+  }
+  return SWE_OK;
+}
+
+}  // namespace
+}  // extern "C++"
+
+int swe_rhs_variant(swe_solver* s, int variant, void* dev_R, void* dev_scratch, size_t scratch_bytes) {
+  if (!s || !dev_R) return fail(SWE_EINVAL, "NULL argument");
+  size_t need = 0;
+  int rc = swe_rhs_scratch_bytes(s, variant, &need);
+  if (rc) return rc;
+  if (need > 0 && (!dev_scratch || scratch_bytes < need)) return fail(SWE_ENOMEM, "scratch too small");
+  if (need > 0 && (reinterpret_cast<uintptr_t>(dev_scratch) & 255))
+    return fail(SWE_EINVAL, "scratch must be 256-byte aligned");
+  if (!s->have_state) return fail(SWE_EINVAL, "no state");
+  if (!synchronous(s)) return fail(SWE_EINVAL, "state is not level-synchronous");
+  if (s->fp64) return rhs_variant_t<double>(s, s->ld, variant, reinterpret_cast<double*>(dev_R),
+                                            reinterpret_cast<char*>(dev_scratch));
+  return rhs_variant_t<float>(s, s->lf, variant, reinterpret_cast<float*>(dev_R),
+                              reinterpret_cast<char*>(dev_scratch));
+}
+
 int swe_substep(swe_solver* s, int32_t n) {
   if (!s || n < 0) return fail(SWE_EINVAL, "bad arguments");
   if (!s->have_state) return fail(SWE_EINVAL, "no state");

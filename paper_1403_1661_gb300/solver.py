@@ -177,6 +177,36 @@ class Solver:
         out.record_stream(self.stream)
         return out
 
+    def rhs_variant(self, variant, scratch=None):
+        """R(Q) by a kernel-structure ablation (nat.SWE_RHS_*), same layout as rhs().
+        scratch: a device uint8 tensor of at least rhs_scratch_bytes(variant) bytes
+        (allocated here when None)."""
+        import torch
+        need = C.c_size_t()
+        nat.check(nat.lib().swe_rhs_scratch_bytes(self.handle, int(variant), C.byref(need)),
+                  "swe_rhs_scratch_bytes")
+        if need.value and scratch is None:
+            scratch = torch.empty(need.value, dtype=torch.uint8, device=self.device)
+        dt = torch.float64 if self.precision == nat.SWE_FP64 else torch.float32
+        out = torch.empty((3, self.K, self.Np), dtype=dt, device=self.device)
+        cur = torch.cuda.current_stream(self.device)
+        self.stream.wait_stream(cur)
+        sp = C.c_void_p(scratch.data_ptr()) if need.value else None
+        sb = scratch.numel() if need.value else 0
+        nat.check(nat.lib().swe_rhs_variant(self.handle, int(variant), C.c_void_p(out.data_ptr()), sp, sb),
+                  "swe_rhs_variant")
+        cur.wait_stream(self.stream)
+        out.record_stream(self.stream)
+        if need.value:
+            scratch.record_stream(self.stream)
+        return out
+
+    def rhs_scratch_bytes(self, variant):
+        need = C.c_size_t()
+        nat.check(nat.lib().swe_rhs_scratch_bytes(self.handle, int(variant), C.byref(need)),
+                  "swe_rhs_scratch_bytes")
+        return need.value
+
     def substep(self, n=1):
         nat.check(nat.lib().swe_substep(self.handle, int(n)), "swe_substep")
 
