@@ -23,10 +23,26 @@ neighbour of another level between that neighbour's steps):
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 from .limiters import pp_limit, tvb_limit, tvb_geometry
 from .swe import SWEModel
+
+
+def cfl_regroup_levels(dt, dt_min: float, level, k: int, nlevels: int):
+    """The regroup rule of MRAB.cfl_levels for per-element CFL steps dt."""
+    dt = np.asarray(dt, np.float64)
+    lev = np.ones(dt.shape, np.int64)
+    for i, d in enumerate(dt):
+        _, e = math.frexp(d / dt_min)          # d / dt_min = m 2^e, m in [0.5, 1)
+        lev[i] = min(max(e, 1), nlevels)
+    lev = np.minimum(lev, np.asarray(level, np.int64) + 1)
+    v2 = (k & -k).bit_length() - 1 if k > 0 else 62
+    lev = np.minimum(lev, 1 + v2)
+    margin = float((dt / (dt_min * 2.0 ** (lev - 1))).min())
+    return lev, margin
 
 
 def ab_coefficients(depth: int):
@@ -147,6 +163,56 @@ class MRAB:
         self.q_end = np.stack(q)
         self.dof_updates += int(active.sum()) * self.q_end.shape[2] * 3
         self.k += 1
+
+    def regroup(self, levels):
+        """Regroup the elements into new levels at a level-synchronous time t_k
+        (Section 4: "elements can be regrouped after every few time steps"), keeping
+        dt_min, the state and the Adams-Bashforth history.
+
+        Reading: an element moved from level l to l' needs its R history at
+        t_k - dt_l' and t_k - 2 dt_l'. It holds R at t_k - s dt_l, s = 1, 2, 3 (its
+        last three activations); the quadratic through those three values is
+        evaluated at the new times (tau' = -r, -2r, -3r in units of dt_l,
+        r = dt_l' / dt_l). The activation count becomes k / 2^{l'-1}, so the ring
+        slot of activation a stays a mod 3. Requires k to be a multiple of
+        2^{max(l')-1} and of 2^{L-1}, and k >= 3 * 2^{L-1} (three activations
+        of every level)."""
+        lev = np.asarray(levels, np.int64)
+        k = self.k
+        if k % (2 ** (self.L - 1)) != 0:
+            raise ValueError("regroup needs a level-synchronous state")
+        if k < 3 * 2 ** (self.L - 1):
+            raise ValueError("regroup needs three activations of every level")
+        if lev.min() < 1 or k % (2 ** (int(lev.max()) - 1)) != 0:
+            raise ValueError("new levels must divide the substep count")
+        moved = np.nonzero(lev != self.level)[0]
+        for e in moved:
+            l0, l1 = int(self.level[e]), int(lev[e])
+            a0, a1 = k >> (l0 - 1), k >> (l1 - 1)
+            H = [self.hist[(a0 - s) % 3, :, e].copy() for s in (1, 2, 3)]   # tau = -1, -2, -3
+            r = 2.0 ** (l1 - l0)
+            for s in (1, 2, 3):
+                x = -s * r
+                w = ((x + 2) * (x + 3) / 2.0, -(x + 1) * (x + 3), (x + 1) * (x + 2) / 2.0)
+                self.hist[(a1 - s) % 3, :, e] = w[0] * H[0] + w[1] * H[1] + w[2] * H[2]
+        self.level = lev
+        self.L = int(lev.max())
+        self.dtl = self.dt_min * 2.0 ** (lev - 1)
+        self.count = k >> (lev - 1)
+        self.q_start = self.q_end.copy()
+
+    def cfl_levels(self, cfl: float, nlevels: int):
+        """Levels for a regroup by the CFL rule (Eq. cfl) with dt_min kept: the
+        largest l with 2^{l-1} dt_min <= dt_k, in 1..nlevels; at most one level
+        coarser than now (the history is extrapolated over at most one old step)
+        and at most 1 + (the power of 2 in k). Returns (levels, margin) with
+        margin = min_k dt_k / dt_l'(k) (< 1: some element's CFL step fell below
+        dt_min and a restart with a smaller dt_min is needed)."""
+        from .mesh import element_dt
+        m = self.model
+        q = self.q_end
+        dt = element_dt(m.mesh, m.ref.N, q[0], q[1], q[2], m.g, cfl)
+        return cfl_regroup_levels(dt, self.dt_min, self.level, self.k, nlevels)
 
     def macro_step(self, n: int = 1):
         for _ in range(n * 2 ** (self.L - 1)):
