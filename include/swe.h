@@ -159,6 +159,25 @@ int swe_setup_levels(swe_solver* solver, int32_t* level_out, double* dt_min_out)
  * finest step dt_min. Restarts the history. */
 int swe_set_levels(swe_solver* solver, const int32_t* level, double dt_min);
 
+/* Regroup the elements into MRAB levels at the current level-synchronous time
+ * without restarting (Section 4: elements may be regrouped every few steps to
+ * follow the changing CFL bound). dt_min, the time, the state and the
+ * Adams-Bashforth history are kept: an element that changes level from l to
+ * l' gets R at its new step times t - s dt_l' (s = 1, 2) from the quadratic
+ * in time through its R at t - s dt_l (s = 1, 2, 3).
+ *   level   the new levels (K, caller order, 1..nlevels_max), or NULL for the
+ *           CFL rule: the largest l with 2^{l-1} dt_min <= dt_k (dt_k of
+ *           Eq. cfl as in swe_setup_levels), at most one level coarser than
+ *           now (the history is extrapolated over at most one old step) and
+ *           at most 1 + the power of two in the substep count k.
+ * Requires k >= 3 * 2^{L-1} substeps since the last restart (three R values
+ * of every level) and 2^{max level - 1} dividing k; SWE_EINVAL otherwise,
+ * with the solver unchanged. level_out (K, caller order) and cfl_margin_out =
+ * min over elements of dt_k / (its new step) may be NULL; a margin below 1
+ * means an element's CFL step fell below dt_min: restart with
+ * swe_setup_levels. Synchronises the solver's stream. */
+int swe_regroup(swe_solver* solver, const int32_t* level, int32_t* level_out, double* cfl_margin_out);
+
 /* One evaluation of R(Q) = N(Q) + S(Q^{g,+}, Q^{g,-}) (Eq. ode) at the current,
  * level-synchronous state. dev_R: device array [3][K][Np] of the solver's
  * precision (double for SWE_FP64, float otherwise), caller order, written on

@@ -169,4 +169,26 @@ double assign_levels(const std::vector<double>& dt, int nlevels, std::vector<int
   return dtmin;
 }
 
+double regroup_levels(const std::vector<double>& dt, double dt_min, const std::vector<int32_t>& old_level,
+                      int64_t k, int nlevels, std::vector<int32_t>& level) {
+  int v2 = 62;   // the power of two in k
+  if (k > 0) {
+    v2 = 0;
+    while (((k >> v2) & 1) == 0) ++v2;
+  }
+  const int cap = v2 + 1 < nlevels ? v2 + 1 : nlevels;
+  level.resize(dt.size());
+  double margin = 1e300;
+  for (size_t i = 0; i < dt.size(); ++i) {
+    int e;
+    std::frexp(dt[i] / dt_min, &e);
+    int l = std::min(std::max(e, 1), nlevels);
+    l = std::min(l, old_level[i] + 1);
+    l = std::min(l, cap);
+    level[i] = l;
+    margin = std::min(margin, dt[i] / std::ldexp(dt_min, l - 1));
+  }
+  return margin;
+}
+
 }  // namespace swe

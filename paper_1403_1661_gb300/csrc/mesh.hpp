@@ -39,5 +39,10 @@ void element_dt(const Mesh& m, int N, const double* h, const double* hu, const d
 
 // Level 1..nlevels (Section 4) from dt; returns dt_min.
 double assign_levels(const std::vector<double>& dt, int nlevels, std::vector<int32_t>& level);
+// Levels for a regroup with dt_min kept (Section 4): the largest l with
+// 2^{l-1} dt_min <= dt_k in 1..nlevels, at most old + 1, at most 1 + (the power
+// of two in k). Returns min_k dt_k / (2^{l_k - 1} dt_min).
+double regroup_levels(const std::vector<double>& dt, double dt_min, const std::vector<int32_t>& old_level,
+                      int64_t k, int nlevels, std::vector<int32_t>& level);
 
 }  // namespace swe

@@ -733,6 +733,88 @@ int apply_levels(swe_solver* s, const std::vector<int32_t>& level, double dt_min
   return SWE_OK;
 }
 
+// Regroup at a level-synchronous substep k with dt_min, k and the Adams-Bashforth
+// history kept (reading in the swe_regroup contract): an element moved from level
+// l to l' gets R at t_k - s dt_l' (s = 1, 2, 3) from the quadratic through its R at
+// t_k - s dt_l; ring slot of activation a = a mod 3 with a = k >> (level - 1).
+template <typename T>
+int regroup_t(swe_solver* s, const std::vector<int32_t>& lev_new) {
+  const int K = s->K, KS = s->KS, np = s->Np;
+  const size_t fs = (size_t)np * KS, bs = 3 * fs, cs = (size_t)K * np;
+  const int64_t k = s->k;
+  std::vector<char> raw;
+  int rc = download_raw_t<T>(s, raw);
+  if (rc) return rc;
+  std::vector<uint8_t> dry_dev(K), dry_caller(K);
+  std::vector<T> ring(3 * bs);
+  SWE_CUDA(cudaMemcpyAsync(dry_dev.data(), s->ws + s->lay.dry, K, cudaMemcpyDeviceToHost, s->stream));
+  SWE_CUDA(cudaMemcpyAsync(ring.data(), s->ws + s->lay.ring, ring.size() * sizeof(T), cudaMemcpyDeviceToHost,
+                           s->stream));
+  SWE_CUDA(cudaStreamSynchronize(s->stream));
+  // history in caller order: hist[slot][field][c][j]
+  std::vector<T> hist(9 * cs);
+  for (int e = 0; e < K; ++e) {
+    const int c = s->perm[e];
+    dry_caller[c] = dry_dev[e];
+    for (int sl = 0; sl < 3; ++sl)
+      for (int f = 0; f < 3; ++f)
+        for (int j = 0; j < np; ++j)
+          hist[((size_t)(sl * 3 + f) * K + c) * np + j] = ring[sl * bs + f * fs + (size_t)j * KS + e];
+  }
+  auto slot = [](int64_t a) { return (int)(((a % 3) + 3) % 3); };
+  for (int c = 0; c < K; ++c) {
+    const int l0 = s->level[c], l1 = lev_new[c];
+    if (l0 == l1) continue;
+    const int64_t a0 = k >> (l0 - 1), a1 = k >> (l1 - 1);
+    const double r = std::ldexp(1.0, l1 - l0);
+    double w[3][3];   // [new s][old s]: Lagrange weights of tau = -1, -2, -3 at -s r
+    for (int sn = 1; sn <= 3; ++sn) {
+      const double x = -sn * r;
+      w[sn - 1][0] = (x + 2) * (x + 3) / 2.0;
+      w[sn - 1][1] = -(x + 1) * (x + 3);
+      w[sn - 1][2] = (x + 1) * (x + 2) / 2.0;
+    }
+    for (int f = 0; f < 3; ++f)
+      for (int j = 0; j < np; ++j) {
+        double H[3];
+        for (int so = 1; so <= 3; ++so) H[so - 1] = (double)hist[((size_t)(slot(a0 - so) * 3 + f) * K + c) * np + j];
+        for (int sn = 1; sn <= 3; ++sn)
+          hist[((size_t)(slot(a1 - sn) * 3 + f) * K + c) * np + j] =
+              (T)(w[sn - 1][0] * H[0] + w[sn - 1][1] * H[1] + w[sn - 1][2] * H[2]);
+      }
+  }
+  s->level = lev_new;
+  build_order(s);
+  invalidate_graph(s);
+  if ((rc = upload_mesh(s))) return rc;
+  // the state into both halves of the double buffer (the current one is (k >> (l-1)) & 1)
+  const T* in = reinterpret_cast<const T*>(raw.data());
+  std::vector<T> q(2 * bs, T(0));
+  for (int e = 0; e < K; ++e) {
+    const int c = s->perm[e];
+    for (int f = 0; f < 3; ++f)
+      for (int j = 0; j < np; ++j) {
+        const T v = in[f * cs + (size_t)c * np + j];
+        q[f * fs + (size_t)j * KS + e] = v;
+        q[bs + f * fs + (size_t)j * KS + e] = v;
+      }
+    for (int sl = 0; sl < 3; ++sl)
+      for (int f = 0; f < 3; ++f)
+        for (int j = 0; j < np; ++j)
+          ring[sl * bs + f * fs + (size_t)j * KS + e] = hist[((size_t)(sl * 3 + f) * K + c) * np + j];
+  }
+  if ((rc = upload(s, s->lay.q, q.data(), q.size() * sizeof(T)))) return rc;
+  if ((rc = upload(s, s->lay.ring, ring.data(), ring.size() * sizeof(T)))) return rc;
+  const long long macro = (long long)(k >> (s->L - 1));
+  SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.macro, &macro, 8, cudaMemcpyHostToDevice, s->stream));
+  // means and P1 values of the re-ordered state (no limiting), then the dry flags
+  if ((rc = launch_limit(s, 0, 0, 0, s->K))) return rc;
+  for (int e = 0; e < K; ++e) dry_dev[e] = dry_caller[s->perm[e]];
+  SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.dry, dry_dev.data(), K, cudaMemcpyHostToDevice, s->stream));
+  SWE_CUDA(cudaStreamSynchronize(s->stream));
+  return SWE_OK;
+}
+
 }  // namespace
 
 namespace swe {
@@ -992,6 +1074,36 @@ int swe_setup_levels(swe_solver* s, int32_t* level_out, double* dt_min_out) {
   if ((rc = apply_levels(s, lev, dtmin))) return rc;
   if (level_out) std::copy(lev.begin(), lev.end(), level_out);
   if (dt_min_out) *dt_min_out = dtmin;
+  return SWE_OK;
+}
+
+int swe_regroup(swe_solver* s, const int32_t* level, int32_t* level_out, double* cfl_margin_out) {
+  if (!s) return fail(SWE_EINVAL, "NULL argument");
+  if (!s->have_state || !s->have_levels) return fail(SWE_EINVAL, "state and levels must come first");
+  if (!synchronous(s)) return fail(SWE_EINVAL, "state is not level-synchronous");
+  if (s->k < 3 * (1LL << (s->L - 1))) return fail(SWE_EINVAL, "regroup needs three activations of every level");
+  const size_t n = (size_t)s->K * s->Np;
+  std::vector<double> h(n), hu(n), hv(n), dt;
+  int rc = download_state(s, h.data(), hu.data(), hv.data());
+  if (rc) return rc;
+  swe::element_dt(s->mesh, s->N, h.data(), hu.data(), hv.data(), s->prm.g, s->prm.cfl, dt);
+  std::vector<int32_t> lev;
+  double margin = swe::regroup_levels(dt, s->dt_min, s->level, s->k, s->prm.nlevels_max, lev);
+  if (level) {
+    lev.assign(level, level + s->K);
+    int lmax = 1;
+    for (int32_t v : lev) {
+      if (v < 1 || v > s->prm.nlevels_max) return fail(SWE_EINVAL, "level out of 1..nlevels_max");
+      lmax = std::max(lmax, (int)v);
+    }
+    if (s->k % (1LL << (lmax - 1))) return fail(SWE_EINVAL, "2^(max level - 1) must divide the substep count");
+    margin = 1e300;
+    for (int c = 0; c < s->K; ++c) margin = std::min(margin, dt[c] / std::ldexp(s->dt_min, lev[c] - 1));
+  }
+  rc = s->fp64 ? regroup_t<double>(s, lev) : regroup_t<float>(s, lev);
+  if (rc) return rc;
+  if (level_out) std::copy(lev.begin(), lev.end(), level_out);
+  if (cfl_margin_out) *cfl_margin_out = margin;
   return SWE_OK;
 }
 

@@ -158,11 +158,26 @@ class Solver:
         lev = np.zeros(self.K, np.int32)
         dtm = C.c_double()
         nat.check(nat.lib().swe_setup_levels(self.handle, nat.iptr(lev), C.byref(dtm)), "swe_setup_levels")
+        self.level = lev
         return lev, dtm.value
 
     def set_levels(self, level, dt_min):
         lev = np.ascontiguousarray(level, np.int32)
         nat.check(nat.lib().swe_set_levels(self.handle, nat.iptr(lev), float(dt_min)), "swe_set_levels")
+        self.level = lev.copy()
+
+    def regroup(self, level=None):
+        """Regroup into new levels without restarting (history kept); level=None
+        applies the CFL rule. Returns (levels in caller order, CFL margin)."""
+        out = np.zeros(self.K, np.int32)
+        margin = C.c_double()
+        lp = None
+        if level is not None:
+            lv = np.ascontiguousarray(level, np.int32)
+            lp = nat.iptr(lv)
+        nat.check(nat.lib().swe_regroup(self.handle, lp, nat.iptr(out), C.byref(margin)), "swe_regroup")
+        self.level = out
+        return out, margin.value
 
     # -- the hot path -----------------------------------------------------
     def rhs(self):
