@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-ablation", action="store_true")
+    ap.add_argument("--no-regroup", action="store_true")
+    ap.add_argument("--no-colloc", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-scenarios", type=int, default=64)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
@@ -362,10 +364,18 @@ def run_ours(args):
                               "fp32_speedup": value / (d64 / (ms64 / 1e3))}
         del s64
 
+    # the nodal-collocation scheme on the same workload (FP32 SIMT kernels)
+    if rank == 0 and not args.no_colloc:
+        result["collocation"] = run_collocation(args, scn, P)
+
     # kernel-structure ablation (Section 7): one R evaluation of the whole mesh by the
     # fused kernels and by the paper's three-kernel split with stored face traces
     if rank == 0 and not args.no_ablation:
         result["kernel_structure"] = run_ablation(s, P)
+
+    # level regrouping without restart (Section 4): one CFL regroup of the full mesh
+    if rank == 0 and not args.no_regroup:
+        result["regroup"] = run_regroup(s)
 
     # batched ensemble: uneven scenarios advanced by one graph launch per macro step
     if rank == 0 and not args.no_batch:
@@ -385,6 +395,34 @@ def run_ours(args):
         print(json.dumps(result), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def run_collocation(args, scn, P, steps=10):
+    """The nodal-collocation scheme (fluxes at the nodes and face nodes) on the same
+    workload and levels: DOF-updates/s, and the stage kernel against HBM."""
+    import torch
+    s = P.solver_from_scenario(scn, precision="fp32", scheme="collocation")
+    s.step(3)
+    torch.cuda.synchronize()
+    d0 = s.stats()["dof_updates"]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    s.step(steps)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    dofs = s.stats()["dof_updates"] - d0
+    L = s.level_info()[0]
+    prof = s.profile_substeps(2 * 2 ** (L - 1))
+    bpe = stage_bytes_per_element(args.order, 4)
+    achieved = prof["stage_elements"] * bpe / (prof["stage_ms"] / 1e3) / 1e9
+    peak, kind = measured_peaks()
+    return {"value": dofs / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "precision": "fp32", "kernel": f"k_stage<float,{16 + args.order}> (collocation code)",
+            "stage_ms_per_step": prof["stage_ms"] / 2, "tvb_ms_per_step": prof["tvb_ms"] / 2,
+            "stage_hbm_frac": achieved / peak, "stage_achieved_gbs": achieved,
+            "note": "same workload, levels and limiters; R from nodal fluxes (Ncub = Np, face nodes)"}
 
 
 def run_ablation(s, P, reps=10):
@@ -425,6 +463,25 @@ def run_ablation(s, P, reps=10):
                      "scratch_mb": nbytes / 1e6}
         del scratch
     return out
+
+
+def run_regroup(s):
+    """Wall time of one swe_regroup by the CFL rule after three macro steps, and of
+    the next macro step (graph re-capture included)."""
+    import numpy as np
+    import torch
+    s.step(3)
+    torch.cuda.synchronize()
+    old = s.level.copy()
+    t0 = time.perf_counter()
+    lev, margin = s.regroup(None)
+    t1 = time.perf_counter()
+    s.step(1)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return {"ms": (t1 - t0) * 1e3, "next_macro_step_ms": (t2 - t1) * 1e3, "elements": int(lev.size),
+            "changed": int((lev != old).sum()), "levels": np.bincount(lev)[1:].tolist(), "cfl_margin": margin,
+            "where": "host: state and history download, re-interpolation, re-ordered mesh and state upload"}
 
 
 def run_batched(args, steps=5):

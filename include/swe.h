@@ -57,6 +57,10 @@ extern "C" {
 #define SWE_FP32_TC 2         /* SWE_FP32 with the volume contractions on tensor cores
                                  (split-BF16 products, FP32 accumulation)         */
 
+/* ---- spatial schemes (swe_params.scheme) -------------------------------- */
+#define SWE_SCHEME_CUBATURE 0     /* Section 3: cubature + Gauss rules             */
+#define SWE_SCHEME_COLLOCATION 1  /* nodal collocation (fewer operations, aliased) */
+
 /* ---- limiter mask bits (Algorithm 2) ----------------------------------- */
 #define SWE_LIM_PP 1          /* positivity-preserving limiter M Pi (Algorithm 3) */
 #define SWE_LIM_TVB 2         /* TVB limiter Lambda Pi (Section 5.3)              */
@@ -76,10 +80,14 @@ typedef struct swe_solver swe_solver;
  *   precision    SWE_FP64, SWE_FP32 or SWE_FP32_TC
  *   limiter_mask SWE_LIM_PP | SWE_LIM_TVB applied after every update
  *   dry_mode     0: a dry element is reset to h = h0, hu = hv = 0 (Algorithm 3,
- *                injected mass tallied); 1: reset to its mean depth (mass kept) */
+ *                injected mass tallied); 1: reset to its mean depth (mass kept)
+ *   scheme       SWE_SCHEME_CUBATURE (the paper's: volume cubature of degree
+ *                3N-1, Gauss points on the faces) or SWE_SCHEME_COLLOCATION
+ *                (fluxes at the nodes and face nodes, their interpolants
+ *                integrated exactly; FP64 and FP32 only) */
 typedef struct {
   double g, h0, eps, tvb_M, tvb_nu, cfl;
-  int32_t N, nlevels_max, precision, limiter_mask, dry_mode, reserved;
+  int32_t N, nlevels_max, precision, limiter_mask, dry_mode, scheme;
 } swe_params;
 
 /* ---- library ------------------------------------------------------------ */

@@ -14,7 +14,7 @@ boundary, giving dQ/dt = N(Q) + S(Q^{g,+}, Q^{g,-}) (Eq. ode):
 Readings where the paper is silent:
 * "-" is the element's own trace, "+" the neighbour's (Section 5.1 wording).
 * LLF speed lambda = max(|u^- . n| + sqrt(g h*^-), |u^+ . n| + sqrt(g h*^+)) per point.
-* velocity u = hu/h where h > h0, else 0 (volume and surface alike).
+* velocity u = hu/h where h > h0 (1 + 1e-6), else 0 (volume and surface alike).
 * reflective wall: ghost h^+ = h^-, B^+ = B^-, m^+ = m^- - 2 (m^- . n) n.
 * Dirichlet faces (used only by the convergence pin): ghost = exact state.
 """
@@ -34,8 +34,15 @@ def physical_flux(h, hu, hv, u, v, g):
     return F, G
 
 
+# The velocity threshold sits a relative 1e-6 above h0: the positivity limiter leaves
+# depths exactly at h0 (the lowest vertex of a limited element), and those must take
+# u = 0 whatever the rounding of a depth computed as eta - B.
+VEL_MARGIN = 1e-6
+
+
 def velocity(h, m, h0):
-    return np.where(h > h0, m / np.where(h > h0, h, 1.0), 0.0)
+    hv = h0 * (1.0 + VEL_MARGIN)
+    return np.where(h > hv, m / np.where(h > hv, h, 1.0), 0.0)
 
 
 def wb_lf_flux(hm, hum, hvm, Bm, hp, hup, hvp, Bp, nx, ny, g, h0):

@@ -25,6 +25,9 @@ SWE_FP64 = 0
 SWE_FP32 = 1
 SWE_FP32_TC = 2
 
+SWE_SCHEME_CUBATURE = 0
+SWE_SCHEME_COLLOCATION = 1
+
 SWE_RHS_FUSED = 0
 SWE_RHS_FUSED_SIMT = 1
 SWE_RHS_GLOBAL_OPS = 2
@@ -37,7 +40,7 @@ class swe_params(C.Structure):
     _fields_ = [("g", C.c_double), ("h0", C.c_double), ("eps", C.c_double), ("tvb_M", C.c_double),
                 ("tvb_nu", C.c_double), ("cfl", C.c_double), ("N", C.c_int32),
                 ("nlevels_max", C.c_int32), ("precision", C.c_int32), ("limiter_mask", C.c_int32),
-                ("dry_mode", C.c_int32), ("reserved", C.c_int32)]
+                ("dry_mode", C.c_int32), ("scheme", C.c_int32)]
 
 
 _dp = C.POINTER(C.c_double)

@@ -10,15 +10,23 @@ namespace swe {
 constexpr int kMaxLevels = 8;
 constexpr int kBlock = 128;
 
-template <int N>
+// Scheme code: the polynomial order N, plus kColloc for the nodal-collocation
+// variant (volume and face integrals of the nodal interpolants: the "cubature
+// points" are the Np nodes and the "Gauss points" the Nfp face nodes, so the
+// same kernels run with other operators).
+constexpr int kColloc = 16;
+
+template <int NN>
 struct Dims {
+  static constexpr int N = NN % kColloc;
+  static constexpr bool COLLOC = NN >= kColloc;
   static constexpr int NP = (N + 1) * (N + 2) / 2;
   static constexpr int NPP = (NP + 3) / 4 * 4;
   static constexpr int NFP = N + 1;
   static constexpr int NFPP = (NFP + 3) / 4 * 4;
   static constexpr int Q = (3 * N + 1) / 2;
-  static constexpr int NCUB = Q * Q;
-  static constexpr int NG = (3 * N + 2) / 2;
+  static constexpr int NCUB = COLLOC ? NP : Q * Q;
+  static constexpr int NG = COLLOC ? NFP : (3 * N + 2) / 2;
 };
 
 // Operator block (element type T), packed by the host, staged in shared memory.
@@ -119,6 +127,7 @@ struct Sched {
 
 struct Phys {
   double g, h0, eps, tvb_M, tvb_nu;
+  double hvel;   // velocity u = hu/h only where h > hvel = h0 (1 + 1e-6), else 0
   float eps_f;
   int pp, dry_mode;
 };

@@ -206,9 +206,9 @@ struct Trace {
 // md (element reference split above).
 template <typename T>
 __device__ __forceinline__ void wb_flux(const Trace<T>& m, const Trace<T>& p, T hf, T epm, T bpm, T md, T nx,
-                                        T ny, T vx, T vy, T hs, T g, T hg, T qg, T h0, T& f0, T& f1, T& f2) {
+                                        T ny, T vx, T vy, T hs, T g, T hg, T qg, T hvel, T& f0, T& f1, T& f2) {
   const T hm = hf + (m.e - m.b), hp = hf + (p.e - p.b);
-  const T im = hm > h0 ? recip(hm) : T(0), ip = hp > h0 ? recip(hp) : T(0);
+  const T im = hm > hvel ? recip(hm) : T(0), ip = hp > hvel ? recip(hp) : T(0);
   const T um = m.hu * im, vm = m.hv * im;
   const T up = p.hu * ip, vp = p.hv * ip;
   const T bmax = tmax(m.b, p.b);
@@ -346,7 +346,7 @@ __device__ __forceinline__ void surface_fluxes(const StageParams<T>& p, const T*
   using O = OpLayout<N>;
   constexpr int NP = D::NP, NPP = D::NPP, NFP = D::NFP, NG = D::NG;
   const Sched& sc = p.sc;
-  const T g = (T)p.ph.g, h0 = (T)p.ph.h0, hg = T(0.5) * g, qg = T(0.25) * g;
+  const T g = (T)p.ph.g, hvel = (T)p.ph.hvel, hg = T(0.5) * g, qg = T(0.25) * g;
   const size_t ks = (size_t)sc.KS;
   const size_t fstride = (size_t)NP * ks;
   const size_t bstride = 3 * fstride;
@@ -382,7 +382,7 @@ __device__ __forceinline__ void surface_fluxes(const StageParams<T>& p, const T*
       const size_t sn = half ? 1 : ks, sf = half ? (size_t)NPP : fstride;   // node, field strides
 #pragma unroll
       for (int m = 0; m < NFP; ++m) {
-        const int jn = face_node_rt(N, fn, m);
+        const int jn = face_node_rt(Dims<N>::N, fn, m);
         const size_t idx = (size_t)jn * sn;
         ne[m] = __ldg(qn + idx);
         nu[m] = __ldg(qn + sf + idx);
@@ -403,7 +403,7 @@ __device__ __forceinline__ void surface_fluxes(const StageParams<T>& p, const T*
           const T* rs = p.s.ring + (size_t)((an - s) % 3) * bstride + nb;
 #pragma unroll
           for (int m = 0; m < NFP; ++m) {
-            const size_t idx = (size_t)face_node_rt(N, fn, m) * ks;
+            const size_t idx = (size_t)face_node_rt(Dims<N>::N, fn, m) * ks;
             ne[m] += ws * __ldg(rs + idx);
             nu[m] += ws * __ldg(rs + fstride + idx);
             nv[m] += ws * __ldg(rs + 2 * fstride + idx);
@@ -415,7 +415,7 @@ __device__ __forceinline__ void surface_fluxes(const StageParams<T>& p, const T*
     T oe[NFP], ou[NFP], ov[NFP], oB[NFP];
 #pragma unroll
     for (int m = 0; m < NFP; ++m) {
-      const int jn = face_node(N, f, m);
+      const int jn = face_node(Dims<N>::N, f, m);
       oe[m] = own(0, jn) - Ef;
       ou[m] = own(1, jn);
       ov[m] = own(2, jn);
@@ -457,7 +457,7 @@ __device__ __forceinline__ void surface_fluxes(const StageParams<T>& p, const T*
         tp = {tm.e, tm.hu - T(2) * mn * nx, tm.hv - T(2) * mn * ny, tm.b};
       }
       T f0, f1, f2;
-      wb_flux<T>(tm, tp, hf, tm.e + dE, tm.b + dB, md, nx, ny, vxn, vyn, hs, g, hg, qg, h0, f0, f1, f2);
+      wb_flux<T>(tm, tp, hf, tm.e + dE, tm.b + dB, md, nx, ny, vxn, vyn, hs, g, hg, qg, hvel, f0, f1, f2);
       emit(f, gq, f0, f1, f2, vxn, vyn);
     }
   }
@@ -625,7 +625,7 @@ template <typename T, int N>
 __device__ __forceinline__ void volume_term(const T* __restrict__ sops, const T (&eta)[Dims<N>::NPP],
                                             const T (&hu)[Dims<N>::NPP], const T (&hv)[Dims<N>::NPP],
                                             const T (&bb)[Dims<N>::NPP], T rx, T ry, T sx, T sy, T md, T g,
-                                            T h0, T (&R0)[Dims<N>::NP], T (&R1)[Dims<N>::NP],
+                                            T hvel, T (&R0)[Dims<N>::NP], T (&R1)[Dims<N>::NP],
                                             T (&R2)[Dims<N>::NP]) {
   using D = Dims<N>;
   using O = OpLayout<N>;
@@ -650,7 +650,7 @@ __device__ __forceinline__ void volume_term(const T* __restrict__ sops, const T 
       bsc += ics[jn] * bp;
     }
     const T hc = (eta[0] - bb[0]) + (ec - bc);
-    const T ih = hc > h0 ? recip(hc) : T(0);
+    const T ih = hc > hvel ? recip(hc) : T(0);
     const T u = huc * ih, v = hvc * ih;
     // cF1 = rx F + ry G and cF2 = sx F + sy G, with the momentum rows written
     // through the mass row: rx (hu u + p) + ry hv u = u (rx hu + ry hv) + rx p;
@@ -692,7 +692,7 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
 
   const Sched& sc = p.sc;
   const long long k = (*p.s.macro) * (1LL << (sc.L - 1)) + p.j;
-  const T g = (T)p.ph.g, h0 = (T)p.ph.h0;
+  const T g = (T)p.ph.g, hvel = (T)p.ph.hvel;
   const size_t ks = (size_t)sc.KS;
   const size_t fstride = (size_t)NP * ks;            // between fields
   const size_t bstride = 3 * fstride;                // between buffers
@@ -709,14 +709,16 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
     load_nodes<T, NP, NPP>(p.s.B + e, ks, bb);
     const T rx = __ldg(p.s.geo + 4 * (size_t)e + 0), ry = __ldg(p.s.geo + 4 * (size_t)e + 1);
     const T sx = __ldg(p.s.geo + 4 * (size_t)e + 2), sy = __ldg(p.s.geo + 4 * (size_t)e + 3);
-    const T md = p.s.dry[e] ? T(1) : T(0);   // depth form of the pressure for dry elements
+    // depth form of the pressure for dry elements; the collocation scheme keeps the
+    // pre-balanced form everywhere (with aliasing the two forms differ)
+    const T md = (!Dims<N>::COLLOC && p.s.dry[e]) ? T(1) : T(0);
 
     T R0[NP], R1[NP], R2[NP];
 #pragma unroll
     for (int i = 0; i < NP; ++i) { R0[i] = 0; R1[i] = 0; R2[i] = 0; }
 
     // ---- volume term (Section 7.1): interpolate, flux + source, project ----
-    volume_term<T, N>(sops, eta, hu, hv, bb, rx, ry, sx, sy, md, g, h0, R0, R1, R2);
+    volume_term<T, N>(sops, eta, hu, hv, bb, rx, ry, sx, sy, md, g, hvel, R0, R1, R2);
 
     auto own = [&](int f, int jn) -> T { return f == 0 ? eta[jn] : (f == 1 ? hu[jn] : (f == 2 ? hv[jn] : bb[jn])); };
     surface_lift<T, N>(p, sops, e, k, own, rx, ry, sx, sy, md, R0, R1, R2);

@@ -12,6 +12,14 @@ const Launchers<double>* launchers_f64_n2();
 const Launchers<double>* launchers_f64_n3();
 const Launchers<double>* launchers_f64_n4();
 const Launchers<double>* launchers_f64_n5();
+const Launchers<float>* launchers_f32_n18();
+const Launchers<float>* launchers_f32_n19();
+const Launchers<float>* launchers_f32_n20();
+const Launchers<float>* launchers_f32_n21();
+const Launchers<double>* launchers_f64_n18();
+const Launchers<double>* launchers_f64_n19();
+const Launchers<double>* launchers_f64_n20();
+const Launchers<double>* launchers_f64_n21();
 
 template <>
 const Launchers<float>* launchers_for<float>(int N) {
@@ -20,6 +28,10 @@ const Launchers<float>* launchers_for<float>(int N) {
     case 3: return launchers_f32_n3();
     case 4: return launchers_f32_n4();
     case 5: return launchers_f32_n5();
+    case kColloc + 2: return launchers_f32_n18();
+    case kColloc + 3: return launchers_f32_n19();
+    case kColloc + 4: return launchers_f32_n20();
+    case kColloc + 5: return launchers_f32_n21();
     default: return nullptr;
   }
 }
@@ -31,6 +43,10 @@ const Launchers<double>* launchers_for<double>(int N) {
     case 3: return launchers_f64_n3();
     case 4: return launchers_f64_n4();
     case 5: return launchers_f64_n5();
+    case kColloc + 2: return launchers_f64_n18();
+    case kColloc + 3: return launchers_f64_n19();
+    case kColloc + 4: return launchers_f64_n20();
+    case kColloc + 5: return launchers_f64_n21();
     default: return nullptr;
   }
 }

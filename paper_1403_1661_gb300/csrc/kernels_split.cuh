@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kBlock) k_split_traces(StageParams<T> p, Split
       T oe[NFP], ou[NFP], ov[NFP], oB[NFP];
 #pragma unroll
       for (int m = 0; m < NFP; ++m) {
-        const size_t idx = (size_t)face_node_rt(N, f, m) * ks;
+        const size_t idx = (size_t)face_node_rt(Dims<N>::N, f, m) * ks;
         oe[m] = __ldg(q + idx) - Ef;
         ou[m] = __ldg(q + fstride + idx);
         ov[m] = __ldg(q + 2 * fstride + idx);
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kBlock) k_split_volume(StageParams<T> p, Split
   stage_ops<T, N>(sops, p.s.ops);
   const Sched& sc = p.sc;
   const long long k = (*p.s.macro) * (1LL << (sc.L - 1)) + p.j;
-  const T g = (T)p.ph.g, h0 = (T)p.ph.h0;
+  const T g = (T)p.ph.g, hvel = (T)p.ph.hvel;
   const size_t ks = (size_t)sc.KS, fstride = (size_t)NP * ks, bstride = 3 * fstride;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.nactive; e += gridDim.x * blockDim.x) {
     const T* q = p.s.q + (size_t)((k >> (level_of(sc, e) - 1)) & 1) * bstride + e;
@@ -106,11 +106,11 @@ __global__ void __launch_bounds__(kBlock) k_split_volume(StageParams<T> p, Split
     load_nodes<T, NP, NPP>(p.s.B + e, ks, bb);
     T gm[4];
     load_row_global<T, 4>(p.s.geo + 4 * (size_t)e, gm);
-    const T md = p.s.dry[e] ? T(1) : T(0);
+    const T md = (!Dims<N>::COLLOC && p.s.dry[e]) ? T(1) : T(0);
     T R0[NP], R1[NP], R2[NP];
 #pragma unroll
     for (int i = 0; i < NP; ++i) { R0[i] = 0; R1[i] = 0; R2[i] = 0; }
-    volume_term<T, N>(sops, eta, hu, hv, bb, gm[0], gm[1], gm[2], gm[3], md, g, h0, R0, R1, R2);
+    volume_term<T, N>(sops, eta, hu, hv, bb, gm[0], gm[1], gm[2], gm[3], md, g, hvel, R0, R1, R2);
     add_reference_pressure<T, N>(sops, eta, bb, g, gm[0], gm[1], gm[2], gm[3], R1, R2);
     store_nodes<T, NP, NP>(sb.rg + e, ks, R0);
     store_nodes<T, NP, NP>(sb.rg + fstride + e, ks, R1);
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kBlock) k_split_surface(StageParams<T> p, Spli
   stage_ops<T, N, O::TAIL>(sops, p.s.ops);
   const Sched& sc = p.sc;
   const long long k = (*p.s.macro) * (1LL << (sc.L - 1)) + p.j;
-  const T g = (T)p.ph.g, h0 = (T)p.ph.h0, hg = T(0.5) * g, qg = T(0.25) * g;
+  const T g = (T)p.ph.g, hvel = (T)p.ph.hvel, hg = T(0.5) * g, qg = T(0.25) * g;
   const size_t ks = (size_t)sc.KS, fstride = (size_t)NP * ks, bstride = 3 * fstride;
   const int K = sc.K;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.nactive; e += gridDim.x * blockDim.x) {
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(kBlock) k_split_surface(StageParams<T> p, Spli
     T gm[4];
     load_row_global<T, 4>(p.s.geo + 4 * (size_t)e, gm);
     const T rx = gm[0], ry = gm[1], sx = gm[2], sy = gm[3];
-    const T md = p.s.dry[e] ? T(1) : T(0);
+    const T md = (!Dims<N>::COLLOC && p.s.dry[e]) ? T(1) : T(0);
     const T E0 = __ldg(p.s.q + (size_t)((k >> (level_of(sc, e) - 1)) & 1) * bstride + e);
     const T B0 = __ldg(p.s.B + e);
     const int4 cn = __ldg(p.s.conn + e);
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kBlock) k_split_surface(StageParams<T> p, Spli
           tp = {tm.e, tm.hu - T(2) * mn * nx, tm.hv - T(2) * mn * ny, tm.b};
         }
         T f0, f1, f2;
-        wb_flux<T>(tm, tp, hf, tm.e + dE, tm.b + dB, md, nx, ny, vxn, vyn, hs, g, hg, qg, h0, f0, f1, f2);
+        wb_flux<T>(tm, tp, hf, tm.e + dE, tm.b + dB, md, nx, ny, vxn, vyn, hs, g, hg, qg, hvel, f0, f1, f2);
         T lg[NPP];
         load_row<T, NPP>(sops + O::LGT + (f * NG + gq) * NPP, lg);
 #pragma unroll

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
 
   const Sched& sc = p.sc;
   const long long k = (*p.s.macro) * (1LL << (sc.L - 1)) + p.j;
-  const float gg = (float)p.ph.g, h0 = (float)p.ph.h0, hg = 0.5f * gg;
+  const float gg = (float)p.ph.g, hvel = (float)p.ph.hvel, hg = 0.5f * gg;
   const size_t ks = (size_t)sc.KS, fstride = (size_t)NP * ks, bstride = 3 * fstride;
   double injected = 0.0;
   const int ntiles = (p.nactive + 31) / 32;
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
         // the element's node-0 flux, subtracted here and from the volume fluxes (see
         // the reference flux below): constant fluxes contribute nothing to R
         const float hu0 = my[(1 * KP) * LS], hv0 = my[(2 * KP) * LS], d0 = my[0] - my[(3 * KP) * LS];
-        const float id0 = d0 > h0 ? recip(d0) : 0.f;
+        const float id0 = d0 > hvel ? recip(d0) : 0.f;
         const float u0 = hu0 * id0, v0 = hv0 * id0;
         surface_fluxes<float, N, true>(p, sops, e, k, own, ge.x, ge.y, ge.z, ge.w, s_md[lane],
                                        [&](int f, int gq, float f0, float f1, float f2, float vx, float vy) {
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
       float fr0[6], fr1[6];
       {
         const float d0 = cE0 - cB0, d1 = cE1 - cB1;
-        const float i0 = d0 > h0 ? recip(d0) : 0.f, i1v = d1 > h0 ? recip(d1) : 0.f;
+        const float i0 = d0 > hvel ? recip(d0) : 0.f, i1v = d1 > hvel ? recip(d1) : 0.f;
         const float u0 = c0[1] * i0, v0 = c0[2] * i0, u1 = c1[1] * i1v, v1 = c1[2] * i1v;
         const float a0r = ge0.x * c0[1] + ge0.y * c0[2], b0r = ge0.z * c0[1] + ge0.w * c0[2];
         const float a1r = ge1.x * c1[1] + ge1.y * c1[2], b1r = ge1.z * c1[1] + ge1.w * c1[2];
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
           const float bpc = acc[3][c];
           const float brc = acc[4][c], bsc = acc[5][c];
           const float hc = (c < 2 ? cE0 - cB0 : cE1 - cB1) + (ec - bpc);
-          const float ih = hc > h0 ? recip(hc) : 0.f;
+          const float ih = hc > hvel ? recip(hc) : 0.f;
           const float u = huc * ih, v = hvc * ih;
           // momentum rows of cF1, cF2 written through the mass row; p'' (the
           // reference part is added in strong form before the commit)

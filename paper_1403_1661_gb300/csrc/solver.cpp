@@ -56,7 +56,7 @@ struct Layout {
 
 int tc_size_of(int N);
 
-Layout make_layout(int K, int N, size_t ts, int op_size) {
+Layout make_layout(int K, int N, size_t ts, int op_size, int code) {
   Layout L;
   const size_t plane = (size_t)np_of(N) * (size_t)ks_of(K);   // one field, all nodes
   size_t off = 0;
@@ -82,7 +82,7 @@ Layout make_layout(int K, int N, size_t ts, int op_size) {
   L.dry = take((size_t)K);
   L.Bbar = take((size_t)K * 8);
   L.ops = take((size_t)op_size * ts);
-  L.tcops = take((size_t)tc_size_of(N) * 4);
+  L.tcops = take((size_t)tc_size_of(code) * 4);
   L.perm = take((size_t)K * 4);
   L.acc = take(8 * 8);
   L.flags = take(4 * 4);
@@ -102,7 +102,15 @@ int check_params(const swe_params* p) {
   if (p->nlevels_max < 1 || p->nlevels_max > swe::kMaxLevels)
     return fail(SWE_EINVAL, "nlevels_max must be in 1..8");
   if (p->limiter_mask & ~3) return fail(SWE_EINVAL, "unknown limiter bits");
+  if (p->scheme != SWE_SCHEME_CUBATURE && p->scheme != SWE_SCHEME_COLLOCATION)
+    return fail(SWE_EINVAL, "unknown scheme");
+  if (p->scheme == SWE_SCHEME_COLLOCATION && p->precision == SWE_FP32_TC)
+    return fail(SWE_EUNSUPPORTED, "the collocation scheme has no tensor-core tier");
   return SWE_OK;
+}
+
+int scheme_code(const swe_params* p) {
+  return p->N + (p->scheme == SWE_SCHEME_COLLOCATION ? swe::kColloc : 0);
 }
 
 // Base class so the C handle does not depend on the precision.
@@ -117,6 +125,7 @@ struct swe_solver {
   swe_params prm;
   swe::RefElem ref;
   int N = 0, K = 0, Np = 0, NPP = 0;
+  int code = 0;                  // N, plus swe::kColloc for the nodal-collocation scheme
   int KS = 0;                    // element stride of the device node planes
   bool fp64 = false;
   bool tc = false;   // FP32 with tensor-core volume contractions
@@ -204,6 +213,9 @@ swe::Phys phys_of(const swe_solver* s, int mask) {
   swe::Phys ph;
   ph.g = s->prm.g;
   ph.h0 = s->prm.h0;
+  // a depth the limiter leaves exactly at h0 (a vertex of a limited element) takes
+  // u = 0 whatever the rounding of eta - B
+  ph.hvel = s->prm.h0 * (1.0 + 1e-6);
   ph.eps = s->prm.eps > 0 ? s->prm.eps : s->prm.h0;
   ph.eps_f = (float)ph.eps;
   ph.tvb_M = s->prm.tvb_M;
@@ -303,6 +315,10 @@ void pack_ops_n(const swe::RefElem& e, std::vector<double>& o, std::vector<uint3
   put_rows(O::PST, e.Ps, nc, np, true);
   put_rows(O::PT, e.P, nc, np, true);
 
+  if constexpr (swe::Dims<N>::COLLOC) {   // no tensor-core tier
+    tc.clear();
+    return;
+  } else {
   // tensor-core fragments (mma.sync m16n8k16 / m16n8k8 bf16 B operands)
   tc.assign(TL::SIZE, 0u);
   const std::vector<double>* interp[3] = {&e.Ic, &e.Icr, &e.Ics};   // nc x np
@@ -380,14 +396,74 @@ void pack_ops_n(const swe::RefElem& e, std::vector<double>& o, std::vector<uint3
         tc[TL::LIFT + base + 0 * 32 + lane] = pack2(h0, h1);
         tc[TL::LIFT + base + 1 * 32 + lane] = pack2(l0, l1);
       }
+  }
 }
 
-void pack_ops(int N, const swe::RefElem& e, std::vector<double>& o, std::vector<uint32_t>& tc) {
-  switch (N) {
+// The operators of the nodal-collocation scheme in the cubature scheme's slots:
+// "cubature points" = the nodes (Ic = I, Icr = Dr, Ics = Ds, Pr = M^-1 Dr^T M,
+// Ps = M^-1 Ds^T M, P = I) and "Gauss points" = the face nodes (I1d = I, lift of
+// face f = Lg_f I1d = M^-1 E_f, exact for the degree-N interpolant along the face).
+swe::RefElem collocation_of(const swe::RefElem& e) {
+  const int np = e.Np, nc = e.Ncub, ng = e.Ng, nfp = e.Nfp;
+  swe::RefElem c = e;
+  std::vector<double> Dr((size_t)np * np, 0.0), Ds((size_t)np * np, 0.0);
+  for (int i = 0; i < np; ++i)
+    for (int j = 0; j < np; ++j)
+      for (int q = 0; q < nc; ++q) {
+        Dr[(size_t)i * np + j] += e.P[(size_t)i * nc + q] * e.Icr[(size_t)q * np + j];
+        Ds[(size_t)i * np + j] += e.P[(size_t)i * nc + q] * e.Ics[(size_t)q * np + j];
+      }
+  // M = invV^T invV, M^-1 = V V^T
+  std::vector<double> M((size_t)np * np, 0.0), Mi((size_t)np * np, 0.0);
+  for (int i = 0; i < np; ++i)
+    for (int j = 0; j < np; ++j)
+      for (int q = 0; q < np; ++q) {
+        M[(size_t)i * np + j] += e.invV[(size_t)q * np + i] * e.invV[(size_t)q * np + j];
+        Mi[(size_t)i * np + j] += e.V[(size_t)i * np + q] * e.V[(size_t)j * np + q];
+      }
+  auto weak = [&](const std::vector<double>& D) {   // M^-1 D^T M
+    std::vector<double> t((size_t)np * np, 0.0), o((size_t)np * np, 0.0);
+    for (int i = 0; i < np; ++i)
+      for (int j = 0; j < np; ++j)
+        for (int q = 0; q < np; ++q) t[(size_t)i * np + j] += D[(size_t)q * np + i] * M[(size_t)q * np + j];
+    for (int i = 0; i < np; ++i)
+      for (int j = 0; j < np; ++j)
+        for (int q = 0; q < np; ++q) o[(size_t)i * np + j] += Mi[(size_t)i * np + q] * t[(size_t)q * np + j];
+    return o;
+  };
+  c.Ncub = np;
+  c.Ic.assign((size_t)np * np, 0.0);
+  for (int i = 0; i < np; ++i) c.Ic[(size_t)i * np + i] = 1.0;
+  c.P = c.Ic;
+  c.Icr = Dr;
+  c.Ics = Ds;
+  c.Pr = weak(Dr);
+  c.Ps = weak(Ds);
+  c.Ng = nfp;
+  c.Lg.assign((size_t)np * 3 * nfp, 0.0);
+  for (int f = 0; f < 3; ++f)
+    for (int i = 0; i < np; ++i)
+      for (int m = 0; m < nfp; ++m) {
+        double v = 0.0;
+        for (int g = 0; g < ng; ++g) v += e.Lg[(size_t)i * 3 * ng + f * ng + g] * e.I1d[(size_t)g * nfp + m];
+        c.Lg[(size_t)i * 3 * nfp + f * nfp + m] = v;
+      }
+  c.I1d.assign((size_t)nfp * nfp, 0.0);
+  for (int m = 0; m < nfp; ++m) c.I1d[(size_t)m * nfp + m] = 1.0;
+  return c;
+}
+
+void pack_ops(int code, const swe::RefElem& e, std::vector<double>& o, std::vector<uint32_t>& tc) {
+  constexpr int C = swe::kColloc;
+  switch (code) {
     case 2: pack_ops_n<2>(e, o, tc); break;
     case 3: pack_ops_n<3>(e, o, tc); break;
     case 4: pack_ops_n<4>(e, o, tc); break;
     case 5: pack_ops_n<5>(e, o, tc); break;
+    case C + 2: pack_ops_n<C + 2>(collocation_of(e), o, tc); break;
+    case C + 3: pack_ops_n<C + 3>(collocation_of(e), o, tc); break;
+    case C + 4: pack_ops_n<C + 4>(collocation_of(e), o, tc); break;
+    case C + 5: pack_ops_n<C + 5>(collocation_of(e), o, tc); break;
     default: break;
   }
 }
@@ -406,7 +482,7 @@ template <typename T>
 int upload_ops_t(swe_solver* s) {
   std::vector<double> o;
   std::vector<uint32_t> tc;
-  pack_ops(s->N, s->ref, o, tc);
+  pack_ops(s->code, s->ref, o, tc);
   const int opsz = s->fp64 ? s->ld->op_size : s->lf->op_size;
   if ((int)o.size() != opsz) return fail(SWE_EINVAL, "internal: operator block size mismatch");
   std::vector<T> ot = to_t<T>(o);
@@ -945,9 +1021,9 @@ int swe_workspace_bytes(const swe_mesh* mesh, const swe_params* params, size_t* 
   int rc = check_params(params);
   if (rc) return rc;
   const bool fp64 = params->precision == SWE_FP64;
-  int opsz = fp64 ? swe::launchers_for<double>(params->N)->op_size
-                  : swe::launchers_for<float>(params->N)->op_size;
-  *bytes = make_layout(mesh->m.K, params->N, fp64 ? 8 : 4, opsz).total;
+  int opsz = fp64 ? swe::launchers_for<double>(scheme_code(params))->op_size
+                  : swe::launchers_for<float>(scheme_code(params))->op_size;
+  *bytes = make_layout(mesh->m.K, params->N, fp64 ? 8 : 4, opsz, scheme_code(params)).total;
   return SWE_OK;
 }
 
@@ -963,6 +1039,7 @@ int swe_solver_create(const swe_mesh* mesh, const swe_params* params, void* dev_
   s->mesh = mesh->m;
   s->prm = *params;
   s->N = params->N;
+  s->code = scheme_code(params);
   s->K = mesh->m.K;
   s->ref = swe::RefElem::build(s->N);
   s->Np = s->ref.Np;
@@ -975,13 +1052,13 @@ int swe_solver_create(const swe_mesh* mesh, const swe_params* params, void* dev_
   s->ws = reinterpret_cast<char*>(dev_workspace);
   s->ws_bytes = bytes;
   if (s->fp64) {
-    s->ld = swe::launchers_for<double>(s->N);
+    s->ld = swe::launchers_for<double>(s->code);
     if (!s->ld) return fail(SWE_EUNSUPPORTED, "order not built");
   } else {
-    s->lf = swe::launchers_for<float>(s->N);
+    s->lf = swe::launchers_for<float>(s->code);
     if (!s->lf) return fail(SWE_EUNSUPPORTED, "order not built");
   }
-  s->lay = make_layout(s->K, s->N, s->ts, s->fp64 ? s->ld->op_size : s->lf->op_size);
+  s->lay = make_layout(s->K, s->N, s->ts, s->fp64 ? s->ld->op_size : s->lf->op_size, s->code);
   if (bytes < s->lay.total) return fail(SWE_ENOMEM, "workspace smaller than swe_workspace_bytes()");
   cudaError_t ce = s->fp64 ? s->ld->prepare(&s->cfg) : s->lf->prepare(&s->cfg);
   if (ce != cudaSuccess) return fail(SWE_ECUDA, std::string("kernel setup: ") + cudaGetErrorString(ce));

@@ -56,7 +56,7 @@ class GpuFactory:
         lev, dtm = mesh.levels(scn.N, h, hu, hv, scn.g, scn.cfl, scn.nlevels)
         prm = nat.swe_params(scn.g, scn.h0, 0.0, scn.tvb_M, scn.tvb_nu, scn.cfl, scn.N, scn.nlevels,
                              {"fp64": 0, "fp32": 1, "fp32tc": 2}[self.precision], scn.limiter_mask,
-                             scn.dry_mode, 0)
+                             scn.dry_mode, nat.SWE_SCHEME_CUBATURE)
         nb = C.c_size_t()
         nat.check(nat.lib().swe_workspace_bytes(mesh.handle, C.byref(prm), C.byref(nb)), "swe_workspace_bytes")
         return {"mesh": mesh, "inputs": (B, h, hu, hv), "levels": (lev, dtm), "bytes": int(nb.value) + 256}

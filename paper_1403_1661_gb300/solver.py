@@ -113,7 +113,8 @@ class Solver:
 
     def __init__(self, mesh: Mesh, N: int, g: float = 9.81, h0: float = 1e-5, cfl: float = 0.5,
                  nlevels_max: int = 1, precision="fp32", limiter_mask: int = 0, tvb_M: float = 0.0,
-                 tvb_nu: float = 1.5, dry_mode: int = 0, eps: float = 0.0, device=None, stream=None):
+                 tvb_nu: float = 1.5, dry_mode: int = 0, eps: float = 0.0, device=None, stream=None,
+                 scheme: str = "cubature"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -123,7 +124,9 @@ class Solver:
         self.K = mesh.K
         self.Np = (N + 1) * (N + 2) // 2
         self.prm = nat.swe_params(g, h0, eps, tvb_M, tvb_nu, cfl, N, nlevels_max,
-                                  _prec_code(precision), limiter_mask, dry_mode, 0)
+                                  _prec_code(precision), limiter_mask, dry_mode,
+                                  {"cubature": nat.SWE_SCHEME_CUBATURE,
+                                   "collocation": nat.SWE_SCHEME_COLLOCATION}[scheme])
         self.precision = self.prm.precision
         nbytes = C.c_size_t()
         nat.check(L.swe_workspace_bytes(mesh.handle, C.byref(self.prm), C.byref(nbytes)),

@@ -7,12 +7,19 @@ import numpy as np
 from oracle import problem
 
 
-def both(scn, precision, levels=None, dt_min=None, mesh_arrays=None):
+def both(scn, precision, levels=None, dt_min=None, mesh_arrays=None, scheme="cubature"):
     import paper_1403_1661_gb300 as P
     arrays = scn.build_mesh() if mesh_arrays is None else mesh_arrays
     om, ref, model, integ = problem.build(scn, levels=levels, dt_min=dt_min, mesh_arrays=arrays)
+    if scheme == "collocation":
+        from oracle.colloc import CollocModel
+        from oracle.mrab import MRAB
+        model = CollocModel(om, ref, model.B, scn.g, scn.h0)
+        B, h, hu, hv = problem.nodal_inputs(scn, om, ref)
+        integ = MRAB(model, h, hu, hv, integ.level, integ.dt_min, limiter_mask=scn.limiter_mask,
+                     tvb_M=scn.tvb_M, tvb_nu=scn.tvb_nu, dry_mode=scn.dry_mode)
     solver = P.solver_from_scenario(scn, precision=precision, levels=integ.level, dt_min=integ.dt_min,
-                                    mesh_arrays=arrays)
+                                    mesh_arrays=arrays, scheme=scheme)
     return om, ref, model, integ, solver
 
 
