@@ -170,10 +170,16 @@ def recorded_traffic(N, precision):
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample
 
-def oracle_sample(args, nsteps=1, nx=200, ny=50):
+def oracle_sample(args, nsteps=1, nx=200, ny=50, scheme="cubature"):
     from oracle import problem
     scn = workload(args, nx=nx, ny=ny)
     om, ref, model, integ = problem.build(scn)
+    if scheme == "collocation":
+        from oracle.colloc import CollocModel
+        from oracle.mrab import MRAB
+        B, h, hu, hv = problem.nodal_inputs(scn, om, ref)
+        integ = MRAB(CollocModel(om, ref, model.B, scn.g, scn.h0), h, hu, hv, integ.level, integ.dt_min,
+                     limiter_mask=scn.limiter_mask, tvb_M=scn.tvb_M, tvb_nu=scn.tvb_nu, dry_mode=scn.dry_mode)
     period = 2 ** (integ.L - 1)
     t = time.perf_counter()
     d0 = integ.dof_updates
@@ -418,7 +424,13 @@ def run_collocation(args, scn, P, steps=10):
     bpe = stage_bytes_per_element(args.order, 4)
     achieved = prof["stage_elements"] * bpe / (prof["stage_ms"] / 1e3) / 1e9
     peak, kind = measured_peaks()
+    out_cpu = None
+    if not args.no_cpu_baseline:
+        v, dt, Ks, _ = oracle_sample(args, 1, 400, 100, scheme="collocation")
+        out_cpu = {"value": v, "unit": UNIT, "cores": cpu_info()[0], "kind": "oracle (oracle/colloc.py)",
+                   "sample": f"same scenario at 400x100x2 = {Ks} triangles, one macro step ({dt:.1f} s)"}
     return {"value": dofs / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "cpu_oracle": out_cpu,
             "precision": "fp32", "kernel": f"k_stage<float,{16 + args.order}> (collocation code)",
             "stage_ms_per_step": prof["stage_ms"] / 2, "tvb_ms_per_step": prof["tvb_ms"] / 2,
             "stage_hbm_frac": achieved / peak, "stage_achieved_gbs": achieved,
