@@ -493,7 +493,8 @@ def run_regroup(s):
     t2 = time.perf_counter()
     return {"ms": (t1 - t0) * 1e3, "next_macro_step_ms": (t2 - t1) * 1e3, "elements": int(lev.size),
             "changed": int((lev != old).sum()), "levels": np.bincount(lev)[1:].tolist(), "cfl_margin": margin,
-            "where": "host: state and history download, re-interpolation, re-ordered mesh and state upload"}
+            "where": "device: CFL steps, history re-interpolation, gather of every per-element array; "
+                     "host: level rule and new order from K steps"}
 
 
 def run_batched(args, steps=5):

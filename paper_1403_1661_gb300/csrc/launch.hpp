@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include "kernel_types.hpp"
 
@@ -56,5 +57,25 @@ template <typename T>
 cudaError_t launch_unpack_state(const T* q, const double* Bc, const int* iperm, const Sched& sc,
                                 long long k, int Np, double* x, cudaStream_t st);
 cudaError_t launch_stats_finalize(const double* partials, int nblocks, double* out, cudaStream_t st);
+
+// Level regrouping on the device (re-interpolated history, then every per-element
+// array gathered into the new order; pi: new index -> old index, sigma: old -> new).
+// Per-element CFL step of Eq. cfl from the current state (device order); H: the
+// inradii in device order; scratch: 8 bytes for the maximum depth.
+template <typename T>
+cudaError_t launch_element_dt(const T* q, const T* B, const Sched& sc, long long k, int NP, const double* H,
+                              double g, double C, unsigned long long* scratch, double* dt, cudaStream_t st);
+template <typename T>
+cudaError_t launch_ring_reinterp(T* ring, int K, int KS, int NP, const uint8_t* lev_old, const uint8_t* lev_new,
+                                 long long k, cudaStream_t st);
+template <typename E>
+cudaError_t launch_gather_planes(const E* src, E* dst, int P, int KS, int K, const int* pi, cudaStream_t st);
+template <typename T>
+cudaError_t launch_gather_state(const T* q, T* dst, int p0, int P, int KS, int K, int NP, const int* pi,
+                                const uint8_t* lev_old, long long k, cudaStream_t st);
+template <typename E>
+cudaError_t launch_gather_rows(const E* src, E* dst, int W, int K, const int* pi, cudaStream_t st);
+cudaError_t launch_remap_conn(const int4* src, int4* dst, int K, const int* pi, const int* sigma,
+                              const uint8_t* lev_new, cudaStream_t st);
 
 }  // namespace swe

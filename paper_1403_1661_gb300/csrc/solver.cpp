@@ -810,84 +810,134 @@ int apply_levels(swe_solver* s, const std::vector<int32_t>& level, double dt_min
 }
 
 // Regroup at a level-synchronous substep k with dt_min, k and the Adams-Bashforth
-// history kept (reading in the swe_regroup contract): an element moved from level
-// l to l' gets R at t_k - s dt_l' (s = 1, 2, 3) from the quadratic through its R at
-// t_k - s dt_l; ring slot of activation a = a mod 3 with a = k >> (level - 1).
+// history kept (reading in the swe_regroup contract), on the device: the history of
+// moved elements is re-interpolated in place (ring slot of activation a = a mod 3,
+// a = k >> (level - 1)), then every per-element array is gathered into the new
+// level order through the FP64 staging buffer. Only index arrays cross the bus.
 template <typename T>
 int regroup_t(swe_solver* s, const std::vector<int32_t>& lev_new) {
   const int K = s->K, KS = s->KS, np = s->Np;
-  const size_t fs = (size_t)np * KS, bs = 3 * fs, cs = (size_t)K * np;
   const int64_t k = s->k;
-  std::vector<char> raw;
-  int rc = download_raw_t<T>(s, raw);
-  if (rc) return rc;
-  std::vector<uint8_t> dry_dev(K), dry_caller(K);
-  std::vector<T> ring(3 * bs);
-  SWE_CUDA(cudaMemcpyAsync(dry_dev.data(), s->ws + s->lay.dry, K, cudaMemcpyDeviceToHost, s->stream));
-  SWE_CUDA(cudaMemcpyAsync(ring.data(), s->ws + s->lay.ring, ring.size() * sizeof(T), cudaMemcpyDeviceToHost,
-                           s->stream));
-  SWE_CUDA(cudaStreamSynchronize(s->stream));
-  // history in caller order: hist[slot][field][c][j]
-  std::vector<T> hist(9 * cs);
-  for (int e = 0; e < K; ++e) {
-    const int c = s->perm[e];
-    dry_caller[c] = dry_dev[e];
-    for (int sl = 0; sl < 3; ++sl)
-      for (int f = 0; f < 3; ++f)
-        for (int j = 0; j < np; ++j)
-          hist[((size_t)(sl * 3 + f) * K + c) * np + j] = ring[sl * bs + f * fs + (size_t)j * KS + e];
-  }
-  auto slot = [](int64_t a) { return (int)(((a % 3) + 3) % 3); };
-  for (int c = 0; c < K; ++c) {
-    const int l0 = s->level[c], l1 = lev_new[c];
-    if (l0 == l1) continue;
-    const int64_t a0 = k >> (l0 - 1), a1 = k >> (l1 - 1);
-    const double r = std::ldexp(1.0, l1 - l0);
-    double w[3][3];   // [new s][old s]: Lagrange weights of tau = -1, -2, -3 at -s r
-    for (int sn = 1; sn <= 3; ++sn) {
-      const double x = -sn * r;
-      w[sn - 1][0] = (x + 2) * (x + 3) / 2.0;
-      w[sn - 1][1] = -(x + 1) * (x + 3);
-      w[sn - 1][2] = (x + 1) * (x + 2) / 2.0;
-    }
-    for (int f = 0; f < 3; ++f)
-      for (int j = 0; j < np; ++j) {
-        double H[3];
-        for (int so = 1; so <= 3; ++so) H[so - 1] = (double)hist[((size_t)(slot(a0 - so) * 3 + f) * K + c) * np + j];
-        for (int sn = 1; sn <= 3; ++sn)
-          hist[((size_t)(slot(a1 - sn) * 3 + f) * K + c) * np + j] =
-              (T)(w[sn - 1][0] * H[0] + w[sn - 1][1] * H[1] + w[sn - 1][2] * H[2]);
-      }
-  }
+  cudaStream_t st = s->stream;
+  const std::vector<int32_t> perm_old = s->perm, iperm_old = s->iperm, lev_old = s->level;
   s->level = lev_new;
   build_order(s);
   invalidate_graph(s);
-  if ((rc = upload_mesh(s))) return rc;
-  // the state into both halves of the double buffer (the current one is (k >> (l-1)) & 1)
-  const T* in = reinterpret_cast<const T*>(raw.data());
-  std::vector<T> q(2 * bs, T(0));
+  // pi: new index -> old index; sigma: old -> new; levels by old and new index
+  std::vector<int32_t> pi(K), sigma(K);
+  std::vector<uint8_t> lo(K), ln_old(K), ln_new(K);
+  for (int e = 0; e < K; ++e) {
+    pi[e] = iperm_old[s->perm[e]];
+    ln_new[e] = (uint8_t)lev_new[s->perm[e]];
+    const int c = perm_old[e];
+    sigma[e] = s->iperm[c];
+    lo[e] = (uint8_t)lev_old[c];
+    ln_old[e] = (uint8_t)lev_new[c];
+  }
+  char* x = s->ws + s->lay.xfer;
+  const size_t xbytes = 3 * (size_t)K * np * 8;
+  int* d_pi = reinterpret_cast<int*>(x);
+  int* d_sigma = d_pi + K;
+  uint8_t* d_lo = reinterpret_cast<uint8_t*>(d_sigma + K);
+  uint8_t* d_lno = d_lo + K;
+  uint8_t* d_lnn = d_lno + K;
+  const size_t idx = ((size_t)K * 11 + 255) / 256 * 256;
+  char* scr = x + idx;
+  const size_t scr_bytes = xbytes > idx ? xbytes - idx : 0;
+  const size_t plane = (size_t)KS * sizeof(T);
+  const int chunk = (int)std::min<size_t>(scr_bytes / plane, (size_t)1 << 20);
+  if (chunk < 1 || scr_bytes < (size_t)K * 8 * sizeof(T) || scr_bytes < (size_t)K * 16)
+    return fail(SWE_ENOMEM, "mesh too small for the regroup staging");
+  SWE_CUDA(cudaMemcpyAsync(d_pi, pi.data(), (size_t)K * 4, cudaMemcpyHostToDevice, st));
+  SWE_CUDA(cudaMemcpyAsync(d_sigma, sigma.data(), (size_t)K * 4, cudaMemcpyHostToDevice, st));
+  SWE_CUDA(cudaMemcpyAsync(d_lo, lo.data(), K, cudaMemcpyHostToDevice, st));
+  SWE_CUDA(cudaMemcpyAsync(d_lno, ln_old.data(), K, cudaMemcpyHostToDevice, st));
+  SWE_CUDA(cudaMemcpyAsync(d_lnn, ln_new.data(), K, cudaMemcpyHostToDevice, st));
+  T* ring = reinterpret_cast<T*>(s->ws + s->lay.ring);
+  T* sT = reinterpret_cast<T*>(scr);
+  SWE_CUDA(swe::launch_ring_reinterp<T>(ring, K, KS, np, d_lo, d_lno, (long long)k, st));
+  // the state: each element's current buffer into both halves, new order
+  T* q = reinterpret_cast<T*>(s->ws + s->lay.q);
+  const size_t bs = (size_t)3 * np * KS;
+  for (int p0 = 0; p0 < 3 * np; p0 += chunk) {
+    const int P = std::min(chunk, 3 * np - p0);
+    SWE_CUDA(swe::launch_gather_state<T>(q, sT, p0, P, KS, K, np, d_pi, d_lo, (long long)k, st));
+    SWE_CUDA(cudaMemcpyAsync(q + (size_t)p0 * KS, sT, P * plane, cudaMemcpyDeviceToDevice, st));
+    SWE_CUDA(cudaMemcpyAsync(q + bs + (size_t)p0 * KS, sT, P * plane, cudaMemcpyDeviceToDevice, st));
+  }
+  // plane arrays
+  auto planes = [&](T* a, int P) -> int {
+    for (int p0 = 0; p0 < P; p0 += chunk) {
+      const int n = std::min(chunk, P - p0);
+      SWE_CUDA(swe::launch_gather_planes<T>(a + (size_t)p0 * KS, sT, n, KS, K, d_pi, st));
+      SWE_CUDA(cudaMemcpyAsync(a + (size_t)p0 * KS, sT, n * plane, cudaMemcpyDeviceToDevice, st));
+    }
+    return SWE_OK;
+  };
+  int rc;
+  if ((rc = planes(ring, 9 * np))) return rc;
+  if ((rc = planes(reinterpret_cast<T*>(s->ws + s->lay.B), np))) return rc;
+  if ((rc = planes(reinterpret_cast<T*>(s->ws + s->lay.vb), 3))) return rc;
+  if ((rc = planes(reinterpret_cast<T*>(s->ws + s->lay.p1), 9))) return rc;
+  // per-element records
+  auto rows_t = [&](size_t off, int W) -> int {
+    T* a = reinterpret_cast<T*>(s->ws + off);
+    SWE_CUDA(swe::launch_gather_rows<T>(a, sT, W, K, d_pi, st));
+    SWE_CUDA(cudaMemcpyAsync(a, sT, (size_t)K * W * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    return SWE_OK;
+  };
+  if ((rc = rows_t(s->lay.geo, 4))) return rc;
+  if ((rc = rows_t(s->lay.tvbg, 8))) return rc;
+  if ((rc = rows_t(s->lay.means, 4))) return rc;
+  double* bbar = reinterpret_cast<double*>(s->ws + s->lay.Bbar);
+  SWE_CUDA(swe::launch_gather_rows<double>(bbar, reinterpret_cast<double*>(scr), 1, K, d_pi, st));
+  SWE_CUDA(cudaMemcpyAsync(bbar, scr, (size_t)K * 8, cudaMemcpyDeviceToDevice, st));
+  uint8_t* dry = reinterpret_cast<uint8_t*>(s->ws + s->lay.dry);
+  SWE_CUDA(swe::launch_gather_rows<uint8_t>(dry, reinterpret_cast<uint8_t*>(scr), 1, K, d_pi, st));
+  SWE_CUDA(cudaMemcpyAsync(dry, scr, (size_t)K, cudaMemcpyDeviceToDevice, st));
+  int4* conn = reinterpret_cast<int4*>(s->ws + s->lay.conn);
+  SWE_CUDA(swe::launch_remap_conn(conn, reinterpret_cast<int4*>(scr), K, d_pi, d_sigma, d_lnn, st));
+  SWE_CUDA(cudaMemcpyAsync(conn, scr, (size_t)K * 16, cudaMemcpyDeviceToDevice, st));
+  if ((rc = upload(s, s->lay.perm, s->perm.data(), (size_t)K * 4))) return rc;
+  if ((rc = upload(s, s->lay.iperm, s->iperm.data(), (size_t)K * 4))) return rc;
+  const long long macro = (long long)(k >> (s->L - 1));
+  SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.macro, &macro, 8, cudaMemcpyHostToDevice, st));
+  SWE_CUDA(cudaStreamSynchronize(st));
+  return SWE_OK;
+}
+
+// Eq. cfl's per-element step (caller order) computed on the device from the
+// current state; the same arithmetic as swe::element_dt on downloaded depths.
+int device_element_dt(swe_solver* s, std::vector<double>& dt) {
+  const int K = s->K;
+  const swe::Mesh& m = s->mesh;
+  std::vector<double> H(K);
   for (int e = 0; e < K; ++e) {
     const int c = s->perm[e];
-    for (int f = 0; f < 3; ++f)
-      for (int j = 0; j < np; ++j) {
-        const T v = in[f * cs + (size_t)c * np + j];
-        q[f * fs + (size_t)j * KS + e] = v;
-        q[bs + f * fs + (size_t)j * KS + e] = v;
-      }
-    for (int sl = 0; sl < 3; ++sl)
-      for (int f = 0; f < 3; ++f)
-        for (int j = 0; j < np; ++j)
-          ring[sl * bs + f * fs + (size_t)j * KS + e] = hist[((size_t)(sl * 3 + f) * K + c) * np + j];
+    const double* L = &m.flen[3 * (size_t)c];
+    H[e] = 2.0 * (2.0 * m.J[c]) / (L[0] + L[1] + L[2]);   // inradius
   }
-  if ((rc = upload(s, s->lay.q, q.data(), q.size() * sizeof(T)))) return rc;
-  if ((rc = upload(s, s->lay.ring, ring.data(), ring.size() * sizeof(T)))) return rc;
-  const long long macro = (long long)(k >> (s->L - 1));
-  SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.macro, &macro, 8, cudaMemcpyHostToDevice, s->stream));
-  // means and P1 values of the re-ordered state (no limiting), then the dry flags
-  if ((rc = launch_limit(s, 0, 0, 0, s->K))) return rc;
-  for (int e = 0; e < K; ++e) dry_dev[e] = dry_caller[s->perm[e]];
-  SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.dry, dry_dev.data(), K, cudaMemcpyHostToDevice, s->stream));
+  char* x = s->ws + s->lay.xfer;   // staging: [max depth][H (K)][dt (K)]
+  unsigned long long* hm = reinterpret_cast<unsigned long long*>(x);
+  double* dH = reinterpret_cast<double*>(x + 256);
+  double* ddt = dH + K;
+  SWE_CUDA(cudaMemcpyAsync(dH, H.data(), (size_t)K * 8, cudaMemcpyHostToDevice, s->stream));
+  const double C = s->prm.cfl / ((s->N + 1.0) * (s->N + 1.0));
+  const swe::Sched sc = sched_of(s);
+  cudaError_t ce = s->fp64 ? swe::launch_element_dt<double>(reinterpret_cast<const double*>(s->ws + s->lay.q),
+                                                              reinterpret_cast<const double*>(s->ws + s->lay.B),
+                                                              sc, (long long)s->k, s->Np, dH, s->prm.g, C, hm,
+                                                              ddt, s->stream)
+                           : swe::launch_element_dt<float>(reinterpret_cast<const float*>(s->ws + s->lay.q),
+                                                             reinterpret_cast<const float*>(s->ws + s->lay.B), sc,
+                                                             (long long)s->k, s->Np, dH, s->prm.g, C, hm, ddt,
+                                                             s->stream);
+  if (ce != cudaSuccess) return fail(SWE_ECUDA, std::string("element dt: ") + cudaGetErrorString(ce));
+  std::vector<double> dd(K);
+  SWE_CUDA(cudaMemcpyAsync(dd.data(), ddt, (size_t)K * 8, cudaMemcpyDeviceToHost, s->stream));
   SWE_CUDA(cudaStreamSynchronize(s->stream));
+  dt.resize(K);
+  for (int e = 0; e < K; ++e) dt[s->perm[e]] = dd[e];
   return SWE_OK;
 }
 
@@ -1159,11 +1209,9 @@ int swe_regroup(swe_solver* s, const int32_t* level, int32_t* level_out, double*
   if (!s->have_state || !s->have_levels) return fail(SWE_EINVAL, "state and levels must come first");
   if (!synchronous(s)) return fail(SWE_EINVAL, "state is not level-synchronous");
   if (s->k < 3 * (1LL << (s->L - 1))) return fail(SWE_EINVAL, "regroup needs three activations of every level");
-  const size_t n = (size_t)s->K * s->Np;
-  std::vector<double> h(n), hu(n), hv(n), dt;
-  int rc = download_state(s, h.data(), hu.data(), hv.data());
+  std::vector<double> dt;
+  int rc = device_element_dt(s, dt);
   if (rc) return rc;
-  swe::element_dt(s->mesh, s->N, h.data(), hu.data(), hv.data(), s->prm.g, s->prm.cfl, dt);
   std::vector<int32_t> lev;
   double margin = swe::regroup_levels(dt, s->dt_min, s->level, s->k, s->prm.nlevels_max, lev);
   if (level) {
