@@ -786,7 +786,7 @@ __device__ __forceinline__ T minmod_tvb(T a, T b, T thr, bool& changed) {
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(kBlock) k_tvb(LimitParams<T> p) {
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_tvb(LimitParams<T> p) {
   using D = Dims<N>;
   using O = OpLayout<N>;
   constexpr int NP = D::NP, NPP = D::NPP;
@@ -797,14 +797,12 @@ __global__ void __launch_bounds__(kBlock) k_tvb(LimitParams<T> p) {
   const long long k = (*p.s.macro) * (1LL << (sc.L - 1)) + p.j;
   const T g = (T)p.ph.g, h0 = (T)p.ph.h0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.nactive; e += gridDim.x * blockDim.x) {
-    if (p.s.dry[e]) continue;
+    // Every load is issued before the first branch on loaded data (an element that is
+    // dry or has a dry neighbour is skipped afterwards), so the latencies overlap:
+    // two dependent trips to memory (connectivity, then the neighbours) instead of four.
     const int4 cn = __ldg(p.s.conn + e);
+    const int de = __ldg(p.s.dry + e);
     const int nbs[3] = {cn.x, cn.y, cn.z};
-    bool skip = false;
-#pragma unroll
-    for (int f = 0; f < 3; ++f)
-      if (nbs[f] >= 0 && p.s.dry[nbs[f]]) skip = true;
-    if (skip) continue;
     const int lev = level_of(sc, e);
     const long long a = k >> (lev - 1);
     const int cur = (int)((a + p.post_stage) & 1);
@@ -816,25 +814,33 @@ __global__ void __launch_bounds__(kBlock) k_tvb(LimitParams<T> p) {
     load_row_global<T, 4>(p.s.geo + 4 * eo, gm);
     load_row_global<T, 4>(p.s.means + 4 * eo, u0);
     load_row_global<T, 8>(p.s.tvbg + 8 * eo, tg);
-    const T rx = gm[0], ry = gm[1], sx = gm[2], sy = gm[3];
     // P1 part: vertex values of Pi1 q for eta, hu, hv (stored with the committed
     // state) and of Pi1 B (static)
     T vq[3][3], vb[3];
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
-      vq[0][v] = p.s.p1[(0 + v) * ks + eo];
-      vq[1][v] = p.s.p1[(3 + v) * ks + eo];
-      vq[2][v] = p.s.p1[(6 + v) * ks + eo];
+      vq[0][v] = __ldg(p.s.p1 + (0 + v) * ks + eo);
+      vq[1][v] = __ldg(p.s.p1 + (3 + v) * ks + eo);
+      vq[2][v] = __ldg(p.s.p1 + (6 + v) * ks + eo);
       vb[v] = __ldg(p.s.vb + v * ks + eo);
     }
-    // neighbour means; a wall face mirrors the normal momentum of the own mean
+    // neighbour means and dry flags
     T un[3][4];
+    int dn = 0;
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
       const int nb = nbs[f];
       if (nb >= 0) {
+        dn |= __ldg(p.s.dry + nb);
         load_row_global<T, 4>(p.s.means + 4 * (size_t)nb, un[f]);
-      } else {
+      }
+    }
+    if (de || dn) continue;
+    const T rx = gm[0], ry = gm[1], sx = gm[2], sy = gm[3];
+    // a wall face mirrors the normal momentum of the own mean
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      if (nbs[f] < 0) {
         const T vxn = f == 0 ? -sx : (f == 1 ? rx + sx : -rx);
         const T vyn = f == 0 ? -sy : (f == 1 ? ry + sy : -ry);
         const T sn = sqrt(vxn * vxn + vyn * vyn);
