@@ -269,7 +269,11 @@ typedef struct swe_batch swe_batch;
  * uneven scenarios overlap on the GPU. The solvers stay usable on their own;
  * work issued on their streams is ordered after a batch step. */
 int swe_batch_create(swe_solver* const* solvers, int32_t n, void* stream, swe_batch** out);
-/* n_macro graph launches (each advances every solver by one macro step). */
+/* n_macro graph launches (each advances every solver by one macro step).
+ * SWE_EINVAL, with nothing launched, if any solver's levels, element order or
+ * launch shape changed since swe_batch_create (swe_set_levels,
+ * swe_setup_levels, swe_regroup, swe_set_launch_config, swe_set_full_state):
+ * the captured graph would run stale launches; create the batch again. */
 int swe_batch_step(swe_batch* batch, int32_t n_macro);
 void swe_batch_destroy(swe_batch* batch);
 

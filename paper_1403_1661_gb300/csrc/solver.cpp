@@ -152,6 +152,7 @@ struct swe_solver {
   int64_t dof_updates = 0;
   int64_t launches = 0;
   cudaGraphExec_t graph = nullptr;
+  uint64_t sched_version = 0;    // bumped whenever captured launches go stale (levels, order, launch shape)
   int graph_launches = 0;
   int64_t graph_dofs = 0;
   swe::KernelCfg cfg_max;   // occupancy limits (set_launch_config caps below these)
@@ -165,6 +166,7 @@ struct swe_batch {
   std::vector<cudaEvent_t> join;
   std::vector<int> launches;
   std::vector<int64_t> dofs;
+  std::vector<uint64_t> versions;   // each solver's sched_version at capture
 };
 
 namespace {
@@ -578,6 +580,7 @@ void build_order(swe_solver* s) {
 }
 
 int invalidate_graph(swe_solver* s) {
+  s->sched_version++;
   if (s->graph) {
     cudaGraphExecDestroy(s->graph);
     s->graph = nullptr;
@@ -1451,7 +1454,7 @@ int swe_stats(const swe_solver* cs, double* mass, double* injected_mass, double*
 namespace {
 struct CkptHeader {
   char magic[8];
-  int32_t K, N, precision, L;
+  int32_t K, N, precision, L, scheme, pad;
   int64_t k, dof_updates;
   double t0, dt_min;
   uint64_t bytes_q, bytes_ring, bytes_qmid, bytes_means, bytes_dry;
@@ -1476,6 +1479,7 @@ int swe_get_full_state(const swe_solver* s, void* host_buf, size_t bytes) {
   std::memset(&h, 0, sizeof(h));
   std::memcpy(h.magic, "SWEGB300", 8);
   h.K = s->K; h.N = s->N; h.precision = s->prm.precision; h.L = s->L;
+  h.scheme = s->prm.scheme; h.pad = 0;
   h.k = s->k; h.dof_updates = s->dof_updates; h.t0 = s->t0; h.dt_min = s->dt_min;
   h.bytes_q = 2 * 3 * (uint64_t)s->Np * s->KS * s->ts;
   h.bytes_ring = 3 * h.bytes_q / 2;
@@ -1506,7 +1510,8 @@ int swe_set_full_state(swe_solver* s, const void* host_buf, size_t bytes) {
   CkptHeader h;
   const char* p = reinterpret_cast<const char*>(host_buf);
   std::memcpy(&h, p, sizeof(h)); p += sizeof(h);
-  if (std::memcmp(h.magic, "SWEGB300", 8) != 0 || h.K != s->K || h.N != s->N || h.precision != s->prm.precision)
+  if (std::memcmp(h.magic, "SWEGB300", 8) != 0 || h.K != s->K || h.N != s->N || h.precision != s->prm.precision ||
+      h.scheme != s->prm.scheme)
     return fail(SWE_EINVAL, "checkpoint does not match this solver");
   std::vector<int32_t> lev(s->K);
   std::memcpy(lev.data(), p, (size_t)s->K * 4); p += (size_t)s->K * 4;
@@ -1576,6 +1581,7 @@ int swe_batch_create(swe_solver* const* solvers, int32_t n, void* stream, swe_ba
   for (int i = 0; i < n; ++i) SWE_CUDA(cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming));
   b->launches.assign(n, 0);
   b->dofs.assign(n, 0);
+  for (int32_t i = 0; i < n; ++i) b->versions.push_back(solvers[i]->sched_version);
   // one macro step of every solver, each on its own stream: parallel graph branches
   cudaGraph_t g = nullptr;
   SWE_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
@@ -1615,6 +1621,9 @@ int swe_batch_create(swe_solver* const* solvers, int32_t n, void* stream, swe_ba
 int swe_batch_step(swe_batch* b, int32_t n_macro) {
   if (!b || n_macro < 0) return fail(SWE_EINVAL, "bad arguments");
   if (n_macro == 0) return SWE_OK;
+  for (size_t i = 0; i < b->solvers.size(); ++i)
+    if (b->solvers[i]->sched_version != b->versions[i])
+      return fail(SWE_EINVAL, "a solver's levels or launch shape changed since swe_batch_create");
   // the batch stream waits for work already queued on the solvers' own streams
   for (size_t i = 0; i < b->solvers.size(); ++i) {
     SWE_CUDA(cudaEventRecord(b->join[i], b->solvers[i]->stream));

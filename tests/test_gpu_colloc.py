@@ -99,3 +99,22 @@ def test_colloc_has_no_tensor_core_tier():
     with pytest.raises(nat.SWEError) as ei:
         P.solver_from_scenario(scn, precision="fp32tc", scheme="collocation")
     assert ei.value.code == nat.SWE_EUNSUPPORTED
+
+
+def test_checkpoint_records_the_scheme():
+    import paper_1403_1661_gb300 as P
+    from paper_1403_1661_gb300 import _native as nat
+    scn = sc.tsunami(nx=24, ny=6, N=3, nlevels=3)
+    c = P.solver_from_scenario(scn, precision="fp32", scheme="collocation")
+    c.step(1)
+    ck = c.full_state()
+    q = P.solver_from_scenario(scn, precision="fp32")
+    with pytest.raises(nat.SWEError) as ei:
+        q.load_full_state(ck)
+    assert ei.value.code == nat.SWE_EINVAL
+    c2 = P.solver_from_scenario(scn, precision="fp32", scheme="collocation")
+    c2.load_full_state(ck)
+    c.step(1)
+    c2.step(1)
+    for x, y in zip(c.get_state()[:3], c2.get_state()[:3]):
+        assert np.array_equal(x, y)

@@ -161,3 +161,26 @@ def _thacker_nodes(scn):
     vx, vy, E = scn.build_mesh()
     m, ref = Mesh(vx, vy, E), RefElement(scn.N)
     return m.map_to_physical(ref.r, ref.s)
+
+
+def test_batch_refuses_stale_graph_after_regroup():
+    """A batch captured before a solver's regroup would replay stale launches:
+    swe_batch_step refuses until the batch is created again."""
+    import paper_1403_1661_gb300 as P
+    from paper_1403_1661_gb300 import _native as nat
+    from paper_1403_1661_gb300.batch import Batch
+    scn = sc.tsunami(nx=24, ny=6, N=3, nlevels=3)
+    a = P.solver_from_scenario(scn, precision="fp32")
+    b = P.solver_from_scenario(scn, precision="fp32")
+    batch = Batch([a, b])
+    batch.step(3)
+    a.regroup(a.level.copy())
+    with pytest.raises(nat.SWEError) as ei:
+        batch.step(1)
+    assert ei.value.code == nat.SWE_EINVAL
+    batch.close()
+    again = Batch([a, b])
+    again.step(1)
+    again.close()
+    for x, y in zip(a.get_state()[:3], b.get_state()[:3]):
+        assert np.array_equal(x, y)
