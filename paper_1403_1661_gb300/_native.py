@@ -63,6 +63,7 @@ SIGNATURES = {
     "swe_mesh_node_coords": (C.c_int, [_vp, C.c_int32, _dp, _dp]),
     "swe_mesh_levels": (C.c_int, [_vp, C.c_int32, _dp, _dp, _dp, C.c_double, C.c_double, C.c_int32,
                                   _ip, _dp]),
+    "swe_regroup_rule": (C.c_int, [_dp, _ip, C.c_int32, C.c_double, C.c_int64, C.c_int32, _ip, _dp]),
     "swe_workspace_bytes": (C.c_int, [_vp, C.POINTER(swe_params), C.POINTER(C.c_size_t)]),
     "swe_solver_create": (C.c_int, [_vp, C.POINTER(swe_params), _vp, C.c_size_t, _vp, C.POINTER(_vp)]),
     "swe_solver_destroy": (None, [_vp]),

@@ -1069,6 +1069,19 @@ int swe_mesh_levels(const swe_mesh* mesh, int32_t N, const double* h, const doub
   return SWE_OK;
 }
 
+int swe_regroup_rule(const double* dt, const int32_t* level, int32_t K, double dt_min, int64_t k,
+                     int32_t nlevels_max, int32_t* level_out, double* margin_out) {
+  if (!dt || !level || !level_out || K < 0) return fail(SWE_EINVAL, "bad arguments");
+  if (!(dt_min > 0) || nlevels_max < 1 || nlevels_max > swe::kMaxLevels || k < 0)
+    return fail(SWE_EINVAL, "bad arguments");
+  std::vector<double> d(dt, dt + K);
+  std::vector<int32_t> old(level, level + K), lev;
+  const double margin = swe::regroup_levels(d, dt_min, old, k, nlevels_max, lev);
+  std::copy(lev.begin(), lev.end(), level_out);
+  if (margin_out) *margin_out = margin;
+  return SWE_OK;
+}
+
 int swe_workspace_bytes(const swe_mesh* mesh, const swe_params* params, size_t* bytes) {
   if (!mesh || !bytes) return fail(SWE_EINVAL, "NULL argument");
   int rc = check_params(params);

@@ -116,3 +116,25 @@ def test_bad_meshes_are_rejected(lib):
         P.Mesh(vx, vy, np.array([[0, 1, 7]]))                           # bad index
     with pytest.raises(lib.SWEError):
         P.Mesh(np.array([0.0, 1.0, 2.0]), np.array([0.0, 0.0, 0.0]), np.array([[0, 1, 2]]))  # degenerate
+
+
+def test_regroup_rule_bit_exact(lib):
+    """The library's CFL regroup rule against the oracle's, on random steps around
+    the powers of two (including exact powers) and several substep counts."""
+    import ctypes as C
+    from oracle.mrab import cfl_regroup_levels
+    rng = np.random.default_rng(9)
+    K = 4000
+    dt_min = 0.37
+    for k, nl in ((24, 4), (8, 4), (12, 5), (7 * 16, 8), (3, 3)):
+        ratio = np.exp2(rng.uniform(-1.5, 7.0, K))
+        ratio[:40] = np.exp2(rng.integers(0, 7, 40))          # exact powers of two
+        dt = np.ascontiguousarray(ratio * dt_min)
+        old = np.ascontiguousarray(rng.integers(1, nl + 1, K).astype(np.int32))
+        out = np.zeros(K, np.int32)
+        margin = C.c_double()
+        lib.check(lib.lib().swe_regroup_rule(lib.dptr(dt), lib.iptr(old), K, dt_min, k, nl, lib.iptr(out),
+                                             C.byref(margin)), "swe_regroup_rule")
+        olev, omargin = cfl_regroup_levels(dt, dt_min, old, k, nl)
+        assert np.array_equal(out, olev)
+        assert margin.value == omargin
