@@ -403,11 +403,9 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_collocation(args, scn, P, steps=10):
-    """The nodal-collocation scheme (fluxes at the nodes and face nodes) on the same
-    workload and levels: DOF-updates/s, and the stage kernel against HBM."""
+def _colloc_run(args, scn, P, precision, steps):
     import torch
-    s = P.solver_from_scenario(scn, precision="fp32", scheme="collocation")
+    s = P.solver_from_scenario(scn, precision=precision, scheme="collocation")
     s.step(3)
     torch.cuda.synchronize()
     d0 = s.stats()["dof_updates"]
@@ -423,17 +421,28 @@ def run_collocation(args, scn, P, steps=10):
     prof = s.profile_substeps(2 * 2 ** (L - 1))
     bpe = stage_bytes_per_element(args.order, 4)
     achieved = prof["stage_elements"] * bpe / (prof["stage_ms"] / 1e3) / 1e9
+    return dofs / (ms / 1e3), ms / steps, prof, achieved
+
+
+def run_collocation(args, scn, P, steps=10):
+    """The nodal-collocation scheme (fluxes at the nodes and face nodes) on the same
+    workload and levels, tensor-core and SIMT FP32 tiers: DOF-updates/s, and the
+    tensor-core stage kernel against HBM."""
+    value, ms_step, prof, achieved = _colloc_run(args, scn, P, "fp32tc", steps)
+    v_simt, ms_simt, _, ach_simt = _colloc_run(args, scn, P, "fp32", steps)
     peak, kind = measured_peaks()
     out_cpu = None
     if not args.no_cpu_baseline:
         v, dt, Ks, _ = oracle_sample(args, 1, 400, 100, scheme="collocation")
         out_cpu = {"value": v, "unit": UNIT, "cores": cpu_info()[0], "kind": "oracle (oracle/colloc.py)",
                    "sample": f"same scenario at 400x100x2 = {Ks} triangles, one macro step ({dt:.1f} s)"}
-    return {"value": dofs / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+    return {"value": value, "unit": UNIT, "ms_per_step": ms_step, "steps": steps,
             "cpu_oracle": out_cpu,
-            "precision": "fp32", "kernel": f"k_stage<float,{16 + args.order}> (collocation code)",
+            "precision": "fp32tc", "kernel": f"k_stage_tc<{16 + args.order}> (collocation code)",
             "stage_ms_per_step": prof["stage_ms"] / 2, "tvb_ms_per_step": prof["tvb_ms"] / 2,
             "stage_hbm_frac": achieved / peak, "stage_achieved_gbs": achieved,
+            "simt_fp32": {"value": v_simt, "ms_per_step": ms_simt, "stage_hbm_frac": ach_simt / peak,
+                          "kernel": f"k_stage<float,{16 + args.order}>"},
             "note": "same workload, levels and limiters; R from nodal fluxes (Ncub = Np, face nodes)"}
 
 

@@ -104,8 +104,6 @@ int check_params(const swe_params* p) {
   if (p->limiter_mask & ~3) return fail(SWE_EINVAL, "unknown limiter bits");
   if (p->scheme != SWE_SCHEME_CUBATURE && p->scheme != SWE_SCHEME_COLLOCATION)
     return fail(SWE_EINVAL, "unknown scheme");
-  if (p->scheme == SWE_SCHEME_COLLOCATION && p->precision == SWE_FP32_TC)
-    return fail(SWE_EUNSUPPORTED, "the collocation scheme has no tensor-core tier");
   return SWE_OK;
 }
 
@@ -317,10 +315,7 @@ void pack_ops_n(const swe::RefElem& e, std::vector<double>& o, std::vector<uint3
   put_rows(O::PST, e.Ps, nc, np, true);
   put_rows(O::PT, e.P, nc, np, true);
 
-  if constexpr (swe::Dims<N>::COLLOC) {   // no tensor-core tier
-    tc.clear();
-    return;
-  } else {
+  {
   // tensor-core fragments (mma.sync m16n8k16 / m16n8k8 bf16 B operands)
   tc.assign(TL::SIZE, 0u);
   const std::vector<double>* interp[3] = {&e.Ic, &e.Icr, &e.Ics};   // nc x np
@@ -476,6 +471,10 @@ int tc_size_of(int N) {
     case 3: return swe::TcLayout<3>::SIZE;
     case 4: return swe::TcLayout<4>::SIZE;
     case 5: return swe::TcLayout<5>::SIZE;
+    case swe::kColloc + 2: return swe::TcLayout<swe::kColloc + 2>::SIZE;
+    case swe::kColloc + 3: return swe::TcLayout<swe::kColloc + 3>::SIZE;
+    case swe::kColloc + 4: return swe::TcLayout<swe::kColloc + 4>::SIZE;
+    case swe::kColloc + 5: return swe::TcLayout<swe::kColloc + 5>::SIZE;
     default: return 0;
   }
 }

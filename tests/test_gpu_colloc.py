@@ -7,7 +7,8 @@ against the oracle's collocation variant (oracle/colloc.py).
 * The multirate beach (4 levels, PP + TVB), two macro steps.
 * Convergence on the stationary vortex (aliasing costs about one order against the
   cubature scheme's N + 1).
-* No tensor-core tier: SWE_FP32_TC is refused.
+* The tensor-core tier: R within its tolerance, the multirate beach within its state
+  tolerance.
 """
 import math
 
@@ -58,7 +59,7 @@ def test_colloc_lake_at_rest(precision, bed):
     assert np.abs(R).max() < {"fp64": 1e-13, "fp32": 1e-5}[precision] * scale
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32tc"])
 def test_colloc_mrab_tsunami_levels(precision):
     scn = sc.tsunami(nx=40, ny=10, N=3, nlevels=4)
     om, ref, model, integ, s = both(scn, precision, scheme="collocation")
@@ -92,13 +93,18 @@ def test_colloc_stationary_vortex_converges(N):
     assert min(eoc) >= N - 0.5
 
 
-def test_colloc_has_no_tensor_core_tier():
-    import paper_1403_1661_gb300 as P
-    from paper_1403_1661_gb300 import _native as nat
-    scn = _rhs_case(3, "fp32tc")
-    with pytest.raises(nat.SWEError) as ei:
-        P.solver_from_scenario(scn, precision="fp32tc", scheme="collocation")
-    assert ei.value.code == nat.SWE_EUNSUPPORTED
+@pytest.mark.parametrize("N", [2, 3, 4, 5])
+def test_colloc_tensor_core_tier(N):
+    """The tensor-core stage kernel runs the collocation scheme too (identity
+    interpolation and projection fragments): R within the tier's tolerance."""
+    scn = _rhs_case(N, "fp32tc")
+    om, ref, model, integ, s = both(scn, "fp32tc", scheme="collocation")
+    q = integ.q_end
+    R_o = model.rhs(q[0], q[1], q[2])
+    R_g = s.rhs().cpu().numpy().astype(np.float64)
+    errs = [np.abs(R_g[c] - R_o[c]).max() / np.abs(R_o[c]).max() for c in range(3)]
+    print(f"PARITY colloc rhs N={N} fp32tc " + " ".join(f"{e:.3e}" for e in errs), flush=True)
+    assert max(errs) < TOL_R["fp32tc"]
 
 
 def test_checkpoint_records_the_scheme():
