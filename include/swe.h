@@ -191,7 +191,9 @@ int swe_set_levels(swe_solver* solver, const int32_t* level, double dt_min);
  * with the solver unchanged. level_out (K, caller order) and cfl_margin_out =
  * min over elements of dt_k / (its new step) may be NULL; a margin below 1
  * means an element's CFL step fell below dt_min: restart with
- * swe_setup_levels. Synchronises the solver's stream. */
+ * swe_setup_levels. Runs on the device through the state staging area;
+ * SWE_ENOMEM for a mesh too small for it to hold one node plane (a single
+ * element of low order). Synchronises the solver's stream. */
 int swe_regroup(swe_solver* solver, const int32_t* level, int32_t* level_out, double* cfl_margin_out);
 
 /* One evaluation of R(Q) = N(Q) + S(Q^{g,+}, Q^{g,-}) (Eq. ode) at the current,

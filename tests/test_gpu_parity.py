@@ -235,3 +235,29 @@ def test_set_state_rejects_nonfinite_and_keeps_state():
     got = s.get_state(out=outs)
     for x, y in zip(before[:3], got[:3]):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32tc"])
+def test_single_element_all_walls(precision):
+    """Degenerate mesh: one triangle, every face a wall (one tile with 31 empty
+    lanes on the tensor-core path): R and ten steps against the oracle."""
+    scn = sc.Scenario(name="one", N=3, g=9.81, h0=1e-5, cfl=0.5, nlevels=1, limiter_mask=3, tvb_M=0.0,
+                      mesh=lambda: (np.array([0.0, 1.0, 0.2]), np.array([0.0, 0.1, 0.9]),
+                                    np.array([[0, 1, 2]], np.int32)),
+                      bathymetry=lambda x, y, cx=None, cy=None: -1.0 + 0.1 * x, init=None)
+    scn.init = lambda x, y, cx, cy, B: (0.05 * np.exp(-((x - 0.4) ** 2 + (y - 0.3) ** 2) / 0.05) - B,
+                                        0.1 * x * (1.0 - B), 0 * x)
+    om, ref, model, integ, s = both(scn, precision)
+    assert om.K == 1
+    q = integ.q_end
+    R_o = model.rhs(q[0], q[1], q[2])
+    R_g = s.rhs().cpu().numpy().astype(np.float64)
+    e = max(np.abs(R_g[c] - R_o[c]).max() / np.abs(R_o[c]).max() for c in range(3))
+    for _ in range(10):
+        integ.substep()
+    s.substep(10)
+    eh, em, _ = state_errors(s, integ)
+    hmax = integ.q_end[0].max()
+    _report(f"one element {precision}", eR=e, eh=eh / hmax, em=em / (hmax * np.sqrt(9.81 * hmax)))
+    assert e < TOL_R[precision]
+    assert eh < TOL_STATE[precision] * hmax and em < TOL_STATE[precision] * hmax * np.sqrt(9.81 * hmax)

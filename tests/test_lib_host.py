@@ -115,6 +115,8 @@ def test_bad_meshes_are_rejected(lib):
     with pytest.raises(lib.SWEError):
         P.Mesh(vx, vy, np.array([[0, 1, 7]]))                           # bad index
     with pytest.raises(lib.SWEError):
+        P.Mesh(vx, vy, np.zeros((0, 3), np.int32))                      # no elements
+    with pytest.raises(lib.SWEError):
         P.Mesh(np.array([0.0, 1.0, 2.0]), np.array([0.0, 0.0, 0.0]), np.array([[0, 1, 2]]))  # degenerate
 
 
