@@ -374,6 +374,16 @@ def run_ours(args):
     if rank == 0 and not args.no_colloc:
         result["collocation"] = run_collocation(args, scn, P)
 
+    # the rules of integration order 2N (Fig. 2's caption) on the same workload
+    if rank == 0 and not args.no_colloc:
+        v, ms2, prof2, ach2 = _colloc_run(args, scn, P, "fp32tc", 10, scheme="cubature_2n")
+        peak2, _ = measured_peaks()
+        result["cubature_2n"] = {"value": v, "unit": UNIT, "ms_per_step": ms2, "steps": 10,
+                                 "precision": "fp32tc", "kernel": f"k_stage_tc<{32 + args.order}>",
+                                 "stage_ms_per_step": prof2["stage_ms"] / 2, "stage_hbm_frac": ach2 / peak2,
+                                 "note": "volume rule of degree 2N ((N+1)^2 points), N+1 Gauss points per "
+                                         "face, pre-balanced form; same workload, levels and limiters"}
+
     # kernel-structure ablation (Section 7): one R evaluation of the whole mesh by the
     # fused kernels and by the paper's three-kernel split with stored face traces
     if rank == 0 and not args.no_ablation:
@@ -403,9 +413,9 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def _colloc_run(args, scn, P, precision, steps):
+def _colloc_run(args, scn, P, precision, steps, scheme="collocation"):
     import torch
-    s = P.solver_from_scenario(scn, precision=precision, scheme="collocation")
+    s = P.solver_from_scenario(scn, precision=precision, scheme=scheme)
     s.step(3)
     torch.cuda.synchronize()
     d0 = s.stats()["dof_updates"]

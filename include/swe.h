@@ -60,6 +60,9 @@ extern "C" {
 /* ---- spatial schemes (swe_params.scheme) -------------------------------- */
 #define SWE_SCHEME_CUBATURE 0     /* Section 3: cubature + Gauss rules             */
 #define SWE_SCHEME_COLLOCATION 1  /* nodal collocation (fewer operations, aliased) */
+#define SWE_SCHEME_CUBATURE_2N 2  /* integration order 2N (Fig. 2's caption): conical
+                                     product of (N+1)^2 points, N+1 Gauss points per
+                                     face; pre-balanced form everywhere             */
 
 /* ---- limiter mask bits (Algorithm 2) ----------------------------------- */
 #define SWE_LIM_PP 1          /* positivity-preserving limiter M Pi (Algorithm 3) */
@@ -82,9 +85,10 @@ typedef struct swe_solver swe_solver;
  *   dry_mode     0: a dry element is reset to h = h0, hu = hv = 0 (Algorithm 3,
  *                injected mass tallied); 1: reset to its mean depth (mass kept)
  *   scheme       SWE_SCHEME_CUBATURE (the paper's: volume cubature of degree
- *                3N-1, Gauss points on the faces) or SWE_SCHEME_COLLOCATION
- *                (fluxes at the nodes and face nodes, their interpolants
- *                integrated exactly; FP64 and FP32 only) */
+ *                3N-1, Gauss points on the faces), SWE_SCHEME_CUBATURE_2N (the
+ *                same with rules of integration order 2N) or
+ *                SWE_SCHEME_COLLOCATION (fluxes at the nodes and face nodes,
+ *                their interpolants integrated exactly) */
 typedef struct {
   double g, h0, eps, tvb_M, tvb_nu, cfl;
   int32_t N, nlevels_max, precision, limiter_mask, dry_mode, scheme;

@@ -27,6 +27,7 @@ SWE_FP32_TC = 2
 
 SWE_SCHEME_CUBATURE = 0
 SWE_SCHEME_COLLOCATION = 1
+SWE_SCHEME_CUBATURE_2N = 2
 
 SWE_RHS_FUSED = 0
 SWE_RHS_FUSED_SIMT = 1

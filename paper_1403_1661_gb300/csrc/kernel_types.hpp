@@ -10,23 +10,30 @@ namespace swe {
 constexpr int kMaxLevels = 8;
 constexpr int kBlock = 128;
 
-// Scheme code: the polynomial order N, plus kColloc for the nodal-collocation
-// variant (volume and face integrals of the nodal interpolants: the "cubature
-// points" are the Np nodes and the "Gauss points" the Nfp face nodes, so the
-// same kernels run with other operators).
+// Scheme code: the polynomial order N (bits 0-3), plus
+//   kColloc   the nodal-collocation variant (volume and face integrals of the nodal
+//             interpolants: the "cubature points" are the Np nodes and the "Gauss
+//             points" the Nfp face nodes, so the same kernels run with other operators)
+//   kReduced  the rules of integration order 2N (a conical product of (N+1)^2 points,
+//             N + 1 Gauss points per face) instead of 3N - 1 and 3N
 constexpr int kColloc = 16;
+constexpr int kReduced = 32;
 
 template <int NN>
 struct Dims {
-  static constexpr int N = NN % kColloc;
-  static constexpr bool COLLOC = NN >= kColloc;
+  static constexpr int N = NN & 15;
+  static constexpr bool COLLOC = (NN & kColloc) != 0;
+  static constexpr bool REDUCED = (NN & kReduced) != 0;
+  // rules exact to degrees 3N - 1 and 3N: only then is the depth form of the
+  // pressure for dry elements the same discretisation as the pre-balanced form
+  static constexpr bool EXACT = !COLLOC && !REDUCED;
   static constexpr int NP = (N + 1) * (N + 2) / 2;
   static constexpr int NPP = (NP + 3) / 4 * 4;
   static constexpr int NFP = N + 1;
   static constexpr int NFPP = (NFP + 3) / 4 * 4;
-  static constexpr int Q = (3 * N + 1) / 2;
+  static constexpr int Q = REDUCED ? N + 1 : (3 * N + 1) / 2;
   static constexpr int NCUB = COLLOC ? NP : Q * Q;
-  static constexpr int NG = COLLOC ? NFP : (3 * N + 2) / 2;
+  static constexpr int NG = COLLOC ? NFP : (REDUCED ? N + 1 : (3 * N + 2) / 2);
 };
 
 // Operator block (element type T), packed by the host, staged in shared memory.

@@ -709,9 +709,9 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
     load_nodes<T, NP, NPP>(p.s.B + e, ks, bb);
     const T rx = __ldg(p.s.geo + 4 * (size_t)e + 0), ry = __ldg(p.s.geo + 4 * (size_t)e + 1);
     const T sx = __ldg(p.s.geo + 4 * (size_t)e + 2), sy = __ldg(p.s.geo + 4 * (size_t)e + 3);
-    // depth form of the pressure for dry elements; the collocation scheme keeps the
-    // pre-balanced form everywhere (with aliasing the two forms differ)
-    const T md = (!Dims<N>::COLLOC && p.s.dry[e]) ? T(1) : T(0);
+    // depth form of the pressure for dry elements; with inexact rules (collocation,
+    // order 2N) the pre-balanced form everywhere (the two forms then differ)
+    const T md = (Dims<N>::EXACT && p.s.dry[e]) ? T(1) : T(0);
 
     T R0[NP], R1[NP], R2[NP];
 #pragma unroll

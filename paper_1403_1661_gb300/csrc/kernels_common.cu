@@ -16,10 +16,18 @@ const Launchers<float>* launchers_f32_n18();
 const Launchers<float>* launchers_f32_n19();
 const Launchers<float>* launchers_f32_n20();
 const Launchers<float>* launchers_f32_n21();
+const Launchers<float>* launchers_f32_n34();
+const Launchers<float>* launchers_f32_n35();
+const Launchers<float>* launchers_f32_n36();
+const Launchers<float>* launchers_f32_n37();
 const Launchers<double>* launchers_f64_n18();
 const Launchers<double>* launchers_f64_n19();
 const Launchers<double>* launchers_f64_n20();
 const Launchers<double>* launchers_f64_n21();
+const Launchers<double>* launchers_f64_n34();
+const Launchers<double>* launchers_f64_n35();
+const Launchers<double>* launchers_f64_n36();
+const Launchers<double>* launchers_f64_n37();
 
 template <>
 const Launchers<float>* launchers_for<float>(int N) {
@@ -32,6 +40,10 @@ const Launchers<float>* launchers_for<float>(int N) {
     case kColloc + 3: return launchers_f32_n19();
     case kColloc + 4: return launchers_f32_n20();
     case kColloc + 5: return launchers_f32_n21();
+    case kReduced + 2: return launchers_f32_n34();
+    case kReduced + 3: return launchers_f32_n35();
+    case kReduced + 4: return launchers_f32_n36();
+    case kReduced + 5: return launchers_f32_n37();
     default: return nullptr;
   }
 }
@@ -47,6 +59,10 @@ const Launchers<double>* launchers_for<double>(int N) {
     case kColloc + 3: return launchers_f64_n19();
     case kColloc + 4: return launchers_f64_n20();
     case kColloc + 5: return launchers_f64_n21();
+    case kReduced + 2: return launchers_f64_n34();
+    case kReduced + 3: return launchers_f64_n35();
+    case kReduced + 4: return launchers_f64_n36();
+    case kReduced + 5: return launchers_f64_n37();
     default: return nullptr;
   }
 }

@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kBlock) k_split_volume(StageParams<T> p, Split
     load_nodes<T, NP, NPP>(p.s.B + e, ks, bb);
     T gm[4];
     load_row_global<T, 4>(p.s.geo + 4 * (size_t)e, gm);
-    const T md = (!Dims<N>::COLLOC && p.s.dry[e]) ? T(1) : T(0);
+    const T md = (Dims<N>::EXACT && p.s.dry[e]) ? T(1) : T(0);
     T R0[NP], R1[NP], R2[NP];
 #pragma unroll
     for (int i = 0; i < NP; ++i) { R0[i] = 0; R1[i] = 0; R2[i] = 0; }
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(kBlock) k_split_surface(StageParams<T> p, Spli
     T gm[4];
     load_row_global<T, 4>(p.s.geo + 4 * (size_t)e, gm);
     const T rx = gm[0], ry = gm[1], sx = gm[2], sy = gm[3];
-    const T md = (!Dims<N>::COLLOC && p.s.dry[e]) ? T(1) : T(0);
+    const T md = (Dims<N>::EXACT && p.s.dry[e]) ? T(1) : T(0);
     const T E0 = __ldg(p.s.q + (size_t)((k >> (level_of(sc, e) - 1)) & 1) * bstride + e);
     const T B0 = __ldg(p.s.B + e);
     const int4 cn = __ldg(p.s.conn + e);

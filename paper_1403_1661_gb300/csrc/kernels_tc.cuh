@@ -140,8 +140,8 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(StageParams<float> p) 
 #pragma unroll
       for (int i = 0; i < NP; ++i) s_state[(3 * KP + i) * LS + lane] = __ldg(p.s.B + e + i * ks);
       reinterpret_cast<float4*>(s_geo)[lane] = __ldg(reinterpret_cast<const float4*>(p.s.geo) + e);
-      // depth form of the pressure for dry elements (not with the collocation scheme)
-      s_md[lane] = (!Dims<N>::COLLOC && p.s.dry[e]) ? 1.f : 0.f;
+      // depth form of the pressure for dry elements (exact rules only)
+      s_md[lane] = (Dims<N>::EXACT && p.s.dry[e]) ? 1.f : 0.f;
     } else {
       s_md[lane] = 0.f;
 #pragma unroll

@@ -249,7 +249,7 @@ int ref_num_cubature(int N) {
 
 int ref_num_gauss(int N) { return (3 * N + 2) / 2; }  // ceil((3N+1)/2)
 
-RefElem RefElem::build(int N) {
+RefElem RefElem::build(int N, int q_in, int ng_in) {
   if (N < 1 || N > 7) throw std::runtime_error("order out of range");
   RefElem e;
   e.N = N;
@@ -263,7 +263,7 @@ RefElem RefElem::build(int N) {
   std::vector<double> Mmat = inverse(VVt, np);
 
   // volume cubature: conical product, Gauss-Legendre (a) x Gauss-Jacobi(1,0) (b)
-  int q = (3 * N + 1) / 2;
+  const int q = q_in > 0 ? q_in : (3 * N + 1) / 2;
   std::vector<double> xa, wa, xb, wb;
   jacobi_gauss(q, 0.0, 0.0, xa, wa);
   jacobi_gauss(q, 1.0, 0.0, xb, wb);
@@ -291,7 +291,7 @@ RefElem RefElem::build(int N) {
   e.P = project(e.Ic);
 
   // faces: Gauss-Legendre, lift and the 1D face interpolation
-  e.Ng = ref_num_gauss(N);
+  e.Ng = ng_in > 0 ? ng_in : ref_num_gauss(N);
   const int ng = e.Ng;
   jacobi_gauss(ng, 0.0, 0.0, e.tg, e.wg);
   const double vr[3] = {-1.0, 1.0, -1.0}, vs[3] = {-1.0, -1.0, 1.0};

@@ -28,7 +28,10 @@ struct RefElem {
   int vertex_node[3] = {0, 0, 0};
   int face_node[3][8] = {};                 // face f, position m (from vertex f to f+1)
 
-  static RefElem build(int N);
+  // q: points per direction of the conical-product volume rule (exact to degree
+  // 2q - 1), ng: Gauss points per face; 0 = the defaults ceil(3N/2) and
+  // ceil((3N+1)/2) (degrees 3N - 1 and 3N)
+  static RefElem build(int N, int q = 0, int ng = 0);
 };
 
 // Library node index of lattice point (i, j): i = N * weight of vertex 2,

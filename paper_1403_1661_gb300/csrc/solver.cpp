@@ -102,13 +102,15 @@ int check_params(const swe_params* p) {
   if (p->nlevels_max < 1 || p->nlevels_max > swe::kMaxLevels)
     return fail(SWE_EINVAL, "nlevels_max must be in 1..8");
   if (p->limiter_mask & ~3) return fail(SWE_EINVAL, "unknown limiter bits");
-  if (p->scheme != SWE_SCHEME_CUBATURE && p->scheme != SWE_SCHEME_COLLOCATION)
+  if (p->scheme != SWE_SCHEME_CUBATURE && p->scheme != SWE_SCHEME_COLLOCATION &&
+      p->scheme != SWE_SCHEME_CUBATURE_2N)
     return fail(SWE_EINVAL, "unknown scheme");
   return SWE_OK;
 }
 
 int scheme_code(const swe_params* p) {
-  return p->N + (p->scheme == SWE_SCHEME_COLLOCATION ? swe::kColloc : 0);
+  return p->N + (p->scheme == SWE_SCHEME_COLLOCATION ? swe::kColloc : 0) +
+         (p->scheme == SWE_SCHEME_CUBATURE_2N ? swe::kReduced : 0);
 }
 
 // Base class so the C handle does not depend on the precision.
@@ -451,7 +453,7 @@ swe::RefElem collocation_of(const swe::RefElem& e) {
 }
 
 void pack_ops(int code, const swe::RefElem& e, std::vector<double>& o, std::vector<uint32_t>& tc) {
-  constexpr int C = swe::kColloc;
+  constexpr int C = swe::kColloc, R = swe::kReduced;
   switch (code) {
     case 2: pack_ops_n<2>(e, o, tc); break;
     case 3: pack_ops_n<3>(e, o, tc); break;
@@ -461,6 +463,10 @@ void pack_ops(int code, const swe::RefElem& e, std::vector<double>& o, std::vect
     case C + 3: pack_ops_n<C + 3>(collocation_of(e), o, tc); break;
     case C + 4: pack_ops_n<C + 4>(collocation_of(e), o, tc); break;
     case C + 5: pack_ops_n<C + 5>(collocation_of(e), o, tc); break;
+    case R + 2: pack_ops_n<R + 2>(e, o, tc); break;   // e holds the order-2N rules
+    case R + 3: pack_ops_n<R + 3>(e, o, tc); break;
+    case R + 4: pack_ops_n<R + 4>(e, o, tc); break;
+    case R + 5: pack_ops_n<R + 5>(e, o, tc); break;
     default: break;
   }
 }
@@ -475,6 +481,10 @@ int tc_size_of(int N) {
     case swe::kColloc + 3: return swe::TcLayout<swe::kColloc + 3>::SIZE;
     case swe::kColloc + 4: return swe::TcLayout<swe::kColloc + 4>::SIZE;
     case swe::kColloc + 5: return swe::TcLayout<swe::kColloc + 5>::SIZE;
+    case swe::kReduced + 2: return swe::TcLayout<swe::kReduced + 2>::SIZE;
+    case swe::kReduced + 3: return swe::TcLayout<swe::kReduced + 3>::SIZE;
+    case swe::kReduced + 4: return swe::TcLayout<swe::kReduced + 4>::SIZE;
+    case swe::kReduced + 5: return swe::TcLayout<swe::kReduced + 5>::SIZE;
     default: return 0;
   }
 }
@@ -1106,7 +1116,8 @@ int swe_solver_create(const swe_mesh* mesh, const swe_params* params, void* dev_
   s->N = params->N;
   s->code = scheme_code(params);
   s->K = mesh->m.K;
-  s->ref = swe::RefElem::build(s->N);
+  s->ref = params->scheme == SWE_SCHEME_CUBATURE_2N ? swe::RefElem::build(s->N, s->N + 1, s->N + 1)
+                                                      : swe::RefElem::build(s->N);
   s->Np = s->ref.Np;
   s->NPP = npp_of(s->N);
   s->KS = ks_of(s->K);

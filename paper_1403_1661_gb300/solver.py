@@ -126,7 +126,8 @@ class Solver:
         self.prm = nat.swe_params(g, h0, eps, tvb_M, tvb_nu, cfl, N, nlevels_max,
                                   _prec_code(precision), limiter_mask, dry_mode,
                                   {"cubature": nat.SWE_SCHEME_CUBATURE,
-                                   "collocation": nat.SWE_SCHEME_COLLOCATION}[scheme])
+                                   "collocation": nat.SWE_SCHEME_COLLOCATION,
+                                   "cubature_2n": nat.SWE_SCHEME_CUBATURE_2N}[scheme])
         self.precision = self.prm.precision
         nbytes = C.c_size_t()
         nat.check(L.swe_workspace_bytes(mesh.handle, C.byref(self.prm), C.byref(nbytes)),

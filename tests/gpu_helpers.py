@@ -11,10 +11,16 @@ def both(scn, precision, levels=None, dt_min=None, mesh_arrays=None, scheme="cub
     import paper_1403_1661_gb300 as P
     arrays = scn.build_mesh() if mesh_arrays is None else mesh_arrays
     om, ref, model, integ = problem.build(scn, levels=levels, dt_min=dt_min, mesh_arrays=arrays)
-    if scheme == "collocation":
-        from oracle.colloc import CollocModel
+    if scheme != "cubature":
         from oracle.mrab import MRAB
-        model = CollocModel(om, ref, model.B, scn.g, scn.h0)
+        if scheme == "collocation":
+            from oracle.colloc import CollocModel
+            model = CollocModel(om, ref, model.B, scn.g, scn.h0)
+        else:   # rules of integration order 2N, pre-balanced form
+            from oracle.prebalanced import PreBalancedModel
+            from oracle.refelem import RefElement
+            ref = RefElement(scn.N, cub_degree=2 * scn.N, ng=scn.N + 1)
+            model = PreBalancedModel(om, ref, model.B, scn.g, scn.h0)
         B, h, hu, hv = problem.nodal_inputs(scn, om, ref)
         integ = MRAB(model, h, hu, hv, integ.level, integ.dt_min, limiter_mask=scn.limiter_mask,
                      tvb_M=scn.tvb_M, tvb_nu=scn.tvb_nu, dry_mode=scn.dry_mode)

@@ -1,0 +1,91 @@
+"""Rules of integration order 2N (the caption of Fig. 2: a conical product of
+(N+1)^2 points, N + 1 Gauss points per face) on the GPU, in the pre-balanced form,
+against oracle/prebalanced.py with the same rules.
+
+* R on the graded, jittered bump with moving water, N = 2..5, every tier.
+* Still water exactly at rest (the pre-balanced pressure is linear in B).
+* The multirate beach (4 levels, PP + TVB), two macro steps.
+* Convergence on the stationary vortex.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from tests.gpu_helpers import both, state_errors
+from tests.test_gpu_parity import TOL_R, TOL_STATE, _rhs_case
+from workloads import scenarios as sc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_1661_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32tc"])
+def test_reduced_rhs_matches_oracle(N, precision):
+    scn = _rhs_case(N, precision)
+    om, ref, model, integ, s = both(scn, precision, scheme="cubature_2n")
+    assert ref.Ncub == (N + 1) ** 2
+    q = integ.q_end
+    R_o = model.rhs(q[0], q[1], q[2])
+    R_g = s.rhs().cpu().numpy().astype(np.float64)
+    errs = [np.abs(R_g[c] - R_o[c]).max() / np.abs(R_o[c]).max() for c in range(3)]
+    print(f"PARITY order-2N rhs N={N} {precision} " + " ".join(f"{e:.3e}" for e in errs), flush=True)
+    assert max(errs) < TOL_R[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32tc"])
+@pytest.mark.parametrize("bed", ["smooth", "discontinuous"])
+def test_reduced_lake_at_rest(precision, bed):
+    scn = _rhs_case(3, precision, moving=False, bed=bed)
+    scn.init = lambda x, y, cx, cy, B: (0.0 - B, 0 * B, 0 * B)
+    om, ref, model, integ, s = both(scn, precision, scheme="cubature_2n")
+    assert np.abs(s.rhs().cpu().numpy()).max() == 0.0
+    scn.init = lambda x, y, cx, cy, B: (0.3 - B, 0 * B, 0 * B)
+    om, ref, model, integ, s = both(scn, precision, scheme="cubature_2n")
+    R = s.rhs().cpu().numpy()
+    scale = 9.81 * 1.3 ** 2 * max(np.abs(om.rx).max(), np.abs(om.sy).max())
+    print(f"PARITY order-2N lake eta=0.3 {bed} {precision} rel={np.abs(R).max() / scale:.3e}", flush=True)
+    assert np.abs(R).max() < {"fp64": 1e-13, "fp32": 1e-5, "fp32tc": 1e-3}[precision] * scale
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32tc"])
+def test_reduced_mrab_tsunami_levels(precision):
+    scn = sc.tsunami(nx=40, ny=10, N=3, nlevels=4)
+    om, ref, model, integ, s = both(scn, precision, scheme="cubature_2n")
+    nsub = 2 * 2 ** (integ.L - 1)
+    for _ in range(nsub):
+        integ.substep()
+    s.substep(nsub)
+    eh, em, _ = state_errors(s, integ)
+    hmax = integ.q_end[0].max()
+    print(f"PARITY order-2N tsunami L={integ.L} {precision} eh={eh / hmax:.3e} "
+          f"em={em / (hmax * np.sqrt(9.81 * hmax)):.3e}", flush=True)
+    tol = TOL_STATE[precision]
+    assert eh < tol * hmax and em < tol * hmax * np.sqrt(9.81 * hmax)
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_reduced_stationary_vortex_converges(N):
+    import paper_1403_1661_gb300 as P
+    import tests.test_gpu_verification as tv
+    errs = []
+    for n in (12, 24, 48):
+        m, ref, x, y, ns, dt = tv._steps(N, n)
+        s = P.solver_from_scenario(tv._scenario(N, n), precision="fp64", levels=np.ones(m.K, np.int32),
+                                   dt_min=dt, scheme="cubature_2n")
+        s.substep(ns)
+        h = s.get_state()[0]
+        errs.append(tv._l2(m, ref, h - tv._exact(x, y)[0]))
+    eoc = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    print(f"PARITY order-2N vortex N={N} errors " + " ".join(f"{e:.3e}" for e in errs)
+          + " EOC " + " ".join(f"{v:.2f}" for v in eoc), flush=True)
+    assert min(eoc) >= N - 0.5
