@@ -327,3 +327,29 @@ def test_parabolic_bowl_rates():
     assert _rate(eg[:2]) >= 1.0 and eg[2] < eg[1] and _rate(el) >= 3.0
     assert max(r[2] for r in res) < 1e-11
     assert min(r[3] for r in res) >= BOWL_DRY - 1e-15
+
+
+@pytest.mark.parametrize("scheme", ["collocation", "cubature_2n"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32tc"])
+def test_thacker_other_schemes(thacker_oracle, scheme, precision):
+    """The oscillating lake with the collocation scheme and with the order-2N rules
+    (PP + TVB, single rate): the quarter-period state against the closed form within
+    the cubature scheme's bound, exact FP64 mass accounting, depth >= the dry depth."""
+    import paper_1403_1661_gb300 as P
+    om, ref, integ, nsub, _ = thacker_oracle
+    s = P.solver_from_scenario(_thacker_scenario(), precision=precision, levels=integ.level,
+                               dt_min=integ.dt_min, scheme=scheme)
+    st0 = s.stats()
+    s.substep(nsub)
+    h, hu, hv, t = s.get_state()
+    x, y = om.map_to_physical(ref.r, ref.s)
+    he = _thacker(x, y, t)[0]
+    wet = he.min(axis=1) > 0.02
+    l1 = np.abs(h - he)[wet].sum() / he[wet].sum()
+    st = s.stats()
+    drift = abs((st["mass"] - st0["mass"]) - (st["injected_mass"] - st0["injected_mass"])) / st0["mass"]
+    print(f"PARITY thacker {scheme} {precision}: L1(wet) vs exact {l1:.3e}, hmin {h.min():.3e}, "
+          f"mass drift {drift:.3e}", flush=True)
+    assert np.isfinite(h).all() and l1 < 2.5e-2
+    assert h.min() >= 1e-3 - {"fp64": 1e-12, "fp32tc": 1e-7}[precision]
+    assert drift < {"fp64": 1e-12, "fp32tc": 1e-3}[precision]
