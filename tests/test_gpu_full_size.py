@@ -69,3 +69,27 @@ def test_full_size_macro_step_matches_oracle(full):
           f"deta={deta:.3e} m (wave amplitude 2 m)", flush=True)
     assert np.isfinite(h).all() and h.min() >= -1e-6
     assert eh < TOL_STATE * hmax and em < TOL_STATE * hmax * np.sqrt(9.81 * hmax)
+
+
+@pytest.mark.parametrize("scheme", ["collocation", "cubature_2n"])
+def test_full_size_rhs_other_schemes(full, scheme):
+    """R of the 500,000-triangle initial state with the collocation scheme and with
+    the order-2N rules (tensor-core tier, as bench.py times them) against their oracles."""
+    import paper_1403_1661_gb300 as P
+    scn, om, model, integ, _ = full
+    if scheme == "collocation":
+        from oracle.colloc import CollocModel
+        m2, ref2 = CollocModel(om, model.ref, model.B, scn.g, scn.h0), model.ref
+    else:
+        from oracle.prebalanced import PreBalancedModel
+        from oracle.refelem import RefElement
+        ref2 = RefElement(scn.N, cub_degree=2 * scn.N, ng=scn.N + 1)
+        m2 = PreBalancedModel(om, ref2, model.B, scn.g, scn.h0)
+    s = P.solver_from_scenario(scn, precision="fp32tc", levels=integ.level, dt_min=integ.dt_min, scheme=scheme)
+    h, hu, hv, _ = s.get_state()            # the device's limited initial state
+    R_o = m2.rhs(h, hu, hv)
+    R_g = s.rhs().cpu().numpy().astype(np.float64)
+    errs = [np.abs(R_g[c] - R_o[c]).max() / np.abs(R_o[c]).max() for c in range(3)]
+    print(f"PARITY full-size rhs {scheme} fp32tc", " ".join(f"{e:.3e}" for e in errs), flush=True)
+    assert np.isfinite(R_g).all()
+    assert max(errs) < TOL_R
