@@ -184,3 +184,38 @@ def test_batch_refuses_stale_graph_after_regroup():
     again.close()
     for x, y in zip(a.get_state()[:3], b.get_state()[:3]):
         assert np.array_equal(x, y)
+
+
+def test_checkpoint_after_regroup_resumes_bit_identically():
+    import paper_1403_1661_gb300 as P
+    scn = sc.tsunami(nx=40, ny=10, N=3, nlevels=4)
+    a = P.solver_from_scenario(scn, precision="fp32tc")
+    a.step(3)
+    a.regroup(_new_levels(a.level, seed=3))
+    a.step(1)
+    ck = a.full_state()
+    a.step(2)
+    ref = a.get_state()
+    b = P.solver_from_scenario(scn, precision="fp32tc")
+    b.load_full_state(ck)
+    b.step(2)
+    for x, y in zip(ref[:3], b.get_state()[:3]):
+        assert np.array_equal(x, y)
+
+
+def test_regroup_collocation_matches_oracle():
+    scn = sc.tsunami(nx=40, ny=10, N=3, nlevels=4)
+    om, ref, model, integ, s = both(scn, "fp64", scheme="collocation")
+    for _ in range(3 * 2 ** (integ.L - 1)):
+        integ.substep()
+    s.step(3)
+    new = _new_levels(integ.level, seed=5)
+    integ.regroup(new)
+    s.regroup(new)
+    for _ in range(2 * 2 ** (integ.L - 1)):
+        integ.substep()
+    s.step(2)
+    eh, em, _ = state_errors(s, integ)
+    hmax = integ.q_end[0].max()
+    print(f"PARITY regroup collocation fp64 eh={eh / hmax:.3e}", flush=True)
+    assert eh < 1e-11 * hmax and em < 1e-11 * hmax * np.sqrt(9.81 * hmax)
