@@ -19,7 +19,8 @@ Readings where the paper is silent or garbled:
   of 1e-6 (hbar + |m-bar|/c) in depth units, times c for the shear component, so
   that deltas at round-off level never count as limited), positive/negative
   redistribution so the deltas sum to zero. The P^N solution is kept when no
-  characteristic component was changed. A wall face uses a ghost neighbour whose
+  characteristic component was changed. A far-field face uses the far-field state
+  (over the own mean bed) as its ghost mean. A wall face uses a ghost neighbour whose
   barycentre is b_0 reflected across the face and whose mean has the normal
   momentum reversed.
 * the limited depth is P1: h = (limited eta) - Pi1 B, then the positivity
@@ -192,7 +193,12 @@ def tvb_limit(model: SWEModel, h, hu, hv, dry, active=None, M: float = 0.0, nu: 
         inner = nb >= 0
         unb[inner, f, :] = ubar[nb[inner]]
         gi = ~inner
-        if np.any(gi):
+        if np.any(gi) and getattr(model, "farfield", None) is not None:
+            hf, huf, hvf = model.farfield      # far-field ghost mean over the own mean bed
+            unb[gi, f, 0] = hf + Bbar[e[gi]]
+            unb[gi, f, 1] = huf
+            unb[gi, f, 2] = hvf
+        elif np.any(gi):
             nx, ny = mesh.nx[e[gi], f], mesh.ny[e[gi], f]
             mn = u0[gi, 1] * nx + u0[gi, 2] * ny
             unb[gi, f, 0] = u0[gi, 0]

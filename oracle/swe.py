@@ -16,7 +16,8 @@ Readings where the paper is silent:
 * LLF speed lambda = max(|u^- . n| + sqrt(g h*^-), |u^+ . n| + sqrt(g h*^+)) per point.
 * velocity u = hu/h where h > h0 (1 + 1e-6), else 0 (volume and surface alike).
 * reflective wall: ghost h^+ = h^-, B^+ = B^-, m^+ = m^- - 2 (m^- . n) n.
-* Dirichlet faces (used only by the convergence pin): ghost = exact state.
+* Dirichlet faces (the convergence pin) and far-field faces (a constant state):
+  ghost = that state, bed continued.
 """
 from __future__ import annotations
 
@@ -76,10 +77,17 @@ class SWEModel:
     """Mesh + reference element + bathymetry: evaluates R(Q) for all elements."""
 
     def __init__(self, mesh: Mesh, ref: RefElement, B, g: float, h0: float,
-                 dirichlet=None):
+                 dirichlet=None, farfield=None):
         self.mesh = mesh
         self.ref = ref
         self.B = np.asarray(B, np.float64)            # (K, Np) nodal bathymetry
+        # far field: every boundary face sees the constant state (h, hu, hv), the bed
+        # continued (B+ = B-); the TVB limiter's ghost mean is that state
+        self.farfield = None if farfield is None else tuple(float(v) for v in farfield)
+        if self.farfield is not None:
+            hf, huf, hvf = self.farfield
+            dirichlet = lambda x, y, t: (np.full(np.shape(x), hf), np.full(np.shape(x), huf),
+                                         np.full(np.shape(x), hvf))
         self.g = float(g)
         self.h0 = float(h0)
         self.dirichlet = dirichlet                     # callable(x, y, t) -> (h, hu, hv) or None
