@@ -135,8 +135,10 @@ struct Sched {
 struct Phys {
   double g, h0, eps, tvb_M, tvb_nu;
   double hvel;   // velocity u = hu/h only where h > hvel = h0 (1 + 1e-6), else 0
+  double ff_h, ff_hu, ff_hv;   // far-field state of the boundary faces (when farfield)
   float eps_f;
   int pp, dry_mode;
+  int farfield;  // 1: boundary faces see the far-field state; 0: reflecting walls
 };
 
 template <typename T>

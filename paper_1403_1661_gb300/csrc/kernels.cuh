@@ -452,6 +452,8 @@ __device__ __forceinline__ void surface_fluxes(const StageParams<T>& p, const T*
           tp.hv += i1n[m] * nv[m];
           tp.b += i1n[m] * nB[m];
         }
+      } else if (p.ph.farfield) {  // far field: the constant state over the continued bed
+        tp = {(T)p.ph.ff_h - hf + tm.b, (T)p.ph.ff_hu, (T)p.ph.ff_hv, tm.b};
       } else {  // reflecting wall: mirror the normal momentum
         const T mn = tm.hu * nx + tm.hv * ny;
         tp = {tm.e, tm.hu - T(2) * mn * nx, tm.hv - T(2) * mn * ny, tm.b};
@@ -837,10 +839,16 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_tvb(LimitPar
     }
     if (de || dn) continue;
     const T rx = gm[0], ry = gm[1], sx = gm[2], sy = gm[3];
-    // a wall face mirrors the normal momentum of the own mean
+    // a far-field face sees the far-field state over the own mean bed; a wall face
+    // mirrors the normal momentum of the own mean
+    const T Bbar_e = (T)p.s.Bbar[e];
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-      if (nbs[f] < 0) {
+      if (nbs[f] < 0 && p.ph.farfield) {
+        un[f][0] = (T)p.ph.ff_h + Bbar_e;
+        un[f][1] = (T)p.ph.ff_hu;
+        un[f][2] = (T)p.ph.ff_hv;
+      } else if (nbs[f] < 0) {
         const T vxn = f == 0 ? -sx : (f == 1 ? rx + sx : -rx);
         const T vyn = f == 0 ? -sy : (f == 1 ? ry + sy : -ry);
         const T sn = sqrt(vxn * vxn + vyn * vyn);
@@ -855,7 +863,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_tvb(LimitPar
     const T Jd = T(1) / (rx * sy - ry * sx);
     const T xr = Jd * sy, xs = -Jd * ry, yr = -Jd * sx, ys = Jd * rx;
     const T dr[3] = {T(1) / 3, T(1) / 3, T(-2) / 3}, ds[3] = {T(-2) / 3, T(1) / 3, T(1) / 3};
-    const T Bbar = (T)p.s.Bbar[e];
+    const T Bbar = Bbar_e;
     const T hb = u0[0] - Bbar;
     const T cb = sqrt(g * hb);
     const T ub = u0[1] / hb, vb0 = u0[2] / hb;

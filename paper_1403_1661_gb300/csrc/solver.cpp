@@ -153,6 +153,8 @@ struct swe_solver {
   int64_t launches = 0;
   cudaGraphExec_t graph = nullptr;
   uint64_t sched_version = 0;    // bumped whenever captured launches go stale (levels, order, launch shape)
+  bool farfield = false;         // boundary faces: far-field state ff (true) or reflecting walls
+  double ff[3] = {0.0, 0.0, 0.0};
   int graph_launches = 0;
   int64_t graph_dofs = 0;
   swe::KernelCfg cfg_max;   // occupancy limits (set_launch_config caps below these)
@@ -224,6 +226,10 @@ swe::Phys phys_of(const swe_solver* s, int mask) {
   ph.tvb_nu = s->prm.tvb_nu > 0 ? s->prm.tvb_nu : 1.5;
   ph.pp = (mask & SWE_LIM_PP) ? 1 : 0;
   ph.dry_mode = s->prm.dry_mode;
+  ph.farfield = s->farfield ? 1 : 0;
+  ph.ff_h = s->ff[0];
+  ph.ff_hu = s->ff[1];
+  ph.ff_hv = s->ff[2];
   return ph;
 }
 
@@ -1580,6 +1586,18 @@ int swe_set_launch_config(swe_solver* s, int32_t ctas_per_sm) {
   s->cfg.grid_tc = cap(s->cfg_max.grid_tc);
   s->cfg.grid_tvb = cap(s->cfg_max.grid_tvb);
   s->cfg.grid_pos = cap(s->cfg_max.grid_pos);
+  invalidate_graph(s);
+  return SWE_OK;
+}
+
+int swe_set_farfield(swe_solver* s, int32_t enable, double h, double hu, double hv) {
+  if (!s || (enable != 0 && enable != 1)) return fail(SWE_EINVAL, "bad arguments");
+  if (enable && !(std::isfinite(h) && std::isfinite(hu) && std::isfinite(hv) && h >= 0.0))
+    return fail(SWE_EINVAL, "far-field state must be finite with h >= 0");
+  s->farfield = enable != 0;
+  s->ff[0] = enable ? h : 0.0;
+  s->ff[1] = enable ? hu : 0.0;
+  s->ff[2] = enable ? hv : 0.0;
   invalidate_graph(s);
   return SWE_OK;
 }

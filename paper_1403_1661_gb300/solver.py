@@ -170,6 +170,14 @@ class Solver:
         nat.check(nat.lib().swe_set_levels(self.handle, nat.iptr(lev), float(dt_min)), "swe_set_levels")
         self.level = lev.copy()
 
+    def set_farfield(self, state=None):
+        """Boundary faces: reflecting walls (state=None) or the far-field (h, hu, hv)."""
+        if state is None:
+            nat.check(nat.lib().swe_set_farfield(self.handle, 0, 0.0, 0.0, 0.0), "swe_set_farfield")
+        else:
+            h, hu, hv = (float(v) for v in state)
+            nat.check(nat.lib().swe_set_farfield(self.handle, 1, h, hu, hv), "swe_set_farfield")
+
     def regroup(self, level=None):
         """Regroup into new levels without restarting (history kept); level=None
         applies the CFL rule. Returns (levels in caller order, CFL margin)."""

@@ -1,0 +1,135 @@
+"""The far-field boundary on the GPU (swe_set_farfield) against the oracle's.
+
+* R with every boundary face open to a far field, moving water over a bump, every
+  tier and N = 2..4.
+* A uniform stream with the same far field stays uniform (R = 0 to round-off).
+* PP + TVB with far-field faces (the limiter's ghost mean): ten steps.
+* Section 6.2's translating vortex on [-5, 10] x [-6, 6] with the far field at the
+  free stream (the vortex's own boundary values to 1e-10): order N + 1/2 or better.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import problem
+from oracle.mrab import MRAB
+from oracle.swe import SWEModel
+from tests.test_gpu_parity import TOL_R, TOL_STATE, _rhs_case
+from workloads import meshes, scenarios as sc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_1661_gb300 import build
+    build.build()
+
+
+def _both_ff(scn, precision, ff):
+    import paper_1403_1661_gb300 as P
+    om, ref, model, integ = problem.build(scn)
+    mff = SWEModel(om, ref, model.B, scn.g, scn.h0, farfield=ff)
+    B, h, hu, hv = problem.nodal_inputs(scn, om, ref)
+    integ = MRAB(mff, h, hu, hv, integ.level, integ.dt_min, limiter_mask=scn.limiter_mask, tvb_M=scn.tvb_M,
+                 tvb_nu=scn.tvb_nu, dry_mode=scn.dry_mode)
+    # the far field is set before the state, whose initial limiting (TVB) sees it
+    vx, vy, E = scn.build_mesh()
+    mesh = P.Mesh(vx, vy, E)
+    s = P.Solver(mesh, scn.N, g=scn.g, h0=scn.h0, cfl=scn.cfl, nlevels_max=max(scn.nlevels, 1),
+                 precision=precision, limiter_mask=scn.limiter_mask, tvb_M=scn.tvb_M, tvb_nu=scn.tvb_nu,
+                 dry_mode=scn.dry_mode)
+    s.set_farfield(ff)
+    Bd, hd, hud, hvd = P.scenario_inputs(scn, mesh)
+    s.set_bathymetry(Bd)
+    s.set_state(hd, hud, hvd)
+    s.set_levels(integ.level, integ.dt_min)
+    return om, ref, mff, integ, s
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32tc"])
+def test_farfield_rhs_matches_oracle(N, precision):
+    scn = _rhs_case(N, precision)
+    om, ref, model, integ, s = _both_ff(scn, precision, (1.05, 0.2, -0.1))
+    q = integ.q_end
+    R_o = model.rhs(q[0], q[1], q[2])
+    R_g = s.rhs().cpu().numpy().astype(np.float64)
+    errs = [np.abs(R_g[c] - R_o[c]).max() / np.abs(R_o[c]).max() for c in range(3)]
+    print(f"PARITY far-field rhs N={N} {precision} " + " ".join(f"{e:.3e}" for e in errs), flush=True)
+    assert max(errs) < TOL_R[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32tc"])
+def test_farfield_free_stream(precision):
+    import paper_1403_1661_gb300 as P
+    scn = _rhs_case(3, precision, moving=False)
+    scn.bathymetry = sc.flat_bed(1.3)
+    scn.init = lambda x, y, cx, cy, B: (0 * x + 1.3, 0 * x + 0.4 * 1.3, 0 * x - 0.25 * 1.3)
+    s = P.solver_from_scenario(scn, precision=precision)
+    s.set_farfield((1.3, 0.4 * 1.3, -0.25 * 1.3))
+    R = s.rhs().cpu().numpy()
+    from oracle.mesh import Mesh
+    vx, vy, E = scn.build_mesh()
+    om = Mesh(vx, vy, E)
+    scale = 9.81 * 1.3 ** 2 * max(np.abs(om.rx).max(), np.abs(om.sy).max())
+    print(f"PARITY far-field free stream {precision} rel={np.abs(R).max() / scale:.3e}", flush=True)
+    assert np.abs(R).max() < {"fp64": 1e-13, "fp32": 1e-5, "fp32tc": 1e-3}[precision] * scale
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32tc"])
+def test_farfield_limiters_ten_steps(precision):
+    scn = _rhs_case(3, precision, limiter_mask=3)
+    scn.tvb_M = 0.0
+    om, ref, model, integ, s = _both_ff(scn, precision, (1.0, 0.3, 0.0))
+    for _ in range(10):
+        integ.substep()
+    s.substep(10)
+    h, hu, hv, t = s.get_state()
+    q = integ.q_end
+    hmax = q[0].max()
+    eh = np.abs(h - q[0]).max() / hmax
+    em = max(np.abs(hu - q[1]).max(), np.abs(hv - q[2]).max()) / (hmax * np.sqrt(9.81 * hmax))
+    print(f"PARITY far-field PP+TVB {precision} eh={eh:.3e} em={em:.3e}", flush=True)
+    assert eh < TOL_STATE[precision] and em < TOL_STATE[precision]
+
+
+def _vortex(x, y, t, beta=5.0):
+    r2 = (x - t) ** 2 + y ** 2
+    e = np.exp(1.0 - r2)
+    h = 1.0 - beta ** 2 / (32.0 * np.pi ** 2) * e ** 2
+    return h, h * (1.0 - beta * e * y / (2 * np.pi)), h * (beta * e * (x - t) / (2 * np.pi))
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_translating_vortex_converges(N):
+    import paper_1403_1661_gb300 as P
+    from oracle.mesh import Mesh, element_dt
+    from oracle.refelem import RefElement
+    T = 0.5
+    errs = []
+    for n in (20, 40, 80):
+        ny = int(n * 12 / 15 + 0.5)
+        scn = sc.Scenario(name="tv", N=N, g=2.0, h0=1e-8, cfl=0.25, nlevels=1, limiter_mask=0, tvb_M=0.0,
+                          mesh=lambda n=n, ny=ny: meshes.structured_rect(-5, 10, -6, 6, n, ny),
+                          bathymetry=lambda x, y, cx=None, cy=None: 0.0 * x, init=None)
+        scn.init = lambda x, y, cx, cy, B: _vortex(x, y, 0.0)
+        vx, vy, E = scn.build_mesh()
+        m, ref = Mesh(vx, vy, E), RefElement(N)
+        x, y = m.map_to_physical(ref.r, ref.s)
+        h, hu, hv = _vortex(x, y, 0.0)
+        ns = int(math.ceil(T / element_dt(m, N, h, hu, hv, 2.0, 0.25).min()))
+        s = P.solver_from_scenario(scn, precision="fp64", levels=np.ones(m.K, np.int32), dt_min=T / ns)
+        s.set_farfield((1.0, 1.0, 0.0))
+        s.substep(ns)
+        hg = s.get_state()[0]
+        err = hg - _vortex(x, y, T)[0]
+        errs.append(math.sqrt((np.einsum("ki,ij,kj->k", err, ref.M, err) * m.J).sum()))
+    eoc = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    print(f"PARITY translating vortex N={N} errors " + " ".join(f"{e:.3e}" for e in errs)
+          + " EOC " + " ".join(f"{v:.2f}" for v in eoc), flush=True)
+    assert eoc[-1] >= N + 0.3
