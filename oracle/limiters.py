@@ -193,17 +193,22 @@ def tvb_limit(model: SWEModel, h, hu, hv, dry, active=None, M: float = 0.0, nu: 
         inner = nb >= 0
         unb[inner, f, :] = ubar[nb[inner]]
         gi = ~inner
-        if np.any(gi) and getattr(model, "farfield", None) is not None:
-            hf, huf, hvf = model.farfield      # far-field ghost mean over the own mean bed
-            unb[gi, f, 0] = hf + Bbar[e[gi]]
-            unb[gi, f, 1] = huf
-            unb[gi, f, 2] = hvf
-        elif np.any(gi):
-            nx, ny = mesh.nx[e[gi], f], mesh.ny[e[gi], f]
-            mn = u0[gi, 1] * nx + u0[gi, 2] * ny
-            unb[gi, f, 0] = u0[gi, 0]
-            unb[gi, f, 1] = u0[gi, 1] - 2.0 * mn * nx
-            unb[gi, f, 2] = u0[gi, 2] - 2.0 * mn * ny
+        go = np.zeros_like(gi)                  # open (far-field) boundary faces
+        if getattr(model, "farfield", None) is not None:
+            ffm = getattr(model, "farfield_faces", None)
+            go = gi if ffm is None else gi & ffm[e, f]
+        gw = gi & ~go                           # walls
+        if np.any(go):
+            hf, huf, hvf = model.farfield       # far-field ghost mean over the own mean bed
+            unb[go, f, 0] = hf + Bbar[e[go]]
+            unb[go, f, 1] = huf
+            unb[go, f, 2] = hvf
+        if np.any(gw):
+            nx, ny = mesh.nx[e[gw], f], mesh.ny[e[gw], f]
+            mn = u0[gw, 1] * nx + u0[gw, 2] * ny
+            unb[gw, f, 0] = u0[gw, 0]
+            unb[gw, f, 1] = u0[gw, 1] - 2.0 * mn * nx
+            unb[gw, f, 2] = u0[gw, 2] - 2.0 * mn * ny
     # P1 part and the edge-midpoint deltas
     vn = ref.vertex_nodes
     qv = np.stack([(eta[e] @ ref.Pi1.T)[:, vn], (hu[e] @ ref.Pi1.T)[:, vn],

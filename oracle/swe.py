@@ -77,13 +77,15 @@ class SWEModel:
     """Mesh + reference element + bathymetry: evaluates R(Q) for all elements."""
 
     def __init__(self, mesh: Mesh, ref: RefElement, B, g: float, h0: float,
-                 dirichlet=None, farfield=None):
+                 dirichlet=None, farfield=None, farfield_faces=None):
         self.mesh = mesh
         self.ref = ref
         self.B = np.asarray(B, np.float64)            # (K, Np) nodal bathymetry
         # far field: every boundary face sees the constant state (h, hu, hv), the bed
         # continued (B+ = B-); the TVB limiter's ghost mean is that state
         self.farfield = None if farfield is None else tuple(float(v) for v in farfield)
+        # which boundary faces are open (K x 3 bool; None: all of them); the rest are walls
+        self.farfield_faces = None if farfield_faces is None else np.asarray(farfield_faces, bool)
         if self.farfield is not None:
             hf, huf, hvf = self.farfield
             dirichlet = lambda x, y, t: (np.full(np.shape(x), hf), np.full(np.shape(x), huf),
@@ -147,15 +149,22 @@ class SWEModel:
         kb, fb = np.nonzero(~inner)
         if kb.size:
             if self.dirichlet is None:
-                mn = hum[kb, fb] * nx[kb, fb] + hvm[kb, fb] * ny[kb, fb]
-                hp[kb, fb] = hm[kb, fb]
-                hup[kb, fb] = hum[kb, fb] - 2.0 * mn * nx[kb, fb]
-                hvp[kb, fb] = hvm[kb, fb] - 2.0 * mn * ny[kb, fb]
-                Bp[kb, fb] = Bm[kb, fb]
+                opn = np.zeros(kb.size, bool)
+            elif self.farfield_faces is None:
+                opn = np.ones(kb.size, bool)
             else:
-                eh, ehu, ehv = self.dirichlet(self.gx[kb, fb], self.gy[kb, fb], t)
-                hp[kb, fb], hup[kb, fb], hvp[kb, fb] = eh, ehu, ehv
-                Bp[kb, fb] = Bm[kb, fb]
+                opn = self.farfield_faces[kb, fb]
+            kw, fw = kb[~opn], fb[~opn]
+            mn = hum[kw, fw] * nx[kw, fw] + hvm[kw, fw] * ny[kw, fw]
+            hp[kw, fw] = hm[kw, fw]
+            hup[kw, fw] = hum[kw, fw] - 2.0 * mn * nx[kw, fw]
+            hvp[kw, fw] = hvm[kw, fw] - 2.0 * mn * ny[kw, fw]
+            Bp[kw, fw] = Bm[kw, fw]
+            ko, fo = kb[opn], fb[opn]
+            if ko.size:
+                eh, ehu, ehv = self.dirichlet(self.gx[ko, fo], self.gy[ko, fo], t)
+                hp[ko, fo], hup[ko, fo], hvp[ko, fo] = eh, ehu, ehv
+                Bp[ko, fo] = Bm[ko, fo]
         return wb_lf_flux(hm, hum, hvm, Bm, hp, hup, hvp, Bp, nx, ny, self.g, self.h0)
 
     # -- surface term, Section 7.2 --------------------------------------------

@@ -51,3 +51,23 @@ def test_still_water_through_far_field_faces():
     # a far field at another level is not at rest
     ff2 = SWEModel(m, ref, B, 9.81, 1e-5, farfield=(eta0 + 1.1, 0.0, 0.0))
     assert np.abs(ff2.rhs(h, 0 * h, 0 * h)).max() > 1e-6 * scale
+
+
+def test_mixed_faces_open_and_walls():
+    """Open faces on the left and right sides, walls at the bottom and top: a stream
+    along x with the same far field is at rest in R only if the walls are parallel
+    to it (they are), and a stream along y is not (the walls reflect it)."""
+    m, ref = _mesh(), RefElement(3)
+    opn = np.zeros((m.K, 3), bool)
+    for f in range(3):
+        bnd = m.EToE[:, f] < 0
+        opn[:, f] = bnd & (np.abs(m.nx[:, f]) > 0.5)      # faces on x = 0 and x = 1
+    h = np.full((m.K, ref.Np), 1.3)
+    B = np.full_like(h, -1.3)
+    scale = 9.81 * 1.3 ** 2 * max(np.abs(m.rx).max(), np.abs(m.sy).max())
+    along_x = SWEModel(m, ref, B, 9.81, 1e-5, farfield=(1.3, 0.5 * 1.3, 0.0), farfield_faces=opn)
+    assert np.abs(along_x.rhs(h, 0.5 * h, 0 * h)).max() < 1e-13 * scale
+    along_y = SWEModel(m, ref, B, 9.81, 1e-5, farfield=(1.3, 0.0, 0.5 * 1.3), farfield_faces=opn)
+    assert np.abs(along_y.rhs(h, 0 * h, 0.5 * h)).max() > 1e-3 * scale
+    h2, hu2, hv2, _ = tvb_limit(along_x, h, 0.5 * h, 0 * h, np.zeros(m.K, bool), M=0.0)
+    assert np.array_equal(hu2, 0.5 * h)
