@@ -287,18 +287,23 @@ int swe_batch_create(swe_solver* const* solvers, int32_t n, void* stream, swe_ba
  * SWE_EINVAL, with nothing launched, if any solver's levels, element order or
  * launch shape changed since swe_batch_create (swe_set_levels,
  * swe_setup_levels, swe_regroup, swe_set_launch_config, swe_set_farfield,
- * swe_set_full_state):
+ * swe_set_open_faces, swe_set_full_state):
  * the captured graph would run stale launches; create the batch again. */
 int swe_batch_step(swe_batch* batch, int32_t n_macro);
 void swe_batch_destroy(swe_batch* batch);
 
-/* Boundary faces (those without a neighbour): reflecting walls (enable = 0, the
- * default; Section 6's tests) or an open far field (enable = 1) whose ghost state is
- * the constant (h, hu, hv) over the continued bed (B+ = B-); the TVB limiter then
- * takes that state over the element's mean bed as the ghost mean. h >= 0 and all
- * finite, SWE_EINVAL otherwise. Takes effect at the next launch (a captured macro
- * step is captured again; batches must be created again). */
+/* Boundary faces (those without a neighbour) are reflecting walls (the default;
+ * Section 6's tests) or open to a far field whose ghost state is the constant
+ * (h, hu, hv) over the continued bed (B+ = B-); at an open face the TVB limiter
+ * takes that state over the element's mean bed as the ghost mean.
+ * swe_set_farfield sets the state and opens every boundary face (enable = 1) or
+ * closes them all (enable = 0); h >= 0 and all finite, SWE_EINVAL otherwise.
+ * swe_set_open_faces then chooses the open faces one by one: open (K x 3, caller
+ * order and face numbering, host) = 1 for open, 0 for a wall; entries of interior
+ * faces are ignored. Both take effect at the next launch (a captured macro step
+ * is captured again; batches must be created again). */
 int swe_set_farfield(swe_solver* solver, int32_t enable, double h, double hu, double hv);
+int swe_set_open_faces(swe_solver* solver, const uint8_t* open);
 
 /* Launch shape of the stage and limiter kernels: at most ctas_per_sm CTAs per
  * SM in their grid-stride loops (0 = as many as fit). Used by the autotuner;

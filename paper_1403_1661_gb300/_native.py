@@ -75,6 +75,7 @@ SIGNATURES = {
     "swe_regroup": (C.c_int, [_vp, _ip, _ip, _dp]),
     "swe_rhs": (C.c_int, [_vp, _vp]),
     "swe_set_farfield": (C.c_int, [_vp, C.c_int32, C.c_double, C.c_double, C.c_double]),
+    "swe_set_open_faces": (C.c_int, [_vp, C.c_void_p]),
     "swe_rhs_scratch_bytes": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_size_t)]),
     "swe_rhs_variant": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_size_t]),
     "swe_substep": (C.c_int, [_vp, C.c_int32]),

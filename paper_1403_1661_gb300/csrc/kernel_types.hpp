@@ -17,6 +17,10 @@ constexpr int kBlock = 128;
 //   kReduced  the rules of integration order 2N (a conical product of (N+1)^2 points,
 //             N + 1 Gauss points per face) instead of 3N - 1 and 3N
 constexpr int kColloc = 16;
+
+// Boundary faces in the connectivity: a neighbour index below zero.
+constexpr int kWall = -1;      // reflecting wall
+constexpr int kFarField = -2;  // open: the far-field state of Phys
 constexpr int kReduced = 32;
 
 template <int NN>
@@ -109,7 +113,7 @@ struct DevState {
   T* p1;                // [3][3][KS] vertex values of Pi1 (eta, hu, hv) after each commit
   const T* vb;          // [3][KS] vertex values of Pi1 B (static)
   const T* geo;         // [K][4] rx, ry, sx, sy
-  const int4* conn;     // [K] neighbour across faces 0,1,2 (-1: wall); .w packs neighbour faces
+  const int4* conn;     // [K] neighbour across faces 0,1,2 (kWall, kFarField); .w packs neighbour faces
                         // (bits 0-5), TVB stencil (6-11) and "has a finer neighbour" (12)
   const T* tvbg;        // [K][8] alpha_i, beta_i (i = 0..2)
   T* means;             // [K][4] element means (eta, hu, hv)
@@ -135,10 +139,9 @@ struct Sched {
 struct Phys {
   double g, h0, eps, tvb_M, tvb_nu;
   double hvel;   // velocity u = hu/h only where h > hvel = h0 (1 + 1e-6), else 0
-  double ff_h, ff_hu, ff_hv;   // far-field state of the boundary faces (when farfield)
+  double ff_h, ff_hu, ff_hv;   // far-field state of the open boundary faces (kFarField)
   float eps_f;
   int pp, dry_mode;
-  int farfield;  // 1: boundary faces see the far-field state; 0: reflecting walls
 };
 
 template <typename T>

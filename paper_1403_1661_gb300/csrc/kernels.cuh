@@ -452,7 +452,7 @@ __device__ __forceinline__ void surface_fluxes(const StageParams<T>& p, const T*
           tp.hv += i1n[m] * nv[m];
           tp.b += i1n[m] * nB[m];
         }
-      } else if (p.ph.farfield) {  // far field: the constant state over the continued bed
+      } else if (nb == kFarField) {  // far field: the constant state over the continued bed
         tp = {(T)p.ph.ff_h - hf + tm.b, (T)p.ph.ff_hu, (T)p.ph.ff_hv, tm.b};
       } else {  // reflecting wall: mirror the normal momentum
         const T mn = tm.hu * nx + tm.hv * ny;
@@ -844,7 +844,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_tvb(LimitPar
     const T Bbar_e = (T)p.s.Bbar[e];
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-      if (nbs[f] < 0 && p.ph.farfield) {
+      if (nbs[f] == kFarField) {
         un[f][0] = (T)p.ph.ff_h + Bbar_e;
         un[f][1] = (T)p.ph.ff_hu;
         un[f][2] = (T)p.ph.ff_hv;

@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kBlock) k_split_surface(StageParams<T> p, Spli
         if (nb >= 0) {   // the neighbour's own point NG-1-gq of its face fn
           const T* op = sb.qg + (size_t)((fn * NG + NG - 1 - gq) * 4) * ks + nb;
           tp = {op[0], op[ks], op[2 * ks], op[3 * ks]};
-        } else if (p.ph.farfield) {   // far field over the continued bed
+        } else if (nb == kFarField) {   // far field over the continued bed
           tp = {(T)p.ph.ff_h - hf + tm.b, (T)p.ph.ff_hu, (T)p.ph.ff_hv, tm.b};
         } else {         // reflecting wall: mirror the normal momentum
           const T mn = tm.hu * nx + tm.hv * ny;

@@ -153,8 +153,8 @@ struct swe_solver {
   int64_t launches = 0;
   cudaGraphExec_t graph = nullptr;
   uint64_t sched_version = 0;    // bumped whenever captured launches go stale (levels, order, launch shape)
-  bool farfield = false;         // boundary faces: far-field state ff (true) or reflecting walls
-  double ff[3] = {0.0, 0.0, 0.0};
+  double ff[3] = {0.0, 0.0, 0.0};   // far-field state of the open boundary faces
+  std::vector<uint8_t> open_face;   // K x 3, caller order: 1 = open (far field), 0 = wall
   int graph_launches = 0;
   int64_t graph_dofs = 0;
   swe::KernelCfg cfg_max;   // occupancy limits (set_launch_config caps below these)
@@ -226,7 +226,6 @@ swe::Phys phys_of(const swe_solver* s, int mask) {
   ph.tvb_nu = s->prm.tvb_nu > 0 ? s->prm.tvb_nu : 1.5;
   ph.pp = (mask & SWE_LIM_PP) ? 1 : 0;
   ph.dry_mode = s->prm.dry_mode;
-  ph.farfield = s->farfield ? 1 : 0;
   ph.ff_h = s->ff[0];
   ph.ff_hu = s->ff[1];
   ph.ff_hv = s->ff[2];
@@ -532,7 +531,7 @@ int upload_mesh_t(swe_solver* s) {
     for (int f = 0; f < 3; ++f) {
       const int nb = m.EToE[3 * (size_t)c + f];
       if (nb >= 0 && s->level[nb] < s->level[c]) w |= 1 << 12;   // a finer neighbour reads qmid
-      conn[4 * (size_t)e + f] = nb >= 0 ? s->iperm[nb] : -1;
+      conn[4 * (size_t)e + f] = nb >= 0 ? s->iperm[nb] : (s->open_face[3 * (size_t)c + f] ? swe::kFarField : swe::kWall);
       const int fn = nb >= 0 ? m.EToF[3 * (size_t)c + f] : 0;
       w |= (fn & 3) << (2 * f);
       w |= (jsel[3 * (size_t)c + f] & 3) << (6 + 2 * f);
@@ -1147,6 +1146,7 @@ int swe_solver_create(const swe_mesh* mesh, const swe_params* params, void* dev_
   s->cfg_max = s->cfg;
   // single level until levels are set up
   s->level.assign(s->K, 1);
+  s->open_face.assign((size_t)3 * s->K, 0);
   s->dt_min = 0.0;
   build_order(s.get());
   SWE_CUDA(cudaMemsetAsync(s->ws, 0, s->lay.total, s->stream));
@@ -1594,12 +1594,21 @@ int swe_set_farfield(swe_solver* s, int32_t enable, double h, double hu, double 
   if (!s || (enable != 0 && enable != 1)) return fail(SWE_EINVAL, "bad arguments");
   if (enable && !(std::isfinite(h) && std::isfinite(hu) && std::isfinite(hv) && h >= 0.0))
     return fail(SWE_EINVAL, "far-field state must be finite with h >= 0");
-  s->farfield = enable != 0;
   s->ff[0] = enable ? h : 0.0;
   s->ff[1] = enable ? hu : 0.0;
   s->ff[2] = enable ? hv : 0.0;
+  s->open_face.assign((size_t)3 * s->K, enable ? 1 : 0);
   invalidate_graph(s);
-  return SWE_OK;
+  return upload_mesh(s);
+}
+
+int swe_set_open_faces(swe_solver* s, const uint8_t* open) {
+  if (!s || !open) return fail(SWE_EINVAL, "NULL argument");
+  for (size_t i = 0; i < (size_t)3 * s->K; ++i)
+    if (open[i] > 1) return fail(SWE_EINVAL, "open-face flags must be 0 or 1");
+  s->open_face.assign(open, open + (size_t)3 * s->K);
+  invalidate_graph(s);
+  return upload_mesh(s);
 }
 
 int swe_batch_create(swe_solver* const* solvers, int32_t n, void* stream, swe_batch** out) {

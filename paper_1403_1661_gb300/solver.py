@@ -170,13 +170,17 @@ class Solver:
         nat.check(nat.lib().swe_set_levels(self.handle, nat.iptr(lev), float(dt_min)), "swe_set_levels")
         self.level = lev.copy()
 
-    def set_farfield(self, state=None):
-        """Boundary faces: reflecting walls (state=None) or the far-field (h, hu, hv)."""
+    def set_farfield(self, state=None, open_faces=None):
+        """Boundary faces: reflecting walls (state=None) or open to the far field
+        (h, hu, hv); open_faces (K x 3 bool, caller order) opens only those faces."""
         if state is None:
             nat.check(nat.lib().swe_set_farfield(self.handle, 0, 0.0, 0.0, 0.0), "swe_set_farfield")
-        else:
-            h, hu, hv = (float(v) for v in state)
-            nat.check(nat.lib().swe_set_farfield(self.handle, 1, h, hu, hv), "swe_set_farfield")
+            return
+        h, hu, hv = (float(v) for v in state)
+        nat.check(nat.lib().swe_set_farfield(self.handle, 1, h, hu, hv), "swe_set_farfield")
+        if open_faces is not None:
+            o = np.ascontiguousarray(open_faces, np.uint8).reshape(self.K, 3)
+            nat.check(nat.lib().swe_set_open_faces(self.handle, C.c_void_p(o.ctypes.data)), "swe_set_open_faces")
 
     def regroup(self, level=None):
         """Regroup into new levels without restarting (history kept); level=None

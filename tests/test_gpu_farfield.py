@@ -133,3 +133,40 @@ def test_translating_vortex_converges(N):
     print(f"PARITY translating vortex N={N} errors " + " ".join(f"{e:.3e}" for e in errs)
           + " EOC " + " ".join(f"{v:.2f}" for v in eoc), flush=True)
     assert eoc[-1] >= N + 0.3
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32tc"])
+def test_open_faces_subset(precision):
+    """Open faces on x = 0 and x = 1 only, walls elsewhere (PP + TVB), ten steps,
+    through a regroup-free multirate schedule: against the oracle's per-face choice."""
+    import paper_1403_1661_gb300 as P
+    from oracle.mesh import Mesh
+    scn = _rhs_case(3, precision, limiter_mask=3)
+    vx, vy, E = scn.build_mesh()
+    om = Mesh(vx, vy, E)
+    opn = np.zeros((om.K, 3), bool)
+    for f in range(3):
+        opn[:, f] = (om.EToE[:, f] < 0) & (np.abs(om.nx[:, f]) > 0.5)
+    ff = (1.0, 0.3, 0.0)
+    o2, ref, model, integ = problem.build(scn)
+    mff = SWEModel(om, ref, model.B, scn.g, scn.h0, farfield=ff, farfield_faces=opn)
+    B, h, hu, hv = problem.nodal_inputs(scn, om, ref)
+    integ = MRAB(mff, h, hu, hv, integ.level, integ.dt_min, limiter_mask=scn.limiter_mask, tvb_M=scn.tvb_M)
+    mesh = P.Mesh(vx, vy, E)
+    s = P.Solver(mesh, scn.N, g=scn.g, h0=scn.h0, cfl=scn.cfl, nlevels_max=1, precision=precision,
+                 limiter_mask=scn.limiter_mask, tvb_M=scn.tvb_M, tvb_nu=scn.tvb_nu)
+    s.set_farfield(ff, open_faces=opn)
+    Bd, hd, hud, hvd = P.scenario_inputs(scn, mesh)
+    s.set_bathymetry(Bd)
+    s.set_state(hd, hud, hvd)
+    s.set_levels(integ.level, integ.dt_min)
+    for _ in range(10):
+        integ.substep()
+    s.substep(10)
+    hg, hug, hvg, t = s.get_state()
+    q = integ.q_end
+    hmax = q[0].max()
+    eh = np.abs(hg - q[0]).max() / hmax
+    em = max(np.abs(hug - q[1]).max(), np.abs(hvg - q[2]).max()) / (hmax * np.sqrt(9.81 * hmax))
+    print(f"PARITY open faces subset {precision} eh={eh:.3e} em={em:.3e}", flush=True)
+    assert eh < TOL_STATE[precision] and em < TOL_STATE[precision]
