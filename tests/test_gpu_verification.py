@@ -241,13 +241,19 @@ def _rare_scenario(nx, N=2):
 
 def test_rarefaction_wave_rates():
     """Section 6.4 reports global L2 rates of about 1.5 and rates of 2.2 - 3.0 away from
-    the front and the rarefaction's head (N = 2: 1.5 and 3.0). Bounds here: 1.0 and 2.5
-    over H = 1.25, 0.625, 0.3125 (FP64), exact mass accounting, depth >= the dry depth."""
+    the front and the rarefaction's head (N = 2: 1.5 and 3.0; tests/golden). Bounds here:
+    1.0 and 2.5 over H = 1.25, 0.625, 0.3125 (FP64), exact mass accounting, depth >= the
+    dry depth."""
+    import json
+    import os
+    paper = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+    pr = paper["rarefaction_rates"]
     res = _wetdry_errors(_rare_scenario, [40, 80, 160], _rare_exact, lambda m: (m.cx > 15) & (m.cx < 35),
                          2.0, 10.0, "fp64")
     g, l = _rate([r[0] for r in res]), _rate([r[1] for r in res])
     print("PARITY rarefaction N=2 fp64 global " + " ".join(f"{r[0]:.3e}" for r in res)
-          + " local " + " ".join(f"{r[1]:.3e}" for r in res) + f" rates {g:.2f} {l:.2f}", flush=True)
+          + " local " + " ".join(f"{r[1]:.3e}" for r in res) + f" rates {g:.2f} {l:.2f} (paper: "
+          f"{pr['global'][1]} {pr['local_15_35'][1]})", flush=True)
     assert g >= 1.0 and l >= 2.5
     assert max(r[2] for r in res) < 1e-12
     assert min(r[3] for r in res) >= 1e-5 - 1e-15
