@@ -78,7 +78,8 @@ typedef struct swe_solver swe_solver;
  *   eps      positivity trigger of Algorithm 3 (<= 0: use h0)
  *   tvb_M    TVB constant M; tvb_nu the minmod weight nu (<= 0: 1.5)
  *   cfl      CFL number; the per-element step is cfl/(N+1)^2 * H_k / a_k (Eq. cfl)
- *   N        polynomial order (2..5 in this build)
+ *   N        polynomial order (1..5 in this build; 2..5 for the collocation and
+ *            order-2N schemes)
  *   nlevels_max  number of MRAB levels allowed (>= 1; 1 = single-rate AB3)
  *   precision    SWE_FP64, SWE_FP32 or SWE_FP32_TC
  *   limiter_mask SWE_LIM_PP | SWE_LIM_TVB applied after every update

@@ -4,10 +4,12 @@
 
 namespace swe {
 
+const Launchers<float>* launchers_f32_n1();
 const Launchers<float>* launchers_f32_n2();
 const Launchers<float>* launchers_f32_n3();
 const Launchers<float>* launchers_f32_n4();
 const Launchers<float>* launchers_f32_n5();
+const Launchers<double>* launchers_f64_n1();
 const Launchers<double>* launchers_f64_n2();
 const Launchers<double>* launchers_f64_n3();
 const Launchers<double>* launchers_f64_n4();
@@ -32,6 +34,7 @@ const Launchers<double>* launchers_f64_n37();
 template <>
 const Launchers<float>* launchers_for<float>(int N) {
   switch (N) {
+    case 1: return launchers_f32_n1();
     case 2: return launchers_f32_n2();
     case 3: return launchers_f32_n3();
     case 4: return launchers_f32_n4();
@@ -51,6 +54,7 @@ const Launchers<float>* launchers_for<float>(int N) {
 template <>
 const Launchers<double>* launchers_for<double>(int N) {
   switch (N) {
+    case 1: return launchers_f64_n1();
     case 2: return launchers_f64_n2();
     case 3: return launchers_f64_n3();
     case 4: return launchers_f64_n4();

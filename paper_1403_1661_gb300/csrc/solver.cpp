@@ -95,7 +95,9 @@ Layout make_layout(int K, int N, size_t ts, int op_size, int code) {
 
 int check_params(const swe_params* p) {
   if (!p) return fail(SWE_EINVAL, "params is NULL");
-  if (p->N < 2 || p->N > 5) return fail(SWE_EUNSUPPORTED, "this build supports N = 2..5");
+  if (p->N < 1 || p->N > 5) return fail(SWE_EUNSUPPORTED, "this build supports N = 1..5");
+  if (p->N == 1 && p->scheme != SWE_SCHEME_CUBATURE)
+    return fail(SWE_EUNSUPPORTED, "N = 1 is built for the default scheme only");
   if (p->precision != SWE_FP64 && p->precision != SWE_FP32 && p->precision != SWE_FP32_TC)
     return fail(SWE_EUNSUPPORTED, "precision must be SWE_FP64, SWE_FP32 or SWE_FP32_TC");
   if (!(p->g > 0) || !(p->h0 > 0) || !(p->cfl > 0)) return fail(SWE_EINVAL, "g, h0 and cfl must be > 0");
@@ -460,6 +462,7 @@ swe::RefElem collocation_of(const swe::RefElem& e) {
 void pack_ops(int code, const swe::RefElem& e, std::vector<double>& o, std::vector<uint32_t>& tc) {
   constexpr int C = swe::kColloc, R = swe::kReduced;
   switch (code) {
+    case 1: pack_ops_n<1>(e, o, tc); break;
     case 2: pack_ops_n<2>(e, o, tc); break;
     case 3: pack_ops_n<3>(e, o, tc); break;
     case 4: pack_ops_n<4>(e, o, tc); break;
@@ -478,6 +481,7 @@ void pack_ops(int code, const swe::RefElem& e, std::vector<double>& o, std::vect
 
 int tc_size_of(int N) {
   switch (N) {
+    case 1: return swe::TcLayout<1>::SIZE;
     case 2: return swe::TcLayout<2>::SIZE;
     case 3: return swe::TcLayout<3>::SIZE;
     case 4: return swe::TcLayout<4>::SIZE;

@@ -58,7 +58,7 @@ TOL_R = {"fp64": 1e-11, "fp32": 2e-5, "fp32tc": 2e-4}
 TOL_STATE = {"fp64": 1e-11, "fp32": 2e-5, "fp32tc": 8e-5}
 
 
-@pytest.mark.parametrize("N", [2, 3, 4, 5])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32tc"])
 def test_rhs_matches_oracle(N, precision):
     scn = _rhs_case(N, precision)
@@ -261,3 +261,20 @@ def test_single_element_all_walls(precision):
     _report(f"one element {precision}", eR=e, eh=eh / hmax, em=em / (hmax * np.sqrt(9.81 * hmax)))
     assert e < TOL_R[precision]
     assert eh < TOL_STATE[precision] * hmax and em < TOL_STATE[precision] * hmax * np.sqrt(9.81 * hmax)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32tc"])
+def test_order_one_multirate_beach(precision):
+    """N = 1 (linear elements, the paper's lowest order in Section 6): the graded beach
+    with 4 levels and PP + TVB, two macro steps against the oracle."""
+    scn = sc.tsunami(nx=40, ny=10, N=1, nlevels=4)
+    om, ref, model, integ, s = both(scn, precision)
+    nsub = 2 * 2 ** (integ.L - 1)
+    for _ in range(nsub):
+        integ.substep()
+    s.substep(nsub)
+    eh, em, _ = state_errors(s, integ)
+    hmax = integ.q_end[0].max()
+    _report(f"tsunami N=1 L={integ.L} {precision}", eh=eh / hmax, em=em / (hmax * np.sqrt(9.81 * hmax)))
+    tol = TOL_STATE[precision]
+    assert eh < tol * hmax and em < tol * hmax * np.sqrt(9.81 * hmax)
