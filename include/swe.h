@@ -137,11 +137,13 @@ int swe_mesh_levels(const swe_mesh* mesh, int32_t N, const double* h, const doub
                     const double* hv, double g, double cfl, int32_t nlevels_max,
                     int32_t* level_out, double* dt_min_out);
 
-/* The CFL regroup rule of swe_regroup for given per-element steps (host only):
- * dt (K), the current levels (K, 1-based), the substep count k and dt_min give
- * level_out (K) = the largest l with 2^{l-1} dt_min <= dt_k in 1..nlevels_max,
- * at most old + 1, at most 1 + the power of two in k; margin_out (may be NULL)
- * = min_k dt_k / (2^{l_k - 1} dt_min). */
+/* The CFL regroup rule of swe_regroup (Section 4's regrouping remark, Eq. cfl's
+ * level rule) for given per-element steps, on the host: dt (K), the current levels
+ * (K, 1-based), the substep count k and dt_min give level_out (K) = the largest l
+ * with 2^{l-1} dt_min <= dt_k in 1..nlevels_max, at most old + 1, at most 1 + the
+ * power of two in k; margin_out (may be NULL) = min_k dt_k / (2^{l_k - 1} dt_min).
+ * Host arrays, read or written during the call only. SWE_EINVAL for NULL arrays,
+ * K < 0, k < 0, dt_min <= 0 or nlevels_max outside 1..8. */
 int swe_regroup_rule(const double* dt, const int32_t* level, int32_t K, double dt_min, int64_t k,
                      int32_t nlevels_max, int32_t* level_out, double* margin_out);
 
