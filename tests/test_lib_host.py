@@ -42,7 +42,7 @@ def test_library_exports_every_declared_symbol(lib):
     assert declared == set(lib.SIGNATURES), declared ^ set(lib.SIGNATURES)
 
 
-@pytest.mark.parametrize("N", [2, 3, 4, 5])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
 def test_reference_element_matches_oracle(lib, N):
     import paper_1403_1661_gb300 as P
     Np, Ncub, Ng = P.ref_sizes(N)

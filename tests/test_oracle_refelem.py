@@ -69,6 +69,65 @@ def test_nodes_count_edges_and_symmetry(N):
         assert np.allclose(np.sort(np.round(L * N, 12), axis=0), np.sort(np.round(L * N), axis=0))
 
 
+def _into_triangle(r, s):
+    """Nearest-ish point of the reference triangle (fold across r + s = 0, clamp at -1)."""
+    d = np.maximum(r + s, 0.0) / 2
+    return np.maximum(r - d, -1.0), np.maximum(s - d, -1.0)
+
+
+def _lebesgue_constant(N, alpha, monkeypatch, M=150, keep=8, rounds=3):
+    """max over the triangle of sum_i |l_i| for the Warp & Blend nodes with blend
+    parameter alpha: a lattice of spacing 2/M (containing the centroid), then the
+    `keep` largest lattice values refined by three nested 21x21 local searches."""
+    table = list(R._ALPHA_OPT)
+    table[N - 1] = alpha
+    monkeypatch.setattr(R, "_ALPHA_OPT", table)
+    rn, sn = R.warp_blend_nodes(N)
+    Vi = np.linalg.inv(R.vandermonde(N, rn, sn))
+    leb = lambda r, s: np.abs(R.vandermonde(N, r, s) @ Vi).sum(axis=1)
+    i, j = np.meshgrid(np.arange(M + 1), np.arange(M + 1), indexing="ij")
+    m = i + j <= M
+    r, s = -1 + 2 * j[m] / M, -1 + 2 * i[m] / M
+    v = leb(r, s)
+    best = v.max()
+    d = np.linspace(-1.0, 1.0, 21)
+    for idx in np.argsort(v)[-keep:]:
+        cr, cs, h = r[idx], s[idx], 2.0 / M
+        for _ in range(rounds):
+            pr, ps = _into_triangle(cr + h * d[:, None] + 0 * d[None, :], cs + h * d[None, :] + 0 * d[:, None])
+            pv = leb(pr.ravel(), ps.ravel())
+            k = int(np.argmax(pv))
+            best = max(best, pv[k])
+            cr, cs, h = pr.ravel()[k], ps.ravel()[k], h / 10
+    return best
+
+
+@pytest.mark.parametrize("N", [5, 6, 7])
+def test_blend_parameter_minimises_lebesgue_constant(N, monkeypatch):
+    """The blend parameters alpha_opt(N) were chosen (Warburton 2006) to minimise
+    the Lebesgue constant of the node set. For N = 5..7 the tabulated value is that
+    minimiser to within 0.002: a wrong digit in the first three decimals fails."""
+    a0 = R._ALPHA_OPT[N - 1]
+    lam0 = _lebesgue_constant(N, a0, monkeypatch)
+    for da in (-0.002, 0.002):
+        assert _lebesgue_constant(N, a0 + da, monkeypatch) > lam0 + 1e-5, da
+    # and it is the global minimum over a coarse scan of alpha in [0, 2]
+    scan = [_lebesgue_constant(N, a, monkeypatch) for a in np.arange(0.0, 2.01, 0.25)]
+    assert lam0 < min(scan)
+
+
+def test_blend_parameter_n4_on_the_flat_lebesgue_curve(monkeypatch):
+    """For N = 4 the Lebesgue constant hardly depends on alpha (its maximum lies
+    next to the alpha-independent edge nodes): the tabulated 0.1001 is within 1e-4
+    (relative) of the minimum over alpha in [0, 2], which a misplaced digit
+    (1.001, 0.01 is fine) breaks by far (1.001 gives +0.5 %)."""
+    a0 = R._ALPHA_OPT[3]
+    lam0 = _lebesgue_constant(4, a0, monkeypatch)
+    scan = [_lebesgue_constant(4, a, monkeypatch) for a in np.arange(0.0, 2.01, 0.1)]
+    assert lam0 <= min(scan) * (1 + 1e-4)
+    assert _lebesgue_constant(4, 1.001, monkeypatch) > min(scan) * (1 + 2e-3)
+
+
 @pytest.mark.parametrize("N", ORDERS)
 def test_basis_orthonormal_bruteforce(N):
     r, s, w = duffy_rule(N + 3)
