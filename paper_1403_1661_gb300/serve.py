@@ -12,6 +12,16 @@ ones. Latency is completion time minus arrival time.
 
 Solves never interact (no shared buffers, deterministic kernels), so a result
 does not depend on what else is running.
+
+Failures stay with their request: a request whose preparation fails (an invalid
+mesh, say) or whose workspace exceeds the whole budget is rejected, one whose
+solver cannot be created fails, and a running solve whose state turned
+non-finite (the device flag that swe_stats reports, checked every few rounds
+while the solve is idle and again before its result is returned) is stopped and
+fails; its memory is released and the others carry on. A request can be
+cancelled from any thread (Server.cancel) or at a scripted time
+(Request.cancel_at): one that has not started is dropped, a running one is
+retired at its next idle point without a result.
 """
 from __future__ import annotations
 
@@ -19,6 +29,7 @@ import collections
 import concurrent.futures as cf
 import dataclasses
 import math
+import threading
 import time
 
 import numpy as np
@@ -35,6 +46,9 @@ class Request:
     dof_updates: int = 0
     bytes: int = 0
     result: object = None
+    cancel_at: float | None = None   # cancel at this many seconds after the start (scripted clients)
+    status: str = "waiting"          # then "done", "rejected", "failed" or "cancelled"
+    error: str | None = None
 
 
 class GpuFactory:
@@ -97,16 +111,23 @@ class _GpuJob:
     def idle(self):
         return (not self.pending) or self.event.query()
 
+    def healthy(self):
+        """False once the device has flagged a non-finite value (call when idle)."""
+        return not self.s.stats()["nonfinite"]
+
     def finish(self):
         st = self.s.stats()
         out = self.s.get_state() if self.factory.keep_state else None
         self.s.close()
         return out, st["dof_updates"]
 
+    def abort(self):
+        self.s.close()
+
 
 class Server:
     def __init__(self, budget_bytes=150e9, max_slots=64, macro_per_round=2, prep_workers=4, factory=None,
-                 clock=time.perf_counter, sleep=time.sleep):
+                 clock=time.perf_counter, sleep=time.sleep, health_every=16):
         self.budget = float(budget_bytes)
         self.max_slots = int(max_slots)
         self.macro_per_round = int(macro_per_round)
@@ -114,64 +135,120 @@ class Server:
         self.factory = factory if factory is not None else GpuFactory()
         self.clock = clock
         self.sleep = sleep
+        self.health_every = int(health_every)    # rounds of a solve between non-finite checks
+        self._cancel = set()
+        self._lock = threading.Lock()
+
+    def cancel(self, rid):
+        """Cancel request ``rid`` (callable from any thread, before or during run)."""
+        with self._lock:
+            self._cancel.add(rid)
+
+    def _cancelled(self, r, now):
+        if r.cancel_at is not None and now >= r.cancel_at:
+            return True
+        with self._lock:
+            return r.rid in self._cancel
 
     def run(self, requests):
-        """Serve the requests (sorted by arrival); returns a summary dict."""
+        """Serve the requests (sorted by arrival); returns a summary dict. Latencies
+        and throughput count the completed requests; the others are listed with
+        their status and error under "ended"."""
         reqs = sorted(requests, key=lambda r: r.arrival)
         pending = collections.deque(reqs)
         preparing = collections.deque()          # (req, future) in arrival order
         ready = collections.deque()               # (req, prepared), FIFO
-        running = []                              # [req, job, remaining_macro]
+        running = []                              # [req, job, remaining_macro, rounds]
         used = 0.0
         peak_used = 0.0
         peak_running = 0
         done = []
+        ended = []
         t0 = self.clock()
+
+        def end(r, status, error=None):
+            r.status, r.error = status, error
+            r.finished = self.clock() - t0
+            ended.append(r)
+
         with cf.ThreadPoolExecutor(max_workers=self.prep_workers) as pool:
             while pending or preparing or ready or running:
                 now = self.clock() - t0
                 progressed = False
                 while pending and pending[0].arrival <= now:
                     r = pending.popleft()
-                    preparing.append((r, pool.submit(self.factory.prepare, r)))
+                    if self._cancelled(r, now):
+                        end(r, "cancelled")
+                    else:
+                        preparing.append((r, pool.submit(self.factory.prepare, r)))
                     progressed = True
                 while preparing and preparing[0][1].done():
                     r, fut = preparing.popleft()
-                    prep = fut.result()
+                    progressed = True
+                    try:
+                        prep = fut.result()
+                    except Exception as ex:          # e.g. an invalid mesh
+                        end(r, "rejected", f"preparation failed: {ex}")
+                        continue
                     r.bytes = self.factory.bytes(prep)
                     if r.bytes > self.budget:
-                        raise MemoryError(f"request {r.rid} needs {r.bytes} B, over the whole budget")
+                        end(r, "rejected", f"needs {r.bytes} B, over the whole budget of {self.budget:.0f} B")
+                        continue
                     ready.append((r, prep))
+                if any(self._cancelled(r, now) for r, _ in ready):
+                    keep = collections.deque()
+                    for r, prep in ready:
+                        if self._cancelled(r, now):
+                            end(r, "cancelled")
+                        else:
+                            keep.append((r, prep))
+                    ready = keep
                     progressed = True
                 # admission: first come first served, by budget and slots
                 while ready and len(running) < self.max_slots and used + ready[0][0].bytes <= self.budget:
                     r, prep = ready.popleft()
-                    job = self.factory.start(r, prep)
+                    progressed = True
+                    try:
+                        job = self.factory.start(r, prep)
+                    except Exception as ex:          # e.g. the device refused the workspace
+                        end(r, "failed", f"start failed: {ex}")
+                        continue
                     r.admitted = self.clock() - t0
                     used += r.bytes
                     peak_used = max(peak_used, used)
-                    running.append([r, job, int(math.ceil(r.substeps / job.macro_period))])
-                    progressed = True
+                    running.append([r, job, int(math.ceil(r.substeps / job.macro_period)), 0])
                 peak_running = max(peak_running, len(running))
-                # issue work and retire finished solves
+                # issue work and retire finished, failed or cancelled solves
                 still = []
                 for item in running:
-                    r, job, rem = item
+                    r, job, rem, rounds = item
                     if not job.idle():
                         still.append(item)
+                        continue
+                    progressed = True
+                    if self._cancelled(r, self.clock() - t0):
+                        job.abort()
+                        used -= r.bytes
+                        end(r, "cancelled")
+                        continue
+                    check = rem == 0 or (self.health_every > 0 and rounds > 0 and rounds % self.health_every == 0)
+                    if check and not getattr(job, "healthy", lambda: True)():
+                        job.abort()
+                        used -= r.bytes
+                        end(r, "failed", "non-finite state")
                         continue
                     if rem > 0:
                         n = min(rem, self.macro_per_round)
                         job.step(n)
                         item[2] = rem - n
+                        item[3] = rounds + 1
                         still.append(item)
-                        progressed = True
                     else:
                         r.result, r.dof_updates = job.finish()
+                        r.status = "done"
                         r.finished = self.clock() - t0
                         used -= r.bytes
                         done.append(r)
-                        progressed = True
                 running = still
                 if not progressed:
                     nxt = pending[0].arrival - (self.clock() - t0) if pending else 0.0
@@ -179,10 +256,13 @@ class Server:
         wall = self.clock() - t0
         lat = np.array([r.finished - r.arrival for r in done]) if done else np.zeros(1)
         dofs = sum(r.dof_updates for r in done)
+        count = collections.Counter(r.status for r in ended)
         return {"requests": len(done), "wall_s": wall, "p50_s": float(np.percentile(lat, 50)),
                 "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
                 "aggregate_dof_per_s": dofs / wall if wall > 0 else 0.0, "dof_updates": int(dofs),
-                "peak_running": peak_running, "peak_bytes": peak_used, "done": done}
+                "peak_running": peak_running, "peak_bytes": peak_used, "done": done,
+                "rejected": count["rejected"], "failed": count["failed"], "cancelled": count["cancelled"],
+                "ended": ended}
 
 
 def requests_from_stream(stream, substeps=500):

@@ -1,9 +1,9 @@
 """Host-side tests of the continuous-batching server with a fake solver factory:
 budget and slot admission, first-come-first-served order, overlap, latency
-accounting (no GPU)."""
+accounting, and failures that stay with their request: rejection, a solve whose
+state turns non-finite, a failed start, cancellation (no GPU)."""
 import math
-
-import pytest
+import threading
 
 from paper_1403_1661_gb300.serve import Request, Server
 
@@ -20,12 +20,15 @@ class FakeClock:
 
 
 class FakeJob:
-    def __init__(self, clock, req, rounds_per_step):
+    def __init__(self, clock, req, rounds_per_step, bad_after=None):
         self.clock = clock
         self.macro_period = 4
         self.busy_until = 0.0
         self.steps = 0
         self.dt = rounds_per_step
+        self.bad_after = bad_after     # macro steps after which the state is non-finite
+        self.aborted = False
+        self.health_checks = 0
 
     def step(self, n):
         self.steps += n
@@ -35,37 +38,63 @@ class FakeJob:
         self.clock.t += 1e-4        # the host loop itself takes time
         return self.clock() >= self.busy_until
 
+    def healthy(self):
+        self.health_checks += 1
+        return self.bad_after is None or self.steps < self.bad_after
+
     def finish(self):
         return None, 100 * self.steps
 
+    def abort(self):
+        self.aborted = True
+
 
 class FakeFactory:
-    def __init__(self, clock, sizes, step_time):
+    def __init__(self, clock, sizes, step_time, bad_prepare=(), bad_start=(), bad_after=None):
         self.clock = clock
         self.sizes = sizes
         self.step_time = step_time
         self.started = []
+        self.jobs = {}
+        self.bad_prepare = set(bad_prepare)
+        self.bad_start = set(bad_start)
+        self.bad_after = bad_after or {}
 
     def prepare(self, req):
+        if req.rid in self.bad_prepare:
+            raise ValueError("mesh is not conforming")
         return {"bytes": self.sizes[req.rid]}
 
     def bytes(self, prep):
         return prep["bytes"]
 
     def start(self, req, prep):
+        if req.rid in self.bad_start:
+            raise RuntimeError("workspace refused")
         self.started.append(req.rid)
-        return FakeJob(self.clock, req, self.step_time)
+        job = FakeJob(self.clock, req, self.step_time, self.bad_after.get(req.rid))
+        self.jobs[req.rid] = job
+        return job
 
 
-def _run(sizes, arrivals, budget, slots, substeps=40, step_time=10.0):
+def _run(sizes, arrivals, budget, slots, substeps=40, step_time=10.0, cancel_at=None, server_cancel=(),
+         health_every=2, **faults):
     # fake device time per macro step is large against the host loop's own time,
     # so admission order does not depend on how fast the preparation threads run
     clock = FakeClock()
-    fac = FakeFactory(clock, sizes, step_time)
+    fac = FakeFactory(clock, sizes, step_time, **faults)
     srv = Server(budget_bytes=budget, max_slots=slots, macro_per_round=2, prep_workers=1, factory=fac,
-                 clock=clock, sleep=clock.sleep)
-    reqs = [Request(rid=i, arrival=a, scenario=None, substeps=substeps) for i, a in enumerate(arrivals)]
+                 clock=clock, sleep=clock.sleep, health_every=health_every)
+    cancel_at = cancel_at or {}
+    reqs = [Request(rid=i, arrival=a, scenario=None, substeps=substeps, cancel_at=cancel_at.get(i))
+            for i, a in enumerate(arrivals)]
+    for rid in server_cancel:
+        srv.cancel(rid)
     return srv, fac, srv.run(reqs)
+
+
+def _status(out):
+    return {r.rid: r.status for r in out["done"] + out["ended"]}
 
 
 def test_all_requests_finish_fifo_within_budget():
@@ -90,6 +119,62 @@ def test_work_overlaps_when_memory_allows():
     assert wide["wall_s"] < 0.5 * narrow["wall_s"]
 
 
-def test_request_over_budget_is_rejected():
-    with pytest.raises(MemoryError):
-        _run([10, 500], [0.0, 0.0], budget=100, slots=2)
+def test_request_over_budget_is_rejected_and_the_rest_are_served():
+    _, fac, out = _run([10, 500, 20], [0.0, 0.0, 0.0], budget=100, slots=2)
+    st = _status(out)
+    assert st == {0: "done", 1: "rejected", 2: "done"}
+    assert 1 not in fac.started and "over the whole budget" in out["ended"][0].error
+    assert out["requests"] == 2 and out["rejected"] == 1
+
+
+def test_failed_preparation_or_start_stays_with_its_request():
+    _, fac, out = _run([10, 10, 10, 10], [0.0] * 4, budget=100, slots=4, bad_prepare={1}, bad_start={2})
+    st = _status(out)
+    assert st == {0: "done", 1: "rejected", 2: "failed", 3: "done"}
+    errs = {r.rid: r.error for r in out["ended"]}
+    assert "not conforming" in errs[1] and "workspace refused" in errs[2]
+    assert out["failed"] == 1 and out["rejected"] == 1
+
+
+def test_nonfinite_solve_is_stopped_and_its_memory_admits_the_next():
+    # room for one solve at a time: request 0 goes non-finite after 4 macro steps,
+    # is stopped at the next check (every 2 rounds), and request 1 then runs
+    _, fac, out = _run([60, 60], [0.0, 0.0], budget=100, slots=2, bad_after={0: 4})
+    st = _status(out)
+    assert st == {0: "failed", 1: "done"}
+    j0 = fac.jobs[0]
+    assert j0.aborted and j0.steps < 10 and out["ended"][0].error == "non-finite state"
+    assert fac.jobs[1].steps == 10 and not fac.jobs[1].aborted
+    assert out["peak_bytes"] <= 100
+    assert out["requests"] == 1 and out["dof_updates"] == 1000
+
+
+def test_health_checked_before_a_result_is_returned():
+    # non-finite only after the last macro step: caught by the check at retirement
+    _, fac, out = _run([10], [0.0], budget=100, slots=1, bad_after={0: 10}, health_every=0)
+    assert _status(out) == {0: "failed"} and fac.jobs[0].steps == 10
+
+
+def test_cancellation_before_start_and_while_running():
+    # request 0 runs alone (budget) and is cancelled mid-run; request 1 waits
+    # behind it and is cancelled before it could start; request 2 is cancelled
+    # through Server.cancel before the run; request 3 is served
+    _, fac, out = _run([60, 60, 10, 10], [0.0, 0.0, 0.0, 0.0], budget=100, slots=4,
+                       cancel_at={0: 25.0, 1: 5.0}, server_cancel=(2,))
+    st = _status(out)
+    assert st == {0: "cancelled", 1: "cancelled", 2: "cancelled", 3: "done"}
+    assert 1 not in fac.started and 2 not in fac.started
+    assert fac.jobs[0].aborted and 0 < fac.jobs[0].steps < 10
+    assert out["cancelled"] == 3 and out["requests"] == 1
+
+
+def test_cancel_from_another_thread():
+    clock = FakeClock()
+    fac = FakeFactory(clock, [10, 10], 10.0)
+    srv = Server(budget_bytes=100, max_slots=2, macro_per_round=2, prep_workers=1, factory=fac,
+                 clock=clock, sleep=clock.sleep)
+    th = threading.Thread(target=srv.cancel, args=(1,))
+    th.start()
+    th.join()
+    out = srv.run([Request(rid=i, arrival=0.0, scenario=None, substeps=40) for i in range(2)])
+    assert _status(out) == {0: "done", 1: "cancelled"}
