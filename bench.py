@@ -562,6 +562,7 @@ def run_served(args):
     return {"requests": out["requests"], "p50_s": out["p50_s"], "p99_s": out["p99_s"], "mean_s": out["mean_s"],
             "aggregate_dof_per_s": out["aggregate_dof_per_s"], "wall_s": out["wall_s"],
             "peak_running": out["peak_running"], "peak_gb": out["peak_bytes"] / 1e9,
+            "rejected": out["rejected"], "failed": out["failed"],
             "arrivals": f"Poisson 50/s for {args.serve_seconds:.0f} s, K log-uniform 2k-1M, N in {{2,3,4}}, "
                         f"500 MRAB substeps each, HBM budget 150 GB"}
 

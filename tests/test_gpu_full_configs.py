@@ -1,0 +1,149 @@
+"""GPU parity on benchmark configurations at their full sizes and full run
+lengths, against FP64 oracle results stored in tests/golden/full_config_oracle.json
+(written by tests/golden/make_full_config_golden.py, which calls only the oracle;
+the oracle needs about 10 minutes for each dam-break run).
+
+* Wet/dry dam break, 20,480 triangles, N = 3, positivity-preserving + TVB
+  (M = 0) limiting every stage, 2000 AB3 steps, on every tier. The run is
+  one-dimensional up to the triangulation: the 320 column averages of the element
+  means and the means of a seeded sample of elements are compared where the
+  oracle's wet/dry state is the same two columns to either side (a front moves by
+  decisions taken in different precisions), and an L1 bound holds over all
+  columns. Minmod and wet/dry decisions carry rounding-level differences through
+  the run, so the FP64 tier is held to 10 times the oracle's own response to a
+  one-ulp change of its initial depth (stored beside its result); the FP32 tiers
+  to their smooth-case state bounds times 10. Depth stays non-negative after
+  every step. Mass: the FP64 books close (mass = initial mass + tallied dry-reset
+  injection) to round-off; FP32 storage rounds every nodal value up to three
+  times a step (commit, positivity rescale, TVB replacement), each by at most
+  2^-24 relative, which bounds the FP32 tiers' drift by
+  3 T 2^-24 sum_k area_k sum_j |w_j| |h_kj| (w the element-mean weights).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from workloads import scenarios as sc
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "full_config_oracle.json")
+
+# dam break, FP32 tiers: state bounds away from the fronts (x 10 of the smooth-case
+# bounds), L1 over all columns relative to sum |h|
+DAM_TOL32 = {"fp32": (2e-4, 2e-4 * np.sqrt(9.81), 1e-4),
+             "fp32tc": (8e-4, 8e-4 * np.sqrt(9.81), 4e-4)}
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def golden():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_1661_gb300 import build
+    build.build()
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def _geometry(scn):
+    vx, vy, E = scn.build_mesh()
+    x, y = vx[E], vy[E]
+    area = 0.5 * np.abs((x[:, 1] - x[:, 0]) * (y[:, 2] - y[:, 0]) - (x[:, 2] - x[:, 0]) * (y[:, 1] - y[:, 0]))
+    return (vx, vy, E), x.mean(axis=1), y.mean(axis=1), area
+
+
+def _mean_weights(N):
+    from oracle.refelem import RefElement
+    return RefElement(N).mean_w
+
+
+def _away_from_fronts(oh):
+    """Columns two or more away from every wet/dry change of the columns ``oh``."""
+    wet = oh > 1e-3
+    fronts = np.nonzero(wet[1:] != wet[:-1])[0]
+    away = np.ones(oh.size, bool)
+    for c in fronts:
+        away[max(0, c - 2):c + 4] = False
+    return away, fronts
+
+
+def _dam_errors(g, hb, hub, hvb, col, away):
+    """Max differences of column averages and sampled element means, and L1 over
+    columns, of element means (hb, hub, hvb) against the oracle summary ``g``."""
+    area = g["_area"]
+    wsum = np.bincount(col, weights=area, minlength=320)
+    c = [np.bincount(col, weights=area * v, minlength=320) / wsum for v in (hb, hub, hvb)]
+    o = [np.asarray(g["columns"][k]) for k in ("h", "hu", "hv")]
+    e_h = np.abs(c[0] - o[0])[away].max()
+    e_m = max(np.abs(c[1] - o[1])[away].max(), np.abs(c[2] - o[2])[away].max())
+    l1 = np.abs(c[0] - o[0]).sum() / np.abs(o[0]).sum()
+    el = np.asarray(g["sample"]["elements"])
+    keep = away[col[el]] & ((hb[el] > 1e-3) == (np.asarray(g["sample"]["h"]) > 1e-3))
+    s_h = np.abs(hb[el] - g["sample"]["h"])[keep].max()
+    s_m = max(np.abs(hub[el] - g["sample"]["hu"])[keep].max(), np.abs(hvb[el] - g["sample"]["hv"])[keep].max())
+    return e_h, e_m, l1, s_h, s_m, keep
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32tc"])
+def test_dam_break_full_size_2000_steps(golden, precision):
+    import paper_1403_1661_gb300 as P
+    g = golden["dam_break"]
+    scn = sc.dam_break()
+    arrays, cx, cy, area = _geometry(scn)
+    K = arrays[2].shape[0]
+    assert K == g["K"] == 20480
+    s = P.solver_from_scenario(scn, precision=precision, levels=np.ones(K, np.int32), dt_min=g["dt"],
+                               mesh_arrays=arrays)
+    st0 = s.stats()
+    hmin = st0["hmin"]
+    for _ in range(g["steps"]):
+        s.substep(1)
+        hmin = min(hmin, s.stats()["hmin"])
+    st = s.stats()
+    h, hu, hv, t = s.get_state()
+    assert abs(t - g["time"]) <= 1e-12 * g["time"]
+    assert not st["nonfinite"] and np.isfinite(h).all()
+
+    w = _mean_weights(scn.N)
+    col = np.floor(cx / g["columns"]["dx"]).astype(np.int64)
+    away, fronts = _away_from_fronts(np.asarray(g["columns"]["h"]))
+    g = dict(g, _area=area)
+    e_h, e_m, l1, s_h, s_m, keep = _dam_errors(g, h @ w, hu @ w, hv @ w, col, away)
+    mass_err = abs(st["mass"] - g["mass"]) / g["mass"]
+    budget = abs(st["mass"] - (st0["mass"] + st["injected_mass"] - st0["injected_mass"])) / g["mass"]
+
+    # the oracle's own response to a one-ulp change of its initial depth
+    u = golden["dam_break_ulp"]
+    ub = np.asarray(u["sample"]["h"]), np.asarray(u["sample"]["hu"]), np.asarray(u["sample"]["hv"])
+    uc = [np.asarray(u["columns"][k]) for k in ("h", "hu", "hv")]
+    oc = [np.asarray(g["columns"][k]) for k in ("h", "hu", "hv")]
+    os_ = [np.asarray(g["sample"][k]) for k in ("h", "hu", "hv")]
+    r_h = max(np.abs(uc[0] - oc[0])[away].max(), np.abs(ub[0] - os_[0])[keep].max())
+    r_m = max(np.abs(uc[1] - oc[1])[away].max(), np.abs(uc[2] - oc[2])[away].max(),
+              np.abs(ub[1] - os_[1])[keep].max(), np.abs(ub[2] - os_[2])[keep].max())
+    r_l1 = np.abs(uc[0] - oc[0]).sum() / np.abs(oc[0]).sum()
+    r_mass = abs(u["mass"] - g["mass"]) / g["mass"]
+    if precision == "fp64":
+        tol_h, tol_m, tol_l1 = (max(1e-9, 10 * r) for r in (r_h, r_m, r_l1))
+        tol_budget = 1e-11
+    else:
+        tol_h, tol_m, tol_l1 = DAM_TOL32[precision]
+        tol_budget = 3 * g["steps"] * U32 * (area @ (np.abs(h) @ np.abs(w))) / g["mass"]
+    tol_mass = tol_budget + 10 * r_mass
+    front_x = (fronts + 1) * g["columns"]["dx"]
+    print(f"PARITY dam break full size {precision} 2000 steps: columns eh={e_h:.3e} em={e_m:.3e} "
+          f"l1={l1:.3e}; sample eh={s_h:.3e} em={s_m:.3e} ({keep.sum()} of {keep.size}); mass {mass_err:.3e}, "
+          f"budget {budget:.3e}; hmin over steps {hmin:.3e} (oracle {g['hmin_over_steps']:.3e}); "
+          f"fronts at x = {front_x.tolist()}; bounds h {tol_h:.3e} m {tol_m:.3e} l1 {tol_l1:.3e} "
+          f"mass {tol_mass:.3e} budget {tol_budget:.3e}; oracle one-ulp response h {r_h:.3e} m {r_m:.3e} "
+          f"l1 {r_l1:.3e} mass {r_mass:.3e}", flush=True)
+    assert hmin >= 0.0
+    assert keep.sum() >= 0.8 * keep.size
+    assert e_h < tol_h and s_h < tol_h
+    assert e_m < tol_m and s_m < tol_m
+    assert l1 < tol_l1
+    assert budget < tol_budget and mass_err < tol_mass
