@@ -13,6 +13,9 @@ scenarios do not exchange data); value sums all ranks' DOF-updates over the max 
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload (there is no reference implementation to install: the paper ships no code).
+
+--oracle-configs times the oracle (no GPU) on bounded samples of every
+configuration, with all host threads and with one, and prints one JSON line.
 """
 from __future__ import annotations
 
@@ -54,6 +57,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-scenarios", type=int, default=64)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--oracle-configs", action="store_true")
+    ap.add_argument("--oracle-configs-child", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -567,8 +572,66 @@ def run_served(args):
                         f"500 MRAB substeps each, HBM budget 150 GB"}
 
 
+def _oracle_rate(scn, substeps):
+    """DOF-updates/s of the oracle over ``substeps`` finest substeps of ``scn``
+    (set-up not timed)."""
+    from oracle import problem
+    om, ref, model, integ = problem.build(scn)
+    d0, t = integ.dof_updates, time.perf_counter()
+    for _ in range(substeps):
+        integ.substep()
+    dt = time.perf_counter() - t
+    return (integ.dof_updates - d0) / dt, dt, om.K
+
+
+def oracle_configs_child():
+    """One line of oracle rates on bounded samples of configurations 1-4."""
+    import numpy as np
+    from workloads import scenarios as sc
+    out = {}
+    v, dt, K = _oracle_rate(sc.hump_square(), 100)
+    out["1_hump_512_N2"] = {"value": v, "seconds": dt, "sample": f"full run: {K} triangles, 100 AB3 steps"}
+    v, dt, K = _oracle_rate(sc.dam_break(), 20)
+    out["2_dam_break_20480_N3"] = {"value": v, "seconds": dt,
+                                   "sample": f"{K} triangles, first 20 of 2000 steps (PP + TVB)"}
+    scn = sc.tsunami(nx=400, ny=100)
+    v, dt, K = _oracle_rate(scn, 8)
+    out["3_tsunami_N4_L4"] = {"value": v, "seconds": dt,
+                              "sample": f"same beach at 400x100x2 = {K} triangles, one macro step (8 substeps)"}
+    ens = sc.ensemble()
+    pick = np.random.Generator(np.random.PCG64(9)).choice(len(ens), size=8, replace=False)
+    dofs, secs, ks = 0.0, 0.0, []
+    for i in sorted(pick):
+        v, dt, K = _oracle_rate(ens[i], 1)
+        dofs, secs = dofs + v * dt, secs + dt
+        ks.append(f"{K}/N{ens[i].N}")
+    out["4_ensemble"] = {"value": dofs / secs, "seconds": secs,
+                         "sample": "8 seeded scenarios of the 64, first finest substep each (all levels active): "
+                                   + ", ".join(ks)}
+    print(json.dumps(out), flush=True)
+
+
+def oracle_configs():
+    """The oracle on every configuration, all host threads and one thread (a fresh
+    interpreter with the BLAS/OpenMP thread counts set to 1)."""
+    cores, model = cpu_info()
+    line = {"kind": "oracle (FP64 numpy)", "unit": UNIT, "cores": cores, "cpu": model}
+    one = {k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for name, extra in (("all_threads", {}), ("one_thread", one)):
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-configs-child"],
+                           env=dict(os.environ, **extra), capture_output=True, text=True, check=True)
+        line[name] = json.loads(r.stdout.strip().splitlines()[-1])
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.oracle_configs_child:
+        oracle_configs_child()
+        return
+    if args.oracle_configs:
+        oracle_configs()
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
