@@ -105,6 +105,26 @@ def test_levels_bit_exact(lib):
     assert len(np.unique(lev)) >= 3
 
 
+def test_levels_of_the_full_benchmark_mesh_equal_the_oracle(lib):
+    """The level rule on the 500,000-triangle beach, evaluated at the library's own
+    nodes, against the oracle's levels stored with its 200-substep run (SHA-256 of
+    the per-element levels, counts, dt_min)."""
+    import hashlib
+    import json
+    import paper_1403_1661_gb300 as P
+    from paper_1403_1661_gb300.solver import scenario_inputs
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "full_config_oracle.json")))["tsunami"]
+    scn = sc.tsunami()
+    vx, vy, E = scn.build_mesh()
+    m = P.Mesh(vx, vy, E)
+    B, h, hu, hv = scenario_inputs(scn, m)
+    lev, dtmin = m.levels(scn.N, h, hu, hv, scn.g, scn.cfl, scn.nlevels)
+    lev = np.asarray(lev, np.int8)
+    assert np.bincount(lev, minlength=5)[1:].tolist() == g["level_counts"]
+    assert hashlib.sha256(lev.tobytes()).hexdigest() == g["level_sha256"]
+    assert abs(dtmin - g["dt_min"]) <= 1e-15 * g["dt_min"]
+
+
 def test_bad_meshes_are_rejected(lib):
     import paper_1403_1661_gb300 as P
     vx = np.array([0.0, 1.0, 0.0, 1.0, 0.5])
