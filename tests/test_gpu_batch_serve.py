@@ -1,6 +1,8 @@
 """Batched and served forms on the GPU: a scenario's result is the same alone, in
 a batch graph, and in the server's mix (bit-identical: no cross-scenario
 interaction, deterministic kernels)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -62,8 +64,13 @@ def test_served_results_equal_alone():
 
 def test_autotuner_and_launch_config_do_not_change_results():
     import paper_1403_1661_gb300 as P
+    from paper_1403_1661_gb300 import batch
+    before = open(batch.CACHE).read() if os.path.exists(batch.CACHE) else None
     best = P.tune(3, "fp32tc", candidates=(1, 0), reps=1, force=True)
     assert best in (1, 0)
+    # a narrower search leaves the cached full-search results alone
+    after = open(batch.CACHE).read() if os.path.exists(batch.CACHE) else None
+    assert after == before
     scn = sc.tsunami(nx=40, ny=10, N=3, nlevels=4)
     a = P.solver_from_scenario(scn, precision="fp32tc")
     b = P.solver_from_scenario(scn, precision="fp32tc")
@@ -72,3 +79,35 @@ def test_autotuner_and_launch_config_do_not_change_results():
     b.step(2)
     for u, v in zip(a.get_state()[:3], b.get_state()[:3]):
         assert np.array_equal(u, v)
+
+
+def test_full_ensemble_batch_equals_alone_on_a_sample():
+    """The batched ensemble at its full size, built as the benchmark builds it (64
+    sloped-beach scenarios of 5k-200k triangles, N in {3, 4, 5}, autotuned launch
+    shapes, one graph launch per macro step of all of them): after three macro
+    steps, eight seeded scenarios equal the same scenarios run alone, bit for bit."""
+    import paper_1403_1661_gb300 as P
+    scns = sc.ensemble()
+    assert len(scns) == 64
+    tuned = {N: P.tune(N, "fp32tc") for N in sorted({s.N for s in scns})}
+    solvers = []
+    for s in scns:
+        so = P.solver_from_scenario(s, precision="fp32tc")
+        so.set_launch_config(tuned[s.N])
+        solvers.append(so)
+    b = P.Batch(solvers)
+    b.step(3)
+    pick = sorted(np.random.Generator(np.random.PCG64(9)).choice(len(scns), size=8, replace=False))
+    for i in pick:
+        a = P.solver_from_scenario(scns[i], precision="fp32tc")
+        a.set_launch_config(tuned[scns[i].N])
+        a.step(3)
+        xa, xb = a.get_state(), solvers[i].get_state()
+        assert np.isfinite(xb[0]).all() and xa[3] == xb[3]
+        for u, v in zip(xa[:3], xb[:3]):
+            assert np.array_equal(u, v)
+        assert a.stats()["dof_updates"] == solvers[i].stats()["dof_updates"]
+        a.close()
+    b.close()
+    for so in solvers:
+        so.close()

@@ -1,7 +1,7 @@
 """GPU parity on benchmark configurations at their full sizes and full run
 lengths, against FP64 oracle results stored in tests/golden/full_config_oracle.json
 (written by tests/golden/make_full_config_golden.py, which calls only the oracle;
-the oracle needs about 10 minutes for each dam-break run).
+the oracle needs about 10 minutes for each dam-break run and 47 for the tsunami).
 
 * Wet/dry dam break, 20,480 triangles, N = 3, positivity-preserving + TVB
   (M = 0) limiting every stage, 2000 AB3 steps, on every tier. The run is
@@ -18,7 +18,16 @@ the oracle needs about 10 minutes for each dam-break run).
   times a step (commit, positivity rescale, TVB replacement), each by at most
   2^-24 relative, which bounds the FP32 tiers' drift by
   3 T 2^-24 sum_k area_k sum_j |w_j| |h_kj| (w the element-mean weights).
+* Sloped-beach tsunami, 500,000 triangles, N = 4, 4 multirate levels, PP + TVB,
+  200 finest substeps (25 macro steps), built and launched as the benchmark does
+  (levels from the library's CFL rule, graph-replayed macro steps, FP32
+  tensor-core tier). The levels equal the oracle's bit for bit; element means of
+  the free surface eta = h + B and of the momenta on seeded samples (uniform,
+  around the source, at the shore) are compared in units of the 2 m wave: the
+  tier's state bound 8e-5 times the amplitude A for eta and times A sqrt(g H),
+  H = 4000 m, the momentum a linear wave of amplitude A carries, for hu and hv.
 """
+import hashlib
 import json
 import os
 
@@ -36,6 +45,8 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "ful
 DAM_TOL32 = {"fp32": (2e-4, 2e-4 * np.sqrt(9.81), 1e-4),
              "fp32tc": (8e-4, 8e-4 * np.sqrt(9.81), 4e-4)}
 U32 = 2.0 ** -24
+TSU_TOL_STATE = 8e-5      # the tensor-core tier's state bound
+TSU_A, TSU_H = 2.0, 4000.0
 
 
 @pytest.fixture(scope="module")
@@ -147,3 +158,50 @@ def test_dam_break_full_size_2000_steps(golden, precision):
     assert e_m < tol_m and s_m < tol_m
     assert l1 < tol_l1
     assert budget < tol_budget and mass_err < tol_mass
+
+
+def test_tsunami_full_size_200_substeps(golden):
+    import paper_1403_1661_gb300 as P
+    from paper_1403_1661_gb300.solver import scenario_inputs
+    g = golden["tsunami"]
+    scn = sc.tsunami()
+    s = P.solver_from_scenario(scn, precision="fp32tc")      # as the benchmark builds it
+    lev = np.asarray(s.level, np.int8)
+    L, counts, dtm = s.level_info()
+    assert lev.size == g["K"] == 500_000
+    assert np.bincount(lev, minlength=5)[1:].tolist() == g["level_counts"]
+    assert hashlib.sha256(lev.tobytes()).hexdigest() == g["level_sha256"]
+    # the device takes each element's CFL step from its FP32 state, so dt_min (and
+    # the time after n substeps) agrees with the oracle's to FP32 rounding
+    assert abs(dtm - g["dt_min"]) <= 1e-6 * g["dt_min"]
+    s.step(g["macro_steps"])
+    st = s.stats()
+    h, hu, hv, t = s.get_state()
+    assert abs(t - g["time"]) <= 1e-6 * g["time"]
+    assert not st["nonfinite"] and np.isfinite(h).all() and h.min() >= -1e-6
+
+    w = _mean_weights(scn.N)
+    B, _, _, _ = scenario_inputs(scn, s.mesh)
+    B32 = B.astype(np.float32).astype(np.float64)             # the bed as the device holds it
+    eta_scale = TSU_TOL_STATE * TSU_A
+    mom_scale = TSU_TOL_STATE * TSU_A * np.sqrt(scn.g * TSU_H)
+    worst = {}
+    for name, grp in g["sample"].items():
+        el = np.asarray(grp["elements"])
+        eta_g = (h[el] + B32[el]) @ w
+        eta_o = np.asarray(grp["h"]) + np.asarray(grp["B"])
+        e_eta = np.abs(eta_g - eta_o).max()
+        e_m = max(np.abs(hu[el] @ w - grp["hu"]).max(), np.abs(hv[el] @ w - grp["hv"]).max())
+        # wet: mean depth above twice the dry-reset depth h0 (a dry element holds h0,
+        # which the FP32 tiers return within a few ulp of the bed's height)
+        wet_agree = ((h[el] @ w > 2 * scn.h0) == (np.asarray(grp["h"]) > 2 * scn.h0)).all()
+        worst[name] = (e_eta, e_m, wet_agree)
+    mass_err = abs(st["mass"] - g["mass"]) / g["mass"]
+    print("PARITY tsunami full size fp32tc 200 substeps: "
+          + "; ".join(f"{n} eta {e:.3e} m, hu/hv {m:.3e} m^2/s, wet/dry agree {a}" for n, (e, m, a) in worst.items())
+          + f"; mass {mass_err:.3e}", flush=True)
+    for name, (e_eta, e_m, wet_agree) in worst.items():
+        assert wet_agree, name
+        assert e_eta < eta_scale, (name, e_eta)
+        assert e_m < mom_scale, (name, e_m)
+    assert mass_err < 1e-6
