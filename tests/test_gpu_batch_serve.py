@@ -111,3 +111,24 @@ def test_full_ensemble_batch_equals_alone_on_a_sample():
     b.close()
     for so in solvers:
         so.close()
+
+
+def test_served_nonfinite_solve_is_stopped_and_the_other_completes():
+    """A served solve whose state turns non-finite is stopped at the server's next
+    health check and reported as failed, and the request served beside it
+    completes. The failing request is the served stream's own (a 3,872-triangle
+    beach at N = 2 whose thin shoreline layers outrun the levels fixed at t = 0;
+    the FP64 oracle diverges on it as well): the kernels run on non-finite numbers
+    and the device flag reports them, no GPU fault is involved."""
+    from paper_1403_1661_gb300.serve import GpuFactory, Request, Server
+    bad = sc.served_stream(duration=5.0)[19][1]
+    assert bad.name == "tsunami_88x22x2_N2_L4"
+    good = sc.tsunami(nx=40, ny=10, N=3, nlevels=4, amp=1.5, src=(150e3, 40e3))
+    reqs = [Request(rid=0, arrival=0.0, scenario=bad, substeps=500),
+            Request(rid=1, arrival=0.0, scenario=good, substeps=24)]
+    srv = Server(budget_bytes=2e9, max_slots=2, macro_per_round=4, factory=GpuFactory("fp32tc"),
+                 health_every=2)
+    out = srv.run(reqs)
+    st = {r.rid: (r.status, r.error) for r in out["done"] + out["ended"]}
+    assert st[0] == ("failed", "non-finite state")
+    assert st[1] == ("done", None) and out["requests"] == 1 and out["failed"] == 1
