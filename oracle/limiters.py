@@ -158,6 +158,24 @@ def swe_eigenvectors(h, u, v, nx, ny, g):
     return R
 
 
+def positivity_modify(hb, dh, h0):
+    """Positivity modification of the limited depth deltas (Section 5.3,
+    Eq. modified_TVB). hb: (n,) mean depths; dh: (n, 3) depth deltas at the three
+    edge midpoints. The vertex values of the P1 depth are hb + S_a with
+    S_a = d_a + d_{a-1} - d_{a+1} (the vertex opposite midpoint a+1). Where the lowest
+    of them lies below h0, the deltas are pulled toward their average dbar by
+    theta = clip((hb + dbar - h0) / (dbar - min_a S_a), 0, 1), which puts that vertex
+    exactly at h0 and keeps the average delta (so the element mean). Returns the
+    modified deltas."""
+    S = np.stack([dh[:, 0] + dh[:, 2] - dh[:, 1], dh[:, 1] + dh[:, 0] - dh[:, 2],
+                  dh[:, 2] + dh[:, 1] - dh[:, 0]], axis=1)
+    dbar = dh.mean(axis=1)
+    need = (hb + S.min(axis=1)) < h0
+    den = dbar - S.min(axis=1)
+    th = np.where(need & (den > 0), np.clip((hb + dbar - h0) / np.where(den > 0, den, 1.0), 0.0, 1.0), 1.0)
+    return dbar[:, None] + th[:, None] * (dh - dbar[:, None])
+
+
 def tvb_limit(model: SWEModel, h, hu, hv, dry, active=None, M: float = 0.0, nu: float = 1.5,
               geom=None):
     """Characteristic TVB limiter + positivity modification on every active, wet
@@ -253,14 +271,7 @@ def tvb_limit(model: SWEModel, h, hu, hv, dry, active=None, M: float = 0.0, nu: 
     Bmid = np.stack([0.5 * (Bv[:, 0] + Bv[:, 1]), 0.5 * (Bv[:, 1] + Bv[:, 2]),
                      0.5 * (Bv[:, 2] + Bv[:, 0])], axis=1)
     dh = dhat[:, :, 0] - (Bmid - Bbar[e][:, None])
-    # positivity modification (Eq. modified_TVB); vertex a = hbar + d_a + d_{a-1} - d_{a+1}
-    S = np.stack([dh[:, 0] + dh[:, 2] - dh[:, 1], dh[:, 1] + dh[:, 0] - dh[:, 2],
-                  dh[:, 2] + dh[:, 1] - dh[:, 0]], axis=1)
-    dbar = dh.mean(axis=1)
-    need = (hb + S.min(axis=1)) < h0
-    den = dbar - S.min(axis=1)
-    th = np.where(need & (den > 0), np.clip((hb + dbar - h0) / np.where(den > 0, den, 1.0), 0.0, 1.0), 1.0)
-    dh = dbar[:, None] + th[:, None] * (dh - dbar[:, None])
+    dh = positivity_modify(hb, dh, h0)
     # rebuild P1 nodal values where anything changed
     lam = np.stack([-(ref.r + ref.s) / 2.0, (1.0 + ref.r) / 2.0, (1.0 + ref.s) / 2.0], axis=0)  # (3, Np)
 
