@@ -333,14 +333,21 @@ int swe_kernel_launches(const swe_solver* solver, int64_t* launches);
  * host application with its own fixed arena, and latency-sensitive monitoring
  * loops for which a cudaMalloc could synchronise the device. The paper has no
  * counterpart of this call; it is a deployment convenience.
- *   N         polynomial order, 2..5
+ *   N         polynomial order, 1..5
  *   K         number of elements, with K*Np <= 2^31-1 (SWE_EINVAL beyond)
- *   dev_h     device, K x Np doubles: nodal depth h in the library's node order
+ *   dev_h     device, K x Np doubles: nodal depth h, element-major (row k holds
+ *             element k's Np nodal values, contiguous, in the library's node order),
+ *             elements in the same order as dev_area -- the layout swe_get_state
+ *             returns, not the solver's internal device layout
  *   dev_area  device, K doubles: element areas
- *   dev_out   device, 2 doubles written: [0] sum_k area_k mean(h_k), [1] min nodal h
+ *   dev_out   device, 2 doubles written: [0] sum_k area_k mean(h_k), [1] min nodal h;
+ *             a NaN depth makes both NaN (the minimum keeps NaN; an infinite depth
+ *             shows in the mass)
  *   stream    cudaStream_t (as void*), may be NULL
  * The first call on each device looks up the scratch array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call before
+ * (cudaGetSymbolAddress, with that device current) and keeps it for the rest of
+ * the process: the call assumes the context current then (a runtime-API caller's
+ * primary context) and no cudaDeviceReset afterwards. Make that first call before
  * any stream capture. Every call shares the one scratch array per device, so
  * calls whose kernels overlap on the GPU (concurrent streams) race and give
  * wrong results; serialise them. Nothing in the scratch needs clearing: each

@@ -33,6 +33,12 @@ struct MeanWeights {
   double w[28];
 };
 
+// Minimum that keeps a NaN: fmin() returns the other operand when one is NaN, which
+// would let a non-finite depth vanish from the minimum.
+__device__ __forceinline__ double min_keep_nan(double a, double b) {
+  return a != a ? a : (b != b ? b : fmin(a, b));
+}
+
 __global__ void __launch_bounds__(kThreads) k_mass_hmin_partials(const double* __restrict__ h,
                                                                  const double* __restrict__ area,
                                                                  int K, int np, MeanWeights mw,
@@ -45,7 +51,7 @@ __global__ void __launch_bounds__(kThreads) k_mass_hmin_partials(const double* _
     double hb = 0.0;
     for (int j = 0; j < np; ++j) {
       hb += mw.w[j] * he[j];
-      hmin = fmin(hmin, he[j]);
+      hmin = min_keep_nan(hmin, he[j]);
     }
     mass += area[e] * hb;
   }
@@ -55,7 +61,7 @@ __global__ void __launch_bounds__(kThreads) k_mass_hmin_partials(const double* _
   for (int s = kThreads / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) {
       sm[threadIdx.x] += sm[threadIdx.x + s];
-      sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + s]);
+      sh[threadIdx.x] = min_keep_nan(sh[threadIdx.x], sh[threadIdx.x + s]);
     }
     __syncthreads();
   }
@@ -72,7 +78,7 @@ __global__ void __launch_bounds__(kThreads) k_mass_hmin_final(const double* part
   double m = 0.0, h = 1e300;
   for (int i = threadIdx.x; i < nblocks; i += kThreads) {
     m += partials[2 * i];
-    h = fmin(h, partials[2 * i + 1]);
+    h = min_keep_nan(h, partials[2 * i + 1]);
   }
   sm[threadIdx.x] = m;
   sh[threadIdx.x] = h;
@@ -80,7 +86,7 @@ __global__ void __launch_bounds__(kThreads) k_mass_hmin_final(const double* part
   for (int s = kThreads / 2; s > 0; s >>= 1) {
     if (threadIdx.x < s) {
       sm[threadIdx.x] += sm[threadIdx.x + s];
-      sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + s]);
+      sh[threadIdx.x] = min_keep_nan(sh[threadIdx.x], sh[threadIdx.x + s]);
     }
     __syncthreads();
   }
@@ -104,7 +110,7 @@ int fail_na(int code, const std::string& msg) {
 
 extern "C" int swe_mass_hmin_static(int32_t N, int32_t K, const double* dev_h, const double* dev_area,
                                     double* dev_out, void* stream) {
-  if (N < 2 || N > 5) return fail_na(SWE_EINVAL, "swe_mass_hmin_static: N must be in 2..5");
+  if (N < 1 || N > 5) return fail_na(SWE_EINVAL, "swe_mass_hmin_static: N must be in 1..5");
   const int np = (N + 1) * (N + 2) / 2;
   if (K < 1 || (int64_t)K * np > INT32_MAX)
     return fail_na(SWE_EINVAL, "swe_mass_hmin_static: K must satisfy 1 <= K and K*Np <= 2^31-1");
@@ -117,7 +123,10 @@ extern "C" int swe_mass_hmin_static(int32_t N, int32_t K, const double* dev_h, c
   MeanWeights mw;
   {
     // once per device, with that device current: the host-side name g_partials is
-    // only a stand-in, the kernels need its device address
+    // only a stand-in, the kernels need its device address. The address belongs to
+    // the context current at that first call (the device's primary context for a
+    // runtime-API caller); it is not looked up again, so the call assumes that
+    // context for the life of the process (no cudaDeviceReset in between).
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_ptr[dev]) {
       void* p = nullptr;
