@@ -15,14 +15,25 @@ and the seeded input generators in ``workloads/``).
   the last place (h (1 + 2^-52)): the oracle's own response to a rounding-level
   change, which bounds how closely a differently rounded FP64 implementation can
   follow it through the minmod and wet/dry decisions of 2000 limited steps.
+* ``dam_break_ulp32``: the same from an initial depth perturbed by one unit in the
+  last place of single precision (h (1 + 2^-23)): the oracle's response to a
+  change of the size single-precision storage makes, which bounds how closely the
+  FP32 tiers can follow it.
+* ``dam_break_noise64`` and ``dam_break_store32``: the same run with the state
+  changed after every step by rounding-level amounts, the way an implementation
+  that rounds differently (or stores single precision) departs from the oracle at
+  every step rather than once: each nodal value multiplied by (1 + d), d uniform in
+  [-2^-52, 2^-52] (seeded), respectively rounded to single precision. These bound
+  how closely the FP64 and the FP32 tiers can follow the oracle.
 * ``tsunami``: the 500,000-triangle sloped-beach run (N = 4, 4 MRAB levels by the
   CFL rule, PP + TVB), 25 macro steps = 200 finest substeps. Summarised by the
   level assignment (counts and a SHA-256 of the per-element levels), dt_min, the
   element means of h, hu, hv and B on seeded samples (uniform, around the source,
   at the shore) and the global mass.
 
-Run: ``python tests/golden/make_full_config_golden.py [dam_break] [dam_break_ulp] [tsunami]``
-(about 10, 10 and 40 minutes on 8 cores).
+Run: ``python tests/golden/make_full_config_golden.py [dam_break] [dam_break_ulp] [dam_break_ulp32]
+[dam_break_noise64] [dam_break_store32] [tsunami]`` (about 7 minutes for each dam-break run and
+40 for the tsunami on 8 cores).
 """
 from __future__ import annotations
 
@@ -55,24 +66,33 @@ def samples(rng, idx, n):
     return np.sort(rng.choice(idx, size=min(n, idx.size), replace=False))
 
 
-def run_dam_break(perturb=False):
+def run_dam_break(perturb=0.0, every_step=None):
+    """every_step: None, "noise64" (each nodal value times (1 + d), d uniform in
+    [-2^-52, 2^-52], seeded) or "store32" (each nodal value rounded to single
+    precision), applied to the state after every step."""
     scn = sc.dam_break()
     if perturb:
-        # the same run from an initial depth one unit in the last place larger: how
-        # far rounding-level differences carry through 2000 limited steps
+        # the same run from an initial depth larger by a relative perturb (one unit in
+        # the last place of double or of single precision): how far rounding-level
+        # differences carry through 2000 limited steps
         init = scn.init
 
         def init_ulp(x, y, cx, cy, B):
             h, hu, hv = init(x, y, cx, cy, B)
-            return np.asarray(h, np.float64) * (1.0 + 2.0 ** -52), hu, hv
+            return np.asarray(h, np.float64) * (1.0 + perturb), hu, hv
         scn.init = init_ulp
     om, ref, model, integ = problem.build(scn)
     assert om.K == 20480 and integ.L == 1
     mass0 = float(om.area @ (integ.q_end[0] @ ref.mean_w))
     hmin = float(integ.q_end[0].min())
     t0 = time.time()
+    rng_step = np.random.Generator(np.random.PCG64(23))
     for _ in range(scn.steps):
         integ.substep()
+        if every_step == "noise64":
+            integ.q_end = integ.q_end * (1.0 + rng_step.uniform(-2.0 ** -52, 2.0 ** -52, integ.q_end.shape))
+        elif every_step == "store32":
+            integ.q_end = integ.q_end.astype(np.float32).astype(np.float64)
         hmin = min(hmin, float(integ.q_end[0].min()))
     q = integ.q_end
     hb, hub, hvb = element_means(ref, q)
@@ -133,8 +153,17 @@ def main(which):
         new["dam_break"] = run_dam_break()
         print("dam_break done", new["dam_break"]["oracle_seconds"], flush=True)
     if "dam_break_ulp" in which:
-        new["dam_break_ulp"] = run_dam_break(perturb=True)
+        new["dam_break_ulp"] = run_dam_break(perturb=2.0 ** -52)
         print("dam_break_ulp done", new["dam_break_ulp"]["oracle_seconds"], flush=True)
+    if "dam_break_ulp32" in which:
+        new["dam_break_ulp32"] = run_dam_break(perturb=2.0 ** -23)
+        print("dam_break_ulp32 done", new["dam_break_ulp32"]["oracle_seconds"], flush=True)
+    if "dam_break_noise64" in which:
+        new["dam_break_noise64"] = run_dam_break(every_step="noise64")
+        print("dam_break_noise64 done", new["dam_break_noise64"]["oracle_seconds"], flush=True)
+    if "dam_break_store32" in which:
+        new["dam_break_store32"] = run_dam_break(every_step="store32")
+        print("dam_break_store32 done", new["dam_break_store32"]["oracle_seconds"], flush=True)
     if "tsunami" in which:
         new["tsunami"] = run_tsunami()
         print("tsunami done", new["tsunami"]["oracle_seconds"], flush=True)
@@ -149,4 +178,5 @@ def main(which):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["dam_break", "dam_break_ulp", "tsunami"])
+    main(sys.argv[1:] or ["dam_break", "dam_break_ulp", "dam_break_ulp32", "dam_break_noise64", "dam_break_store32",
+                          "tsunami"])
