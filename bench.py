@@ -532,22 +532,49 @@ def run_batched(args, steps=5):
         so = P.solver_from_scenario(s, precision=args.precision)
         so.set_launch_config(tuned[s.N])
         solvers.append(so)
-    b = P.Batch(solvers)
+    b = P.Batch(solvers, max_macro=1)
     b.step(1)
     torch.cuda.synchronize()
     d0 = sum(so.stats()["dof_updates"] for so in solvers)
+    l0 = b.launches()
+    # every batch step reads its per-scenario statuses back (a synchronisation), so
+    # the step is timed as a whole: CUDA events around the replays on the batch stream
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(b.stream)
-    b.step(steps)
+    for _ in range(steps):
+        b.step(1)
     e1.record(b.stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     dofs = sum(so.stats()["dof_updates"] for so in solvers) - d0
+    # element-stages of one macro step per scenario (active levels per substep)
+    d_step = {}
+    for so in solvers:
+        L, counts, _ = so.level_info()
+        per_macro = 0
+        for j in range(2 ** (L - 1)):
+            m = 1
+            while j and m < L and j % (2 ** m) == 0:
+                m += 1
+            per_macro += int(sum(counts[:(L if j == 0 else m)]))
+        d_step[so] = per_macro
+    bpe = {N: stage_bytes_per_element(N, 4 if args.precision != "fp64" else 8) for N in {s.N for s in scns}}
+    byts = sum(d_step[so] * bpe[s_.N] for s_, so in zip(scns, solvers))
+    peak, peak_kind = measured_peaks()
+    ach = byts / (ms / steps / 1e3) / 1e9
     out = {"value": dofs / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "scenarios": len(scns),
            "triangles": int(sum(so.K for so in solvers)), "orders": sorted({s.N for s in scns}),
            "autotuned_ctas_per_sm": {str(k): v for k, v in tuned.items()},
-           "step": "one graph launch = one macro step of every scenario (parallel graph branches)"}
+           "gpu_launches_per_step": (b.launches() - l0) / steps,
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                        "kernel": "k_batch (persistent; stage + TVB tickets)",
+                        "algorithmic_bytes_per_step": byts,
+                        "basis": "stage-kernel algorithmic bytes of every element-stage of the step over the "
+                                 "whole step time (the TVB work inside the same kernels is not counted)",
+                        "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"},
+           "step": "one graph replay = one macro step of every scenario: per (tier, order) group one "
+                   "persistent kernel over a device ticket queue"}
     b.close()
     for so in solvers:
         so.close()

@@ -278,21 +278,65 @@ int swe_set_full_state(swe_solver* solver, const void* host_buf, size_t bytes);
 int swe_level_info(const swe_solver* solver, int32_t* L, int32_t* counts, double* dt_min);
 
 /* ---- batched scenarios -------------------------------------------------- */
+/* Many independent scenarios (solvers) advanced together on one GPU. The paper
+ * solves one scenario at a time; this batching is a systems layer over its method
+ * (Algorithms 1-3 per scenario, unchanged). The solvers are grouped by precision
+ * tier and scheme / order (at most 48 per group); each group is advanced by ONE
+ * persistent kernel that takes its work from a device queue of tickets, one ticket
+ * being a tile of 128 elements of one phase (the stage kernel or the TVB limiter of
+ * one finest substep) of one scenario. Tickets are ordered phase by phase,
+ * round-robin over the scenarios, and a ticket waits (bounded in time) until every
+ * tile of its scenario's earlier phases is complete, so uneven scenarios fill each
+ * other's gaps. One batch step is one replay of a captured CUDA graph (per group:
+ * counters cleared, the persistent kernel, the macro-counter update; the groups as
+ * parallel branches). Results equal those of each solver stepped alone, bit for
+ * bit (the same per-element operations; nothing crosses scenarios). */
 typedef struct swe_batch swe_batch;
 
-/* Group n solvers (each on its own CUDA stream, level-synchronous) so that one
- * graph launch on `stream` advances every one of them by one of its own macro
- * steps: the graph holds each solver's substep kernels as a parallel branch, so
- * uneven scenarios overlap on the GPU. The solvers stay usable on their own;
- * work issued on their streams is ordered after a batch step. */
-int swe_batch_create(swe_solver* const* solvers, int32_t n, void* stream, swe_batch** out);
-/* n_macro graph launches (each advances every solver by one macro step).
- * SWE_EINVAL, with nothing launched, if any solver's levels, element order or
- * launch shape changed since swe_batch_create (swe_set_levels,
+/* Bytes of caller-owned device workspace (the ticket tables and counters) for a
+ * batch of these solvers that advances each by at most max_macro macro steps per
+ * swe_batch_step. SWE_EINVAL for NULL arrays, n < 1, max_macro < 1 or a solver
+ * without state and levels. */
+int swe_batch_workspace_bytes(swe_solver* const* solvers, int32_t n, int32_t max_macro, size_t* bytes);
+
+/* Create a batch of n distinct solvers, each with a valid level-synchronous state
+ * and its own (non-default) stream, in caller-owned device memory dev_workspace
+ * (bytes >= swe_batch_workspace_bytes, 256-byte aligned; owned by the caller, not
+ * freed by the library). stream: the batch's own non-default stream. The solvers
+ * stay usable on their own; work issued on their streams is ordered before and
+ * after a batch step. SWE_ENOMEM if the workspace is too small. */
+int swe_batch_create(swe_solver* const* solvers, int32_t n, int32_t max_macro, void* dev_workspace,
+                     size_t bytes, void* stream, swe_batch** out);
+
+/* Advance solver i by n_macro_each[i] macro steps (0..max_macro; host array of n),
+ * all in one batch step, and report per solver in status_each (host array of n):
+ * SWE_OK, or SWE_ETIMEOUT when one of its bounded waits gave up (its remaining
+ * work is skipped; the others carry on). A solver that timed out before any of its
+ * work ran (for instance while held, swe_batch_hold) keeps its state and time; one
+ * that timed out later has no valid state until swe_set_state or
+ * swe_set_full_state. Returns SWE_OK, or SWE_ETIMEOUT if any solver timed out.
+ * Synchronises the batch stream (the statuses are read back). SWE_EINVAL, with
+ * nothing launched, for a count outside 0..max_macro, a solver without a valid
+ * level-synchronous state, or a solver whose levels, element order, launch shape
+ * or boundary faces changed since swe_batch_create (swe_set_levels,
  * swe_setup_levels, swe_regroup, swe_set_launch_config, swe_set_farfield,
- * swe_set_open_faces, swe_set_full_state):
- * the captured graph would run stale launches; create the batch again. */
-int swe_batch_step(swe_batch* batch, int32_t n_macro);
+ * swe_set_open_faces, swe_set_full_state): create the batch again. */
+int swe_batch_step(swe_batch* batch, const int32_t* n_macro_each, int32_t* status_each);
+
+/* Bound (seconds, in (0, 3600); default 10) of every device wait of a batch step:
+ * a scenario's wait for its earlier phases and for its release. */
+int swe_batch_set_wait_limit(swe_batch* batch, double seconds);
+
+/* hold = 1: withhold solver i's release at the following batch steps, so its first
+ * phase waits until the wait limit and the step reports SWE_ETIMEOUT for it with
+ * its state unchanged (a scenario kept out of the batch without rebuilding it);
+ * hold = 0 releases it again. */
+int swe_batch_hold(swe_batch* batch, int32_t i, int32_t hold);
+
+/* Kernels this batch has launched (two per group and step). */
+int swe_batch_launches(const swe_batch* batch, int64_t* launches);
+
+/* Waits for the batch stream, then frees the host handle (not the workspace). */
 void swe_batch_destroy(swe_batch* batch);
 
 /* Boundary faces (those without a neighbour) are reflecting walls (the default;

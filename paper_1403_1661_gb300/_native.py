@@ -89,8 +89,12 @@ SIGNATURES = {
     "swe_level_info": (C.c_int, [_vp, _ip, _ip, _dp]),
     "swe_kernel_launches": (C.c_int, [_vp, _i64p]),
     "swe_profile_substeps": (C.c_int, [_vp, C.c_int32, _dp]),
-    "swe_batch_create": (C.c_int, [C.POINTER(_vp), C.c_int32, _vp, C.POINTER(_vp)]),
-    "swe_batch_step": (C.c_int, [_vp, C.c_int32]),
+    "swe_batch_workspace_bytes": (C.c_int, [C.POINTER(_vp), C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
+    "swe_batch_create": (C.c_int, [C.POINTER(_vp), C.c_int32, C.c_int32, _vp, C.c_size_t, _vp, C.POINTER(_vp)]),
+    "swe_batch_step": (C.c_int, [_vp, _ip, _ip]),
+    "swe_batch_set_wait_limit": (C.c_int, [_vp, C.c_double]),
+    "swe_batch_hold": (C.c_int, [_vp, C.c_int32, C.c_int32]),
+    "swe_batch_launches": (C.c_int, [_vp, _i64p]),
     "swe_batch_destroy": (None, [_vp]),
     "swe_set_launch_config": (C.c_int, [_vp, C.c_int32]),
     "swe_mass_hmin_static": (C.c_int, [C.c_int32, C.c_int32, _vp, _vp, _vp, _vp]),

@@ -14,30 +14,68 @@ from .build import BUILD
 
 
 class Batch:
-    """Many independent solvers advanced by one CUDA-graph launch per macro step."""
+    """Many independent solvers advanced together: per (tier, order) group one
+    persistent kernel over a device ticket queue, one CUDA-graph replay per step."""
 
-    def __init__(self, solvers, stream=None):
+    def __init__(self, solvers, stream=None, max_macro=8):
         import torch
         self.solvers = list(solvers)
         if not self.solvers:
             raise ValueError("empty batch")
+        self.max_macro = int(max_macro)
         dev = self.solvers[0].device
+        n = len(self.solvers)
+        handles = (C.c_void_p * n)(*[s.handle.value for s in self.solvers])
+        nbytes = C.c_size_t()
+        nat.check(nat.lib().swe_batch_workspace_bytes(handles, n, self.max_macro, C.byref(nbytes)),
+                  "swe_batch_workspace_bytes")
         with torch.cuda.device(dev):
             self.stream = torch.cuda.Stream(dev) if stream is None else stream
-        handles = (C.c_void_p * len(self.solvers))(*[s.handle.value for s in self.solvers])
+            self.workspace = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=dev)
         h = C.c_void_p()
         with torch.cuda.device(dev):
-            nat.check(nat.lib().swe_batch_create(handles, len(self.solvers), C.c_void_p(self.stream.cuda_stream),
+            nat.check(nat.lib().swe_batch_create(handles, n, self.max_macro, C.c_void_p(self.workspace.data_ptr()),
+                                                 self.workspace.numel(), C.c_void_p(self.stream.cuda_stream),
                                                  C.byref(h)), "swe_batch_create")
         self.handle = h
+        self.last_status = np.zeros(n, np.int32)
 
-    def step(self, n_macro=1):
-        nat.check(nat.lib().swe_batch_step(self.handle, int(n_macro)), "swe_batch_step")
+    def step(self, n_macro=1, check=True):
+        """Advance every solver by n_macro macro steps (an int, or one count per
+        solver). Returns the per-solver status codes of the last batch step; with
+        check, a timed-out solver raises."""
+        n = len(self.solvers)
+        counts = np.broadcast_to(np.asarray(n_macro, np.int32), (n,)).copy()
+        status = np.zeros(n, np.int32)
+        while counts.max(initial=0) > 0:
+            now = np.minimum(counts, self.max_macro).astype(np.int32)
+            rc = nat.lib().swe_batch_step(self.handle, nat.iptr(now), nat.iptr(status))
+            if rc not in (nat.SWE_OK, nat.SWE_ETIMEOUT):
+                nat.check(rc, "swe_batch_step")
+            counts -= now
+            if rc == nat.SWE_ETIMEOUT:
+                break
+        self.last_status = status
+        if check and (status != nat.SWE_OK).any():
+            raise nat.SWEError(int(status[status != nat.SWE_OK][0]), "swe_batch_step")
+        return status
+
+    def set_wait_limit(self, seconds):
+        nat.check(nat.lib().swe_batch_set_wait_limit(self.handle, float(seconds)), "swe_batch_set_wait_limit")
+
+    def hold(self, i, hold=True):
+        nat.check(nat.lib().swe_batch_hold(self.handle, int(i), 1 if hold else 0), "swe_batch_hold")
+
+    def launches(self):
+        v = C.c_int64()
+        nat.check(nat.lib().swe_batch_launches(self.handle, C.byref(v)), "swe_batch_launches")
+        return v.value
 
     def close(self):
         if getattr(self, "handle", None):
             nat.lib().swe_batch_destroy(self.handle)
             self.handle = None
+            self.workspace = None
 
     def __del__(self):
         try:

@@ -20,6 +20,11 @@ BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(BUILD, "libswe_gb300.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The front end forms fused multiply-adds; the assembler is not allowed to fuse
+# further multiplies and adds on its own, since it compiles a shared out-of-line
+# function separately for each calling kernel and could round them differently:
+# the stage and limiter bodies then compute the same bits in every kernel.
+PTXAS = ["-Xptxas", "--fmad=false"]
 CXX_SOURCES = ["refelem.cpp", "mesh.cpp", "solver.cpp"]
 CU_SOURCES = ["kernels_n1.cu", "kernels_n2.cu", "kernels_n3.cu", "kernels_n4.cu", "kernels_n5.cu",
               "kernels_c2.cu", "kernels_c3.cu", "kernels_c4.cu", "kernels_c5.cu",
@@ -81,7 +86,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
         obj = os.path.join(BUILD, f + ".o")
         objs.append(obj)
         if _stale(obj, src, headers):
-            cmd = [nvcc, "-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
+            cmd = [nvcc, "-std=c++17", "-O3", *ARCH, *PTXAS, "-lineinfo", "-Xcompiler", "-fPIC",
                    f"-I{INCLUDE}", "-c", src, "-o", obj]
             if ptxas_info:
                 cmd.insert(1, "-Xptxas=-v")

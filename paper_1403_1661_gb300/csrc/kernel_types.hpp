@@ -166,4 +166,60 @@ struct LimitParams {
   int post_stage;  // 1: limit the just-committed state of active elements; 0: current state
 };
 
+// ---- persistent batched launch ------------------------------------------
+// Many scenarios advance in one persistent kernel per (tier, scheme and order)
+// group. The work is a queue of tickets; a ticket is one tile of 128 elements of one
+// phase (the stage kernel or the TVB limiter of one finest substep) of one
+// scenario. Tickets are ordered phase by phase, round-robin over the scenarios, so a
+// ticket depends only on tickets handed out before it (its scenario's earlier
+// phases): the lowest outstanding ticket can always run, with or without every CTA
+// resident.
+
+constexpr int kBatchTile = 128;     // threads per CTA
+constexpr int kBatchStageTile = 256;  // elements per stage ticket: two warp-tiles per warp
+constexpr int kBatchTvbTile = 512;  // elements per TVB ticket (the limiter is cheap per element)
+constexpr int kBatchMaxScn = 48;    // scenarios per group launch (kernel-parameter space)
+
+template <typename T>
+struct BatchScn {
+  DevState<T> s;
+  Sched sc;
+  Phys ph;          // with the scenario's limiter mask applied
+};
+
+struct BatchSeg {   // one phase of one scenario: tickets [t0, t0 + ntiles)
+  int t0;
+  int ntiles;
+  int need;         // tiles of this scenario that must be complete first
+  int scn;          // scenario (index in the group)
+  int nactive;      // active elements
+  int kind;         // 0: stage kernel, 1: TVB limiter
+  int j;            // substep within the macro step
+  int kofs;         // k of this phase minus k at the start of the call
+  int first;        // the scenario's first phase in this call: waits for its release
+  int pad;
+};
+
+struct BatchCtl {   // per group, in the batch workspace
+  int head;         // next ticket
+  int total;        // tickets of this call
+  int nseg;         // segments of this call
+  int pad;
+  long long wait_ns;  // bound of every wait
+};
+
+template <typename T>
+struct BatchLaunch {
+  BatchScn<T> scn[kBatchMaxScn];
+  const BatchSeg* segs;
+  const int* seg_of;  // [tickets] the segment of each ticket
+  BatchCtl* ctl;
+  int* done;          // [nscn] tiles completed (run or skipped) per scenario
+  int* ran;           // [nscn] tiles run per scenario
+  int* status;        // [nscn] 0, or SWE_ETIMEOUT when a wait gave up
+  const int* release; // [nscn] nonzero: the scenario may start
+  int nscn;
+  int period[kBatchMaxScn];   // finest substeps per macro step of each scenario
+};
+
 }  // namespace swe

@@ -100,6 +100,14 @@ __device__ __forceinline__ void load_row_global(const T* __restrict__ p, T (&o)[
 }
 
 template <typename T, int LEN>
+__device__ __forceinline__ void load_row_m(const T* p, T (&o)[LEN]) {
+  using V = Vec16<T>;
+  const typename V::type* pv = reinterpret_cast<const typename V::type*>(p);
+#pragma unroll
+  for (int k = 0; k < LEN / V::n; ++k) V::unpack(pv[k], &o[k * V::n]);
+}
+
+template <typename T, int LEN>
 __device__ __forceinline__ void store_row_global(T* __restrict__ p, const T (&o)[LEN]) {
   using V = Vec16<T>;
   typename V::type* pv = reinterpret_cast<typename V::type*>(p);
@@ -135,6 +143,24 @@ __device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
 // Only addresses inside live buffers are ever passed.
 __device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// Loads of the arrays the kernels write (state, Adams-Bashforth history, half-step
+// records, means, dry flags, P1 values): ordinary coherent global loads, never the
+// read-only data path. Inside the persistent batch kernel other CTAs of the same
+// launch wrote these arrays in earlier phases, and an ordinary load after the
+// acquire of the phase counter sees their stores. The separate launches use the
+// same loads, so both compile the stage and limiter bodies to the same code and a
+// scenario's result is the same, bit for bit, alone and in a batch.
+template <typename T>
+__device__ __forceinline__ T ldm(const T* p) {
+  return *p;
+}
+
+template <typename T, int NP, int LEN>
+__device__ __forceinline__ void load_nodes_m(const T* p, size_t ks, T (&o)[LEN]) {
+#pragma unroll
+  for (int i = 0; i < LEN; ++i) o[i] = i < NP ? ldm(p + i * ks) : T(0);
+}
 
 template <typename T>
 __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
@@ -384,13 +410,13 @@ __device__ __forceinline__ void surface_fluxes(const StageParams<T>& p, const T*
       for (int m = 0; m < NFP; ++m) {
         const int jn = face_node_rt(Dims<N>::N, fn, m);
         const size_t idx = (size_t)jn * sn;
-        ne[m] = __ldg(qn + idx);
-        nu[m] = __ldg(qn + sf + idx);
-        nv[m] = __ldg(qn + 2 * sf + idx);
+        ne[m] = ldm(qn + idx);
+        nu[m] = ldm(qn + sf + idx);
+        nv[m] = ldm(qn + 2 * sf + idx);
         nB[m] = __ldg(p.s.B + nb + (size_t)jn * ks);
       }
       if (phase == 0 && nb < e) {   // an active neighbour numbered lower: its node 0
-        Ef = __ldg(qn);
+        Ef = ldm(qn);
         Bf = __ldg(p.s.B + nb);
       }
       if (phase != 0 && !half) {  // other fractions: Adams-Bashforth polynomial at t_k
@@ -404,9 +430,9 @@ __device__ __forceinline__ void surface_fluxes(const StageParams<T>& p, const T*
 #pragma unroll
           for (int m = 0; m < NFP; ++m) {
             const size_t idx = (size_t)face_node_rt(Dims<N>::N, fn, m) * ks;
-            ne[m] += ws * __ldg(rs + idx);
-            nu[m] += ws * __ldg(rs + fstride + idx);
-            nv[m] += ws * __ldg(rs + 2 * fstride + idx);
+            ne[m] += ws * ldm(rs + idx);
+            nu[m] += ws * ldm(rs + fstride + idx);
+            nv[m] += ws * ldm(rs + 2 * fstride + idx);
           }
         }
       }
@@ -578,7 +604,8 @@ __device__ __forceinline__ void commit_and_limit(const StageParams<T>& p, const 
     const T* rs = ring + (size_t)((a - s) % 3) * bstride + eo;
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-      const T r0 = __ldg(rs + i * ks), r1 = __ldg(rs + fstride + i * ks), r2 = __ldg(rs + 2 * fstride + i * ks);
+      const T r0 = ldm(rs + i * ks), r1 = ldm(rs + fstride + i * ks);
+      const T r2 = ldm(rs + 2 * fstride + i * ks);
       eta[i] += cs * r0;
       hu[i] += cs * r1;
       hv[i] += cs * r2;
@@ -677,12 +704,61 @@ __device__ __forceinline__ void volume_term(const T* __restrict__ sops, const T 
   }
 }
 
+// One element of the stage: R(Q) (volume + surface + lift), then the
+// Adams-Bashforth commit and the positivity limiter (mode 0) or R only (mode 1).
+// k is the finest substep count of the schedule.
+template <typename T, int N>
+__device__ __forceinline__ void stage_element(const StageParams<T>& p, const T* __restrict__ sops, int e,
+                                              long long k, double* injected) {
+  using D = Dims<N>;
+  constexpr int NP = D::NP, NPP = D::NPP;
+  const Sched& sc = p.sc;
+  const T g = (T)p.ph.g, hvel = (T)p.ph.hvel;
+  const size_t ks = (size_t)sc.KS;
+  const size_t fstride = (size_t)NP * ks;            // between fields
+  const size_t bstride = 3 * fstride;                // between buffers
+  const int lev = level_of(sc, e);
+  const long long a = k >> (lev - 1);
+  const int src = (int)(a & 1);
+  T eta[NPP], hu[NPP], hv[NPP], bb[NPP];
+  load_nodes_m<T, NP, NPP>(p.s.q + src * bstride + 0 * fstride + e, ks, eta);
+  load_nodes_m<T, NP, NPP>(p.s.q + src * bstride + 1 * fstride + e, ks, hu);
+  load_nodes_m<T, NP, NPP>(p.s.q + src * bstride + 2 * fstride + e, ks, hv);
+  load_nodes<T, NP, NPP>(p.s.B + e, ks, bb);
+  const T rx = __ldg(p.s.geo + 4 * (size_t)e + 0), ry = __ldg(p.s.geo + 4 * (size_t)e + 1);
+  const T sx = __ldg(p.s.geo + 4 * (size_t)e + 2), sy = __ldg(p.s.geo + 4 * (size_t)e + 3);
+  // depth form of the pressure for dry elements; with inexact rules (collocation,
+  // order 2N) the pre-balanced form everywhere (the two forms then differ)
+  const T md = (Dims<N>::EXACT && ldm(p.s.dry + e)) ? T(1) : T(0);
+
+  T R0[NP], R1[NP], R2[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) { R0[i] = 0; R1[i] = 0; R2[i] = 0; }
+
+  // ---- volume term (Section 7.1): interpolate, flux + source, project ----
+  volume_term<T, N>(sops, eta, hu, hv, bb, rx, ry, sx, sy, md, g, hvel, R0, R1, R2);
+
+  auto own = [&](int f, int jn) -> T { return f == 0 ? eta[jn] : (f == 1 ? hu[jn] : (f == 2 ? hv[jn] : bb[jn])); };
+  surface_lift<T, N, false>(p, sops, e, k, own, rx, ry, sx, sy, md, R0, R1, R2);
+  add_reference_pressure<T, N>(sops, eta, bb, g, rx, ry, sx, sy, R1, R2);
+  commit_and_limit<T, N>(p, sops, e, lev, a, eta, hu, hv, bb, rx, ry, sx, sy, R0, R1, R2, injected);
+}
+
+// Elements e0, e0 + step, ... below e1 of the stage; returns the mass the
+// positivity limiter's dry resets injected (inlined by the separate launch and the
+// persistent batch kernel alike).
+template <typename T, int N>
+__device__ __forceinline__ double stage_range(const StageParams<T>& __restrict__ p, const T* __restrict__ sops,
+                                           int e0, int step, int e1, long long k) {
+  double injected = 0.0;
+  for (int e = e0; e < e1; e += step) stage_element<T, N>(p, sops, e, k, &injected);
+  return injected;
+}
+
 // kGlobalOps: the operators are read from global memory (through L1) instead of
 // the block's shared-memory copy (the operator-placement comparison of Section 7.4).
 template <typename T, int N, bool kGlobalOps = false>
-__global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
-  using D = Dims<N>;
-  constexpr int NP = D::NP, NPP = D::NPP;
+__global__ void __launch_bounds__(kBlock) k_stage(const __grid_constant__ StageParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const T* sops;
   if constexpr (kGlobalOps) {
@@ -691,41 +767,15 @@ __global__ void __launch_bounds__(kBlock) k_stage(StageParams<T> p) {
     stage_ops<T, N>(reinterpret_cast<T*>(smem_raw), p.s.ops);
     sops = reinterpret_cast<const T*>(smem_raw);
   }
-
-  const Sched& sc = p.sc;
-  const long long k = (*p.s.macro) * (1LL << (sc.L - 1)) + p.j;
-  const T g = (T)p.ph.g, hvel = (T)p.ph.hvel;
-  const size_t ks = (size_t)sc.KS;
-  const size_t fstride = (size_t)NP * ks;            // between fields
-  const size_t bstride = 3 * fstride;                // between buffers
-  double injected = 0.0;
-
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.nactive; e += gridDim.x * blockDim.x) {
-    const int lev = level_of(sc, e);
-    const long long a = k >> (lev - 1);
-    const int src = (int)(a & 1);
-    T eta[NPP], hu[NPP], hv[NPP], bb[NPP];
-    load_nodes<T, NP, NPP>(p.s.q + src * bstride + 0 * fstride + e, ks, eta);
-    load_nodes<T, NP, NPP>(p.s.q + src * bstride + 1 * fstride + e, ks, hu);
-    load_nodes<T, NP, NPP>(p.s.q + src * bstride + 2 * fstride + e, ks, hv);
-    load_nodes<T, NP, NPP>(p.s.B + e, ks, bb);
-    const T rx = __ldg(p.s.geo + 4 * (size_t)e + 0), ry = __ldg(p.s.geo + 4 * (size_t)e + 1);
-    const T sx = __ldg(p.s.geo + 4 * (size_t)e + 2), sy = __ldg(p.s.geo + 4 * (size_t)e + 3);
-    // depth form of the pressure for dry elements; with inexact rules (collocation,
-    // order 2N) the pre-balanced form everywhere (the two forms then differ)
-    const T md = (Dims<N>::EXACT && p.s.dry[e]) ? T(1) : T(0);
-
-    T R0[NP], R1[NP], R2[NP];
-#pragma unroll
-    for (int i = 0; i < NP; ++i) { R0[i] = 0; R1[i] = 0; R2[i] = 0; }
-
-    // ---- volume term (Section 7.1): interpolate, flux + source, project ----
-    volume_term<T, N>(sops, eta, hu, hv, bb, rx, ry, sx, sy, md, g, hvel, R0, R1, R2);
-
-    auto own = [&](int f, int jn) -> T { return f == 0 ? eta[jn] : (f == 1 ? hu[jn] : (f == 2 ? hv[jn] : bb[jn])); };
-    surface_lift<T, N>(p, sops, e, k, own, rx, ry, sx, sy, md, R0, R1, R2);
-    add_reference_pressure<T, N>(sops, eta, bb, g, rx, ry, sx, sy, R1, R2);
-    commit_and_limit<T, N>(p, sops, e, lev, a, eta, hu, hv, bb, rx, ry, sx, sy, R0, R1, R2, &injected);
+  const long long k = (*p.s.macro) * (1LL << (p.sc.L - 1)) + p.j;
+  double injected;
+  if constexpr (kGlobalOps) {
+    injected = 0.0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.nactive; e += gridDim.x * blockDim.x)
+      stage_element<T, N>(p, sops, e, k, &injected);
+  } else {
+    injected = stage_range<T, N>(p, sops, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x,
+                                 p.nactive, k);
   }
   if (injected != 0.0) atomicAdd(p.s.acc, injected);
 }
@@ -787,23 +837,23 @@ __device__ __forceinline__ T minmod_tvb(T a, T b, T thr, bool& changed) {
   return r;
 }
 
+// The TVB limiter with the positivity modification on element e (k: the finest
+// substep count of the schedule); returns without change for an element that is dry,
+// has a dry neighbour or needs no limiting.
 template <typename T, int N>
-__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_tvb(LimitParams<T> p) {
+__device__ __forceinline__ void tvb_element(const LimitParams<T>& p, const T* __restrict__ sops, int e,
+                                            long long k) {
   using D = Dims<N>;
   using O = OpLayout<N>;
   constexpr int NP = D::NP, NPP = D::NPP;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sops = reinterpret_cast<T*>(smem_raw);
-  stage_ops<T, N, OpLayout<N>::TAIL>(sops, p.s.ops);
   const Sched& sc = p.sc;
-  const long long k = (*p.s.macro) * (1LL << (sc.L - 1)) + p.j;
   const T g = (T)p.ph.g, h0 = (T)p.ph.h0;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.nactive; e += gridDim.x * blockDim.x) {
+  {
     // Every load is issued before the first branch on loaded data (an element that is
     // dry or has a dry neighbour is skipped afterwards), so the latencies overlap:
     // two dependent trips to memory (connectivity, then the neighbours) instead of four.
     const int4 cn = __ldg(p.s.conn + e);
-    const int de = __ldg(p.s.dry + e);
+    const int de = ldm(p.s.dry + e);
     const int nbs[3] = {cn.x, cn.y, cn.z};
     const int lev = level_of(sc, e);
     const long long a = k >> (lev - 1);
@@ -814,16 +864,16 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_tvb(LimitPar
     // positivity pass, the neighbour-mean weights
     T gm[4], u0[4], tg[8];
     load_row_global<T, 4>(p.s.geo + 4 * eo, gm);
-    load_row_global<T, 4>(p.s.means + 4 * eo, u0);
+    load_row_m<T, 4>(p.s.means + 4 * eo, u0);
     load_row_global<T, 8>(p.s.tvbg + 8 * eo, tg);
     // P1 part: vertex values of Pi1 q for eta, hu, hv (stored with the committed
     // state) and of Pi1 B (static)
     T vq[3][3], vb[3];
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
-      vq[0][v] = __ldg(p.s.p1 + (0 + v) * ks + eo);
-      vq[1][v] = __ldg(p.s.p1 + (3 + v) * ks + eo);
-      vq[2][v] = __ldg(p.s.p1 + (6 + v) * ks + eo);
+      vq[0][v] = ldm(p.s.p1 + (0 + v) * ks + eo);
+      vq[1][v] = ldm(p.s.p1 + (3 + v) * ks + eo);
+      vq[2][v] = ldm(p.s.p1 + (6 + v) * ks + eo);
       vb[v] = __ldg(p.s.vb + v * ks + eo);
     }
     // neighbour means and dry flags
@@ -833,11 +883,11 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_tvb(LimitPar
     for (int f = 0; f < 3; ++f) {
       const int nb = nbs[f];
       if (nb >= 0) {
-        dn |= __ldg(p.s.dry + nb);
-        load_row_global<T, 4>(p.s.means + 4 * (size_t)nb, un[f]);
+        dn |= ldm(p.s.dry + nb);
+        load_row_m<T, 4>(p.s.means + 4 * (size_t)nb, un[f]);
       }
     }
-    if (de || dn) continue;
+    if (de || dn) return;
     const T rx = gm[0], ry = gm[1], sx = gm[2], sy = gm[3];
     // a far-field face sees the far-field state over the own mean bed; a wall face
     // mirrors the normal momentum of the own mean
@@ -914,7 +964,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_tvb(LimitPar
 #pragma unroll
       for (int c = 0; c < 3; ++c) dl[i][c] = Rm[c][0] * wl[0] + Rm[c][1] * wl[1] + Rm[c][2] * wl[2];
     }
-    if (!changed) continue;
+    if (!changed) return;
     // redistribution: deltas of each field sum to zero
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -952,17 +1002,56 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_tvb(LimitPar
     const T* bary = sops + O::BARY;
     T fld[3][NPP], bb[NPP];
     load_nodes<T, NP, NPP>(p.s.B + eo, ks, bb);
+    if constexpr (sizeof(T) == 4) {
+      // Single precision: rebuild about the means, eta = eta-bar + sum_v l_v S_v +
+      // (B - B-bar) with S_v the vertex deltas. The stored barycentric weights sum to
+      // one only to rounding (2^-25 at worst), so sum_v l_v (h-bar + S_v) would scale
+      // every rebuilt element's mean by that sum; about the mean the rounding is of
+      // the size of the deltas, not of the depth.
+      const T Sh[3] = {dh[0] + dh[2] - dh[1], dh[1] + dh[0] - dh[2], dh[2] + dh[1] - dh[0]};
+      const T Su[3] = {dl[0][1] + dl[2][1] - dl[1][1], dl[1][1] + dl[0][1] - dl[2][1],
+                       dl[2][1] + dl[1][1] - dl[0][1]};
+      const T Sv[3] = {dl[0][2] + dl[2][2] - dl[1][2], dl[1][2] + dl[0][2] - dl[2][2],
+                       dl[2][2] + dl[1][2] - dl[0][2]};
 #pragma unroll
-    for (int jn = 0; jn < NP; ++jn) {
-      const T l0 = bary[4 * jn], l1 = bary[4 * jn + 1], l2 = bary[4 * jn + 2];
-      fld[0][jn] = l0 * vh[0] + l1 * vh[1] + l2 * vh[2] + bb[jn];
-      fld[1][jn] = l0 * vu[0] + l1 * vu[1] + l2 * vu[2];
-      fld[2][jn] = l0 * vv[0] + l1 * vv[1] + l2 * vv[2];
+      for (int jn = 0; jn < NP; ++jn) {
+        const T l0 = bary[4 * jn], l1 = bary[4 * jn + 1], l2 = bary[4 * jn + 2];
+        fld[0][jn] = u0[0] + (l0 * Sh[0] + l1 * Sh[1] + l2 * Sh[2]) + (bb[jn] - Bbar);
+        fld[1][jn] = u0[1] + (l0 * Su[0] + l1 * Su[1] + l2 * Su[2]);
+        fld[2][jn] = u0[2] + (l0 * Sv[0] + l1 * Sv[1] + l2 * Sv[2]);
+      }
+    } else {
+#pragma unroll
+      for (int jn = 0; jn < NP; ++jn) {
+        const T l0 = bary[4 * jn], l1 = bary[4 * jn + 1], l2 = bary[4 * jn + 2];
+        fld[0][jn] = l0 * vh[0] + l1 * vh[1] + l2 * vh[2] + bb[jn];
+        fld[1][jn] = l0 * vu[0] + l1 * vu[1] + l2 * vu[2];
+        fld[2][jn] = l0 * vv[0] + l1 * vv[1] + l2 * vv[2];
+      }
     }
     store_nodes<T, NP, NPP>(q + eo, ks, fld[0]);
     store_nodes<T, NP, NPP>(q + fstride + eo, ks, fld[1]);
     store_nodes<T, NP, NPP>(q + 2 * fstride + eo, ks, fld[2]);
   }
+}
+
+// Elements e0, e0 + step, ... below e1 of the TVB limiter. Out of line: the
+// separate launch and the persistent batch kernel then run one compiled copy of its
+// arithmetic (its many short multiply-add chains were rounded differently when it
+// was inlined into the two kernels), at no measured cost.
+template <typename T, int N>
+__device__ __noinline__ void tvb_range(const LimitParams<T>& __restrict__ p, const T* __restrict__ sops, int e0,
+                                       int step, int e1, long long k) {
+  for (int e = e0; e < e1; e += step) tvb_element<T, N>(p, sops, e, k);
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_tvb(const __grid_constant__ LimitParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sops = reinterpret_cast<T*>(smem_raw);
+  stage_ops<T, N, OpLayout<N>::TAIL>(sops, p.s.ops);
+  const long long k = (*p.s.macro) * (1LL << (p.sc.L - 1)) + p.j;
+  tvb_range<T, N>(p, sops, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, p.nactive, k);
 }
 
 }  // namespace swe

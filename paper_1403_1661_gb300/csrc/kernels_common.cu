@@ -374,4 +374,21 @@ cudaError_t launch_stats_finalize(const double* partials, int nblocks, double* o
   return cudaGetLastError();
 }
 
+// After a persistent batch kernel: the macro counters of the scenarios that
+// completed advance by their macro steps of the call.
+template <typename T>
+__global__ void k_batch_finish(const __grid_constant__ BatchLaunch<T> bl, const int* n_macro) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < bl.nscn && bl.status[i] == 0) *bl.scn[i].s.macro += n_macro[i];
+}
+
+template <typename T>
+cudaError_t launch_batch_finish(const BatchLaunch<T>& bl, const int* n_macro, cudaStream_t st) {
+  k_batch_finish<T><<<1, kBatchMaxScn, 0, st>>>(bl, n_macro);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_batch_finish<float>(const BatchLaunch<float>&, const int*, cudaStream_t);
+template cudaError_t launch_batch_finish<double>(const BatchLaunch<double>&, const int*, cudaStream_t);
+
 }  // namespace swe

@@ -18,6 +18,8 @@ struct KernelCfg {
   int smem_tc = 0, grid_tc = 0;   // tensor-core stage kernel (FP32 only)
   int grid_stage_g = 0;           // stage kernel with the operators in global memory
   int grid_split_t = 0, grid_split_v = 0, grid_split_s = 0;   // kernel-split ablation
+  int smem_batch = 0, occ_batch = 0;         // persistent batch kernel, SIMT body
+  int smem_batch_tc = 0, occ_batch_tc = 0;   // persistent batch kernel, tensor-core body (FP32)
 };
 
 template <typename T>
@@ -36,6 +38,9 @@ struct Launchers {
   cudaError_t (*stage_global_ops)(const StageParams<T>&, const KernelCfg&, cudaStream_t);
   cudaError_t (*split_rhs)(const StageParams<T>&, T* qg, T* rg, const KernelCfg&, cudaStream_t);
   int split_planes;
+  // Persistent batch kernel over a group of scenarios of this order (tc: the
+  // tensor-core stage body, FP32 only), grid CTAs.
+  cudaError_t (*batch)(const BatchLaunch<T>& bl, bool tc, int grid, const KernelCfg&, cudaStream_t);
 };
 
 // Registered per order by kernels_n*.cu; nullptr when the order is not built.
@@ -57,6 +62,11 @@ template <typename T>
 cudaError_t launch_unpack_state(const T* q, const double* Bc, const int* iperm, const Sched& sc,
                                 long long k, int Np, double* x, cudaStream_t st);
 cudaError_t launch_stats_finalize(const double* partials, int nblocks, double* out, cudaStream_t st);
+
+// After a persistent batch kernel: advance the macro counters of the scenarios that
+// completed by n_macro (device, per scenario).
+template <typename T>
+cudaError_t launch_batch_finish(const BatchLaunch<T>& bl, const int* n_macro, cudaStream_t st);
 
 // Level regrouping on the device (re-interpolated history, then every per-element
 // array gathered into the new order; pi: new index -> old index, sigma: old -> new).

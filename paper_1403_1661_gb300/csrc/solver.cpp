@@ -162,15 +162,37 @@ struct swe_solver {
   swe::KernelCfg cfg_max;   // occupancy limits (set_launch_config caps below these)
 };
 
+// One persistent kernel's scenarios: the same precision tier and scheme code.
+struct BatchGroup {
+  bool fp64 = false, tc = false;
+  int code = 0;
+  std::vector<int> idx;              // solvers of the batch in this group
+  size_t off_ctl = 0, off_segs = 0, off_cnt = 0, off_release = 0, off_nmacro = 0, off_segof = 0;
+  int seg_cap = 0;
+  int ticket_cap = 0;
+  std::vector<int> seg_of;           // host copy of this call's ticket -> segment table
+  int grid = 0;
+  cudaStream_t stream = nullptr;     // its branch of the captured graph
+  cudaEvent_t join = nullptr;
+  std::vector<swe::BatchSeg> segs;   // host copy of this call's ticket segments
+};
+
 struct swe_batch {
   std::vector<swe_solver*> solvers;
   cudaStream_t stream = nullptr;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  int max_macro = 1;
+  double wait_s = 10.0;
+  std::vector<BatchGroup> groups;
+  std::vector<int32_t> hold;          // per solver: withhold its release
+  std::vector<int32_t> last_nmacro;   // the segment tables were built for these
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t fork = nullptr, done = nullptr;
-  std::vector<cudaEvent_t> join;
-  std::vector<int> launches;
-  std::vector<int64_t> dofs;
-  std::vector<uint64_t> versions;   // each solver's sched_version at capture
+  std::vector<cudaEvent_t> join;      // per solver: work queued on its own stream
+  std::vector<int64_t> dofs;          // per solver: DOF updates of one macro step
+  std::vector<uint64_t> versions;     // each solver's sched_version at creation
+  int64_t launches = 0;               // kernels this batch has launched
 };
 
 namespace {
@@ -1615,54 +1637,246 @@ int swe_set_open_faces(swe_solver* s, const uint8_t* open) {
   return upload_mesh(s);
 }
 
-int swe_batch_create(swe_solver* const* solvers, int32_t n, void* stream, swe_batch** out) {
-  if (!solvers || n < 1 || !out) return fail(SWE_EINVAL, "bad arguments");
+// ---- persistent batched launch --------------------------------------------
+
+extern "C++" {
+namespace {
+
+int batch_period(const swe_solver* s) { return 1 << (s->L - 1); }
+
+bool batch_tvb(const swe_solver* s) { return (s->prm.limiter_mask & SWE_LIM_TVB) != 0; }
+
+// tickets of one phase: tiles of kBatchStageTile elements (stage) or kBatchTvbTile (TVB)
+int batch_tiles(int nactive, int kind) {
+  const int t = kind == 0 ? swe::kBatchStageTile : swe::kBatchTvbTile;
+  return (nactive + t - 1) / t;
+}
+
+// tickets of one macro step of a solver
+int batch_tickets_per_macro(const swe_solver* s) {
+  int n = 0;
+  for (int j = 0; j < batch_period(s); ++j) {
+    const int na = s->off[active_levels(s, j)];
+    n += batch_tiles(na, 0) + (batch_tvb(s) ? batch_tiles(na, 1) : 0);
+  }
+  return n;
+}
+
+// Group the solvers by precision tier and scheme code, at most kBatchMaxScn per group.
+std::vector<BatchGroup> batch_groups(swe_solver* const* solvers, int n) {
+  std::vector<BatchGroup> gs;
+  for (int i = 0; i < n; ++i) {
+    const swe_solver* s = solvers[i];
+    BatchGroup* g = nullptr;
+    for (BatchGroup& c : gs)
+      if (c.fp64 == s->fp64 && c.tc == s->tc && c.code == s->code && (int)c.idx.size() < swe::kBatchMaxScn) g = &c;
+    if (!g) {
+      gs.emplace_back();
+      g = &gs.back();
+      g->fp64 = s->fp64;
+      g->tc = s->tc;
+      g->code = s->code;
+    }
+    g->idx.push_back(i);
+  }
+  return gs;
+}
+
+// Workspace layout of the batch (each section 256-byte aligned): per group the
+// control block, the ticket segments (capacity for max_macro macro steps of every
+// scenario), the counters done / ran / status (one int each per scenario), the
+// release flags and the macro steps of the call.
+size_t batch_layout(std::vector<BatchGroup>& gs, swe_solver* const* solvers, int max_macro) {
+  size_t off = 0;
+  for (BatchGroup& g : gs) {
+    int cap = 0, tcap = 0;
+    for (int i : g.idx) {
+      cap += max_macro * batch_period(solvers[i]) * (batch_tvb(solvers[i]) ? 2 : 1);
+      tcap += max_macro * batch_tickets_per_macro(solvers[i]);
+    }
+    g.seg_cap = cap;
+    g.ticket_cap = tcap;
+    const size_t n = g.idx.size();
+    g.off_ctl = off;
+    off = align256(off + sizeof(swe::BatchCtl));
+    g.off_segs = off;
+    off = align256(off + (size_t)cap * sizeof(swe::BatchSeg));
+    g.off_cnt = off;
+    off = align256(off + 3 * n * sizeof(int));
+    g.off_release = off;
+    off = align256(off + n * sizeof(int));
+    g.off_nmacro = off;
+    off = align256(off + n * sizeof(int));
+    g.off_segof = off;
+    off = align256(off + (size_t)tcap * sizeof(int));
+  }
+  return off;
+}
+
+// Ticket segments of one call: the phases of every scenario (per macro step and
+// finest substep: the stage kernel, then the TVB limiter), ordered phase by phase,
+// round-robin over the scenarios, each after the tickets of its scenario's earlier
+// phases.
+void batch_segments(BatchGroup& g, const std::vector<swe_solver*>& solvers, const int32_t* nmacro) {
+  g.segs.clear();
+  const int n = (int)g.idx.size();
+  std::vector<int> nph(n), need(n, 0);
+  int maxp = 0;
+  for (int a = 0; a < n; ++a) {
+    const swe_solver* s = solvers[g.idx[a]];
+    nph[a] = nmacro[g.idx[a]] * batch_period(s) * (batch_tvb(s) ? 2 : 1);
+    maxp = std::max(maxp, nph[a]);
+  }
+  int t0 = 0;
+  for (int ph = 0; ph < maxp; ++ph)
+    for (int a = 0; a < n; ++a) {
+      if (ph >= nph[a]) continue;
+      const swe_solver* s = solvers[g.idx[a]];
+      const int per = batch_period(s), kinds = batch_tvb(s) ? 2 : 1;
+      const int step = ph / kinds;   // substeps since the start of the call
+      const int j = step % per;
+      swe::BatchSeg sg;
+      std::memset(&sg, 0, sizeof(sg));
+      sg.t0 = t0;
+      sg.nactive = s->off[active_levels(s, j)];
+      sg.kind = ph % kinds;
+      sg.ntiles = batch_tiles(sg.nactive, sg.kind);
+      sg.need = need[a];
+      sg.scn = a;
+      sg.j = j;
+      sg.kofs = step;
+      sg.first = ph == 0 ? 1 : 0;
+      need[a] += sg.ntiles;
+      t0 += sg.ntiles;
+      g.segs.push_back(sg);
+    }
+  g.seg_of.resize(t0);
+  for (size_t q = 0; q < g.segs.size(); ++q)
+    for (int t = 0; t < g.segs[q].ntiles; ++t) g.seg_of[g.segs[q].t0 + t] = (int)q;
+}
+
+template <typename T>
+swe::BatchLaunch<T> batch_params(const swe_batch* b, const BatchGroup& g) {
+  swe::BatchLaunch<T> bl;
+  std::memset(&bl, 0, sizeof(bl));
+  for (size_t a = 0; a < g.idx.size(); ++a) {
+    swe_solver* s = b->solvers[g.idx[a]];
+    bl.scn[a].s = dev_state<T>(s);
+    bl.scn[a].sc = sched_of(s);
+    bl.scn[a].ph = phys_of(s, s->prm.limiter_mask);
+    bl.period[a] = batch_period(s);
+  }
+  const size_t n = g.idx.size();
+  bl.segs = reinterpret_cast<const swe::BatchSeg*>(b->ws + g.off_segs);
+  bl.seg_of = reinterpret_cast<const int*>(b->ws + g.off_segof);
+  bl.ctl = reinterpret_cast<swe::BatchCtl*>(b->ws + g.off_ctl);
+  bl.done = reinterpret_cast<int*>(b->ws + g.off_cnt);
+  bl.ran = bl.done + n;
+  bl.status = bl.done + 2 * n;
+  bl.release = reinterpret_cast<const int*>(b->ws + g.off_release);
+  bl.nscn = (int)n;
+  return bl;
+}
+
+template <typename T>
+cudaError_t batch_enqueue_group(swe_batch* b, const BatchGroup& g) {
+  const swe_solver* s0 = b->solvers[g.idx[0]];
+  const swe::Launchers<T>* lt;
+  if constexpr (sizeof(T) == 8) lt = s0->ld; else lt = s0->lf;
+  const swe::BatchLaunch<T> bl = batch_params<T>(b, g);
+  cudaError_t e;
+  // a fresh queue: head and the per-scenario counters start at zero
+  if ((e = cudaMemsetAsync(b->ws + g.off_ctl, 0, sizeof(int), g.stream))) return e;
+  if ((e = cudaMemsetAsync(b->ws + g.off_cnt, 0, 3 * g.idx.size() * sizeof(int), g.stream))) return e;
+  if ((e = lt->batch(bl, g.tc, g.grid, s0->cfg, g.stream))) return e;
+  return swe::launch_batch_finish<T>(bl, reinterpret_cast<const int*>(b->ws + g.off_nmacro), g.stream);
+}
+
+}  // namespace
+}  // extern "C++"
+
+int swe_batch_workspace_bytes(swe_solver* const* solvers, int32_t n, int32_t max_macro, size_t* bytes) {
+  if (!solvers || n < 1 || max_macro < 1 || !bytes) return fail(SWE_EINVAL, "bad arguments");
+  for (int i = 0; i < n; ++i)
+    if (!solvers[i] || !solvers[i]->have_state || !(solvers[i]->dt_min > 0))
+      return fail(SWE_EINVAL, "every solver needs state and levels");
+  std::vector<BatchGroup> gs = batch_groups(solvers, n);
+  *bytes = batch_layout(gs, solvers, max_macro);
+  return SWE_OK;
+}
+
+int swe_batch_create(swe_solver* const* solvers, int32_t n, int32_t max_macro, void* dev_workspace, size_t bytes,
+                     void* stream, swe_batch** out) {
+  if (!solvers || n < 1 || max_macro < 1 || !out) return fail(SWE_EINVAL, "bad arguments");
   *out = nullptr;
   for (int i = 0; i < n; ++i) {
     swe_solver* s = solvers[i];
     if (!s || !s->have_state || !(s->dt_min > 0)) return fail(SWE_EINVAL, "every solver needs state and levels");
     if (!synchronous(s)) return fail(SWE_EINVAL, "every solver must be level-synchronous");
     if (!s->stream) return fail(SWE_EINVAL, "batched solvers need their own (non-default) streams");
+    for (int j = 0; j < i; ++j)
+      if (solvers[j] == s) return fail(SWE_EINVAL, "a solver appears twice in the batch");
   }
+  if (!stream) return fail(SWE_EINVAL, "the batch needs a non-default stream");
+  if (!dev_workspace || (reinterpret_cast<uintptr_t>(dev_workspace) & 255))
+    return fail(SWE_EINVAL, "the batch workspace must be 256-byte aligned device memory");
   std::unique_ptr<swe_batch> b(new (std::nothrow) swe_batch);
   if (!b) return fail(SWE_ENOMEM, "host allocation failed");
   b->solvers.assign(solvers, solvers + n);
   b->stream = reinterpret_cast<cudaStream_t>(stream);
-  if (!b->stream) return fail(SWE_EINVAL, "the batch needs a non-default stream");
+  b->max_macro = max_macro;
+  b->groups = batch_groups(solvers, n);
+  const size_t need = batch_layout(b->groups, solvers, max_macro);
+  if (bytes < need) return fail(SWE_ENOMEM, "batch workspace smaller than swe_batch_workspace_bytes");
+  b->ws = static_cast<char*>(dev_workspace);
+  b->ws_bytes = bytes;
+  b->hold.assign(n, 0);
+  b->dofs.assign(n, 0);
+  for (int i = 0; i < n; ++i) {
+    swe_solver* s = solvers[i];
+    for (int j = 0; j < batch_period(s); ++j) b->dofs[i] += substep_dofs(s, j);
+    b->versions.push_back(s->sched_version);
+  }
+  // grids: every group's kernel is given as many CTAs as fit on the GPU; the groups
+  // run side by side and the hardware places their CTAs as room frees up. A CTA takes
+  // tickets only while it is resident, so one that starts late takes fewer, and no
+  // group is held to a share that leaves SMs idle once the others are done.
+  int dev = 0, nsm = 0;
+  SWE_CUDA(cudaGetDevice(&dev));
+  SWE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    BatchGroup& g = b->groups[gi];
+    const swe_solver* s0 = solvers[g.idx[0]];
+    const int occ = g.tc ? s0->cfg_max.occ_batch_tc : s0->cfg_max.occ_batch;
+    if (occ < 1) return fail(SWE_ECUDA, "the batch kernel does not fit on an SM");
+    g.grid = occ * nsm;
+    SWE_CUDA(cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking));
+    SWE_CUDA(cudaEventCreateWithFlags(&g.join, cudaEventDisableTiming));
+  }
   SWE_CUDA(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
   SWE_CUDA(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming));
   b->join.resize(n, nullptr);
   for (int i = 0; i < n; ++i) SWE_CUDA(cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming));
-  b->launches.assign(n, 0);
-  b->dofs.assign(n, 0);
-  for (int32_t i = 0; i < n; ++i) b->versions.push_back(solvers[i]->sched_version);
-  // one macro step of every solver, each on its own stream: parallel graph branches
-  cudaGraph_t g = nullptr;
+  // the captured step: per group (a parallel branch) fresh counters, the persistent
+  // kernel and the macro-counter update
+  cudaGraph_t graph = nullptr;
   SWE_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-  int rc = SWE_OK;
   cudaError_t ce = cudaEventRecord(b->fork, b->stream);
-  for (int i = 0; i < n && rc == SWE_OK && ce == cudaSuccess; ++i) {
-    swe_solver* s = b->solvers[i];
-    ce = cudaStreamWaitEvent(s->stream, b->fork, 0);
-    const int period = 1 << (s->L - 1);
-    for (int j = 0; j < period && ce == cudaSuccess; ++j) {
-      int nl = enqueue_substep(s, j);
-      if (nl < 0) { rc = nl; break; }
-      b->launches[i] += nl;
-      b->dofs[i] += substep_dofs(s, j);
-    }
-    if (rc == SWE_OK && ce == cudaSuccess) ce = cudaEventRecord(b->join[i], s->stream);
-    if (rc == SWE_OK && ce == cudaSuccess) ce = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+  for (size_t gi = 0; gi < b->groups.size() && ce == cudaSuccess; ++gi) {
+    BatchGroup& g = b->groups[gi];
+    ce = cudaStreamWaitEvent(g.stream, b->fork, 0);
+    if (ce == cudaSuccess) ce = g.fp64 ? batch_enqueue_group<double>(b.get(), g) : batch_enqueue_group<float>(b.get(), g);
+    if (ce == cudaSuccess) ce = cudaEventRecord(g.join, g.stream);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(b->stream, g.join, 0);
   }
-  cudaError_t ce2 = cudaStreamEndCapture(b->stream, &g);
-  if (rc != SWE_OK) { if (g) cudaGraphDestroy(g); swe_batch_destroy(b.release()); return rc; }
+  cudaError_t ce2 = cudaStreamEndCapture(b->stream, &graph);
   if (ce != cudaSuccess || ce2 != cudaSuccess) {
-    if (g) cudaGraphDestroy(g);
+    if (graph) cudaGraphDestroy(graph);
     swe_batch_destroy(b.release());
     return fail(SWE_ECUDA, std::string("batch capture: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
   }
-  ce = cudaGraphInstantiate(&b->graph, g, 0);
-  cudaGraphDestroy(g);
+  ce = cudaGraphInstantiate(&b->graph, graph, 0);
+  cudaGraphDestroy(graph);
   if (ce != cudaSuccess) {
     b->graph = nullptr;
     swe_batch_destroy(b.release());
@@ -1672,26 +1886,106 @@ int swe_batch_create(swe_solver* const* solvers, int32_t n, void* stream, swe_ba
   return SWE_OK;
 }
 
-int swe_batch_step(swe_batch* b, int32_t n_macro) {
-  if (!b || n_macro < 0) return fail(SWE_EINVAL, "bad arguments");
-  if (n_macro == 0) return SWE_OK;
-  for (size_t i = 0; i < b->solvers.size(); ++i)
-    if (b->solvers[i]->sched_version != b->versions[i])
-      return fail(SWE_EINVAL, "a solver's levels or launch shape changed since swe_batch_create");
+int swe_batch_set_wait_limit(swe_batch* b, double seconds) {
+  if (!b || !(seconds > 0.0) || !(seconds < 3600.0)) return fail(SWE_EINVAL, "wait limit must be in (0, 3600) s");
+  b->wait_s = seconds;
+  return SWE_OK;
+}
+
+int swe_batch_hold(swe_batch* b, int32_t i, int32_t hold) {
+  if (!b || i < 0 || i >= (int32_t)b->solvers.size()) return fail(SWE_EINVAL, "bad scenario index");
+  b->hold[i] = hold ? 1 : 0;
+  return SWE_OK;
+}
+
+int swe_batch_step(swe_batch* b, const int32_t* n_macro_each, int32_t* status_each) {
+  if (!b || !n_macro_each || !status_each) return fail(SWE_EINVAL, "bad arguments");
+  const int n = (int)b->solvers.size();
+  for (int i = 0; i < n; ++i) {
+    if (n_macro_each[i] < 0 || n_macro_each[i] > b->max_macro)
+      return fail(SWE_EINVAL, "n_macro_each outside 0..max_macro");
+    const swe_solver* s = b->solvers[i];
+    if (s->sched_version != b->versions[i])
+      return fail(SWE_EINVAL, "a solver's levels, order or boundary faces changed since swe_batch_create");
+    if (!s->have_state || !synchronous(s)) return fail(SWE_EINVAL, "a solver has no valid level-synchronous state");
+  }
+  const bool rebuild = b->last_nmacro.size() != (size_t)n ||
+                       !std::equal(b->last_nmacro.begin(), b->last_nmacro.end(), n_macro_each);
+  // this call's tables: ticket segments (when the macro steps changed), the control
+  // block, the release flags and the macro steps, uploaded on the batch stream
+  for (BatchGroup& g : b->groups) {
+    if (rebuild) {
+      batch_segments(g, b->solvers, n_macro_each);
+      if ((int)g.segs.size() > g.seg_cap || (int)g.seg_of.size() > g.ticket_cap)
+        return fail(SWE_EINVAL, "internal: ticket table overflow");
+      if (!g.segs.empty()) {
+        SWE_CUDA(cudaMemcpyAsync(b->ws + g.off_segs, g.segs.data(), g.segs.size() * sizeof(swe::BatchSeg),
+                                 cudaMemcpyHostToDevice, b->stream));
+        SWE_CUDA(cudaMemcpyAsync(b->ws + g.off_segof, g.seg_of.data(), g.seg_of.size() * sizeof(int),
+                                 cudaMemcpyHostToDevice, b->stream));
+      }
+    }
+    swe::BatchCtl ctl;
+    std::memset(&ctl, 0, sizeof(ctl));
+    ctl.total = g.segs.empty() ? 0 : g.segs.back().t0 + g.segs.back().ntiles;
+    ctl.nseg = (int)g.segs.size();
+    ctl.wait_ns = (long long)(b->wait_s * 1e9);
+    SWE_CUDA(cudaMemcpyAsync(b->ws + g.off_ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, b->stream));
+    std::vector<int> rel(g.idx.size()), nm(g.idx.size());
+    for (size_t a = 0; a < g.idx.size(); ++a) {
+      rel[a] = b->hold[g.idx[a]] ? 0 : 1;
+      nm[a] = n_macro_each[g.idx[a]];
+    }
+    SWE_CUDA(cudaMemcpyAsync(b->ws + g.off_release, rel.data(), rel.size() * sizeof(int), cudaMemcpyHostToDevice,
+                             b->stream));
+    SWE_CUDA(cudaMemcpyAsync(b->ws + g.off_nmacro, nm.data(), nm.size() * sizeof(int), cudaMemcpyHostToDevice,
+                             b->stream));
+  }
+  b->last_nmacro.assign(n_macro_each, n_macro_each + n);
   // the batch stream waits for work already queued on the solvers' own streams
-  for (size_t i = 0; i < b->solvers.size(); ++i) {
+  for (int i = 0; i < n; ++i) {
     SWE_CUDA(cudaEventRecord(b->join[i], b->solvers[i]->stream));
     SWE_CUDA(cudaStreamWaitEvent(b->stream, b->join[i], 0));
   }
-  for (int32_t r = 0; r < n_macro; ++r) SWE_CUDA(cudaGraphLaunch(b->graph, b->stream));
-  SWE_CUDA(cudaEventRecord(b->done, b->stream));
-  for (size_t i = 0; i < b->solvers.size(); ++i) {
-    swe_solver* s = b->solvers[i];
-    SWE_CUDA(cudaStreamWaitEvent(s->stream, b->done, 0));
-    s->k += (int64_t)n_macro << (s->L - 1);
-    s->dof_updates += b->dofs[i] * n_macro;
-    s->launches += (int64_t)b->launches[i] * n_macro;
+  SWE_CUDA(cudaGraphLaunch(b->graph, b->stream));
+  b->launches += 2 * (int64_t)b->groups.size();
+  // per scenario: status and tiles run, read back when the step is over
+  std::vector<std::vector<int>> host(b->groups.size());
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    host[gi].resize(3 * b->groups[gi].idx.size());
+    SWE_CUDA(cudaMemcpyAsync(host[gi].data(), b->ws + b->groups[gi].off_cnt, host[gi].size() * sizeof(int),
+                             cudaMemcpyDeviceToHost, b->stream));
   }
+  SWE_CUDA(cudaEventRecord(b->done, b->stream));
+  SWE_CUDA(cudaStreamSynchronize(b->stream));
+  int rc = SWE_OK;
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    const BatchGroup& g = b->groups[gi];
+    const size_t m = g.idx.size();
+    for (size_t a = 0; a < m; ++a) {
+      const int i = g.idx[a];
+      swe_solver* s = b->solvers[i];
+      const int st = host[gi][2 * m + a], ran = host[gi][m + a];
+      status_each[i] = st;
+      if (st == SWE_OK) {
+        s->k += (int64_t)n_macro_each[i] << (s->L - 1);
+        s->dof_updates += b->dofs[i] * n_macro_each[i];
+      } else {
+        rc = st;
+        // gave up before any of its tiles ran: its state is as before the call;
+        // otherwise part of a macro step ran and the state must be set again
+        if (ran > 0) s->have_state = false;
+      }
+    }
+  }
+  for (int i = 0; i < n; ++i) SWE_CUDA(cudaStreamWaitEvent(b->solvers[i]->stream, b->done, 0));
+  if (rc != SWE_OK) return fail(rc, "a scenario's bounded wait gave up (status_each)");
+  return SWE_OK;
+}
+
+int swe_batch_launches(const swe_batch* b, int64_t* launches) {
+  if (!b || !launches) return fail(SWE_EINVAL, "NULL argument");
+  *launches = b->launches;
   return SWE_OK;
 }
 
@@ -1703,6 +1997,13 @@ void swe_batch_destroy(swe_batch* b) {
   if (b->done) cudaEventDestroy(b->done);
   for (cudaEvent_t e : b->join)
     if (e) cudaEventDestroy(e);
+  for (BatchGroup& g : b->groups) {
+    if (g.stream) {
+      cudaStreamSynchronize(g.stream);
+      cudaStreamDestroy(g.stream);
+    }
+    if (g.join) cudaEventDestroy(g.join);
+  }
   delete b;
 }
 

@@ -45,6 +45,62 @@ def test_batch_graph_equals_solvers_alone(precision):
     b.close()
 
 
+def test_batch_uneven_macro_counts_equal_alone():
+    """One batch step advances each scenario by its own number of macro steps
+    (n_macro_each = 0, 1, 2, 3): every result equals the same solver stepped alone
+    that many macro steps, bit for bit, and a count of 0 leaves a solver untouched."""
+    import paper_1403_1661_gb300 as P
+    counts = [2, 0, 3, 1]
+    alone = [P.solver_from_scenario(s, precision="fp32tc") for s in _mix()]
+    mixed = [P.solver_from_scenario(s, precision="fp32tc") for s in _mix()]
+    for s, c in zip(alone, counts):
+        if c:
+            s.step(c)
+    b = P.Batch(mixed, max_macro=3)
+    st = b.step(counts)
+    assert (st == 0).all()
+    for a, m in zip(alone, mixed):
+        xa, xm = a.get_state(), m.get_state()
+        for u, v in zip(xa[:3], xm[:3]):
+            assert np.array_equal(u, v)
+        assert xa[3] == xm[3]
+        assert a.stats()["dof_updates"] == m.stats()["dof_updates"]
+    assert b.launches() == 2 * 3   # two kernels per (tier, order) group: N = 3, 4, 2
+    b.close()
+
+
+def test_batch_held_scenario_times_out_and_the_rest_complete():
+    """The bounded device wait: scenario 1's release is withheld (swe_batch_hold), so
+    its first phase waits until the 50 ms wait limit and gives up; the step reports
+    SWE_ETIMEOUT for it alone, its state and time are untouched, the other scenarios
+    complete and equal their solvers run alone. Released again, it steps normally.
+    Nothing faults: the kernel's wait ends on a time bound and it returns."""
+    import paper_1403_1661_gb300 as P
+    from paper_1403_1661_gb300 import _native as nat
+    alone = [P.solver_from_scenario(s, precision="fp32tc") for s in _mix()]
+    mixed = [P.solver_from_scenario(s, precision="fp32tc") for s in _mix()]
+    before = mixed[1].get_state()
+    b = P.Batch(mixed, max_macro=2)
+    b.set_wait_limit(0.05)
+    b.hold(1)
+    st = b.step(2, check=False)
+    assert st.tolist() == [0, nat.SWE_ETIMEOUT, 0, 0]
+    after = mixed[1].get_state()
+    for u, v in zip(before, after):
+        assert np.array_equal(np.asarray(u), np.asarray(v))
+    for i in (0, 2, 3):
+        alone[i].step(2)
+        for u, v in zip(alone[i].get_state()[:3], mixed[i].get_state()[:3]):
+            assert np.array_equal(u, v)
+    b.hold(1, False)
+    st = b.step([0, 2, 0, 0])
+    assert (st == 0).all()
+    alone[1].step(2)
+    for u, v in zip(alone[1].get_state()[:3], mixed[1].get_state()[:3]):
+        assert np.array_equal(u, v)
+    b.close()
+
+
 def test_served_results_equal_alone():
     import paper_1403_1661_gb300 as P
     from paper_1403_1661_gb300.serve import GpuFactory, Request, Server
