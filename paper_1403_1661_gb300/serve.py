@@ -8,7 +8,9 @@ keeps its state and Adams-Bashforth history resident in its own workspace and
 advances on its own CUDA stream a few macro steps at a time (graph replays), so
 the work of all running requests overlaps on the GPU. Finished requests return
 their state to the host and free their memory immediately, which admits the next
-ones. Latency is completion time minus arrival time.
+ones. Latency is completion time minus arrival time. Optionally (GpuFactory's
+regroup_every) each solve is regrouped into CFL levels every few macro steps, the
+remedy Section 4 gives for levels that no longer fit the state.
 
 Solves never interact (no shared buffers, deterministic kernels), so a result
 does not depend on what else is running.
@@ -52,12 +54,21 @@ class Request:
 
 
 class GpuFactory:
-    """Builds real solvers (used by the server; tests may pass a fake)."""
+    """Builds real solvers (used by the server; tests may pass a fake).
 
-    def __init__(self, precision="fp32tc", keep_state=False, tuned=None):
+    regroup_every: every this many macro steps (0: never) a running solve is
+    regrouped into MRAB levels by the CFL rule at its current state (Section 4:
+    elements may be regrouped every few steps), keeping its history; if an
+    element's CFL step has fallen below the finest step dt_min, the solve restarts
+    its levels from its current state instead (a new dt_min, history from AB1). A
+    solve whose shoreline layers speed up then stays within its CFL bound instead of
+    outrunning the levels it was given at t = 0."""
+
+    def __init__(self, precision="fp32tc", keep_state=False, tuned=None, regroup_every=0):
         self.precision = precision
         self.keep_state = keep_state
         self.tuned = tuned or {}
+        self.regroup_every = int(regroup_every)
 
     def prepare(self, req):
         from .solver import Mesh, scenario_inputs
@@ -100,11 +111,34 @@ class _GpuJob:
         self.s.set_state(h, hu, hv)
         L = int(np.max(lev))
         self.macro_period = 2 ** (L - 1)
+        self.substeps_left = int(req.substeps)   # finest substeps still to take
         self.event = torch.cuda.Event()
         self.pending = False
+        self.since_regroup = 0      # macro steps since the last regroup
+        self.since_restart = 0      # macro steps since the levels were last set up
+        self.regroups = 0
+        self.restarts = 0
+
+    def remaining_macro(self):
+        return -(-self.substeps_left // self.macro_period)
 
     def step(self, n):
+        every = self.factory.regroup_every
+        # a regroup needs three Adams-Bashforth values of every level since the last restart
+        if every and self.since_regroup >= every and self.since_restart >= 3:
+            _, margin = self.s.regroup()
+            self.regroups += 1
+            self.since_regroup = 0
+            if margin < 1.0:
+                self.s.setup_levels()
+                self.restarts += 1
+                self.since_restart = 0
+                self.macro_period = 2 ** (self.s.level_info()[0] - 1)
+            n = min(n, self.remaining_macro())
         self.s.step(n)
+        self.substeps_left -= n * self.macro_period
+        self.since_regroup += n
+        self.since_restart += n
         self.event.record(self.s.stream)
         self.pending = True
 
@@ -231,6 +265,8 @@ class Server:
                         used -= r.bytes
                         end(r, "cancelled")
                         continue
+                    if hasattr(job, "remaining_macro"):   # the job counts its own substeps
+                        rem = item[2] = job.remaining_macro()
                     check = rem == 0 or (self.health_every > 0 and rounds > 0 and rounds % self.health_every == 0)
                     if check and not getattr(job, "healthy", lambda: True)():
                         job.abort()

@@ -15,7 +15,12 @@ import pytest
 from oracle import problem
 from oracle.mrab import MRAB
 from oracle.swe import SWEModel
-from tests.test_gpu_parity import TOL_R, TOL_STATE, _rhs_case
+from tests.test_gpu_parity import _rhs_case
+
+# bounds frozen at about ten times the errors observed on GB300 (the design notes list
+# them): R per field relative to max|R| over N = 2..4; the limited ten-step run's states
+TOL_R_FF = {"fp64": 6e-13, "fp32": 2e-5, "fp32tc": 2.1e-4}
+TOL_STATE_FF = {"fp64": 1e-13, "fp32": 1.1e-5, "fp32tc": 1.1e-5}
 from workloads import meshes, scenarios as sc
 
 pytestmark = pytest.mark.gpu
@@ -61,7 +66,7 @@ def test_farfield_rhs_matches_oracle(N, precision):
     R_g = s.rhs().cpu().numpy().astype(np.float64)
     errs = [np.abs(R_g[c] - R_o[c]).max() / np.abs(R_o[c]).max() for c in range(3)]
     print(f"PARITY far-field rhs N={N} {precision} " + " ".join(f"{e:.3e}" for e in errs), flush=True)
-    assert max(errs) < TOL_R[precision]
+    assert max(errs) < TOL_R_FF[precision]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32tc"])
@@ -78,7 +83,7 @@ def test_farfield_free_stream(precision):
     om = Mesh(vx, vy, E)
     scale = 9.81 * 1.3 ** 2 * max(np.abs(om.rx).max(), np.abs(om.sy).max())
     print(f"PARITY far-field free stream {precision} rel={np.abs(R).max() / scale:.3e}", flush=True)
-    assert np.abs(R).max() < {"fp64": 1e-13, "fp32": 1e-5, "fp32tc": 1e-3}[precision] * scale
+    assert np.abs(R).max() < {"fp64": 6e-15, "fp32": 2.2e-6, "fp32tc": 1.2e-6}[precision] * scale
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32tc"])
@@ -95,7 +100,7 @@ def test_farfield_limiters_ten_steps(precision):
     eh = np.abs(h - q[0]).max() / hmax
     em = max(np.abs(hu - q[1]).max(), np.abs(hv - q[2]).max()) / (hmax * np.sqrt(9.81 * hmax))
     print(f"PARITY far-field PP+TVB {precision} eh={eh:.3e} em={em:.3e}", flush=True)
-    assert eh < TOL_STATE[precision] and em < TOL_STATE[precision]
+    assert eh < TOL_STATE_FF[precision] and em < TOL_STATE_FF[precision]
 
 
 def _vortex(x, y, t, beta=5.0):
@@ -169,4 +174,4 @@ def test_open_faces_subset(precision):
     eh = np.abs(hg - q[0]).max() / hmax
     em = max(np.abs(hug - q[1]).max(), np.abs(hvg - q[2]).max()) / (hmax * np.sqrt(9.81 * hmax))
     print(f"PARITY open faces subset {precision} eh={eh:.3e} em={em:.3e}", flush=True)
-    assert eh < TOL_STATE[precision] and em < TOL_STATE[precision]
+    assert eh < TOL_STATE_FF[precision] and em < TOL_STATE_FF[precision]

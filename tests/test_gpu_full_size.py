@@ -20,8 +20,11 @@ from workloads import scenarios as sc
 
 pytestmark = pytest.mark.gpu
 
-TOL_R = 2e-4        # same bounds as tests/test_gpu_parity.py for the tensor-core tier
-TOL_STATE = 8e-5
+# R per field relative to max|R| (the tier's derived bound; observed 4.3e-5 at this
+# size and depth); one macro step: depth relative to max h, momentum relative to
+# max h sqrt(g max h), free surface in metres (about ten times the observed errors)
+TOL_R = 2e-4
+TOL_STEP_H, TOL_STEP_M, TOL_STEP_ETA = 4e-7, 1.2e-10, 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -69,7 +72,8 @@ def test_full_size_macro_step_matches_oracle(full):
     print(f"PARITY full-size macro step fp32tc eh={eh / hmax:.3e} em={em / (hmax * np.sqrt(9.81 * hmax)):.3e} "
           f"deta={deta:.3e} m (wave amplitude 2 m)", flush=True)
     assert np.isfinite(h).all() and h.min() >= -1e-6
-    assert eh < TOL_STATE * hmax and em < TOL_STATE * hmax * np.sqrt(9.81 * hmax)
+    assert eh < TOL_STEP_H * hmax and em < TOL_STEP_M * hmax * np.sqrt(9.81 * hmax)
+    assert deta < TOL_STEP_ETA
 
 
 @pytest.mark.parametrize("scheme", ["collocation", "cubature_2n"])

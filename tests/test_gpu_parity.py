@@ -1,16 +1,14 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
-Tolerances (derived from the arithmetic; see the design notes):
-* FP64 tier: every output within 1e-11 of the oracle, relative to the field's
-  max-norm (the two sides differ only in rounding order and in the pre-balanced
-  rewrite of the momentum flux, both O(1e-16) per operation over O(10^3) operations).
-* FP32 tier: R within 2e-5 of max|R| per field (single-precision rounding of the
-  state, bed and operators, amplified by the ~Np*Ncub-term contractions); states
-  after T steps within 2e-5 max(h) (depth) and 2e-5 max(h) sqrt(g max h) (momentum)
-  on smooth configurations.
-* FP32 tensor-core tier (split-BF16 products): each product carries a relative
-  error of about 3 * 2^-16; R within 2e-4 of max|R|, states within 8e-5 of the
-  FP32 scales (four times the FP32 bounds).
+Bounds: first derived from the arithmetic -- FP64 1e-11 relative per field; FP32 R
+within 2e-5 of max|R| (single-precision rounding of the state, bed and operators,
+amplified by the ~Np*Ncub-term contractions), states within 2e-5 max(h) (depth) and
+2e-5 max(h) sqrt(g max h) (momentum); FP32 tensor cores (split-BF16 products,
+relative error about 3 * 2^-16 each) R within 2e-4, states within 8e-5 -- then
+tightened to about ten times the largest error observed on GB300 per tier,
+configuration and order and frozen (the observed values are listed in the design
+notes). Still water over any bed gives R = 0 exactly in the
+FP32 tiers (the element reference split), so that bound is zero.
 """
 import numpy as np
 import pytest
@@ -54,8 +52,24 @@ def _rhs_case(N, precision, moving=True, bed="smooth", nx=9, ny=7, limiter_mask=
     return scn
 
 
-TOL_R = {"fp64": 1e-11, "fp32": 2e-5, "fp32tc": 2e-4}
-TOL_STATE = {"fp64": 1e-11, "fp32": 2e-5, "fp32tc": 8e-5}
+# R per field relative to max|R|, by tier and order N (observed x 10)
+TOL_R = {"fp64": {1: 2e-13, 2: 4e-13, 3: 6e-13, 4: 5e-13, 5: 5e-13},
+         "fp32": {1: 5e-6, 2: 6e-6, 3: 7e-6, 4: 6e-6, 5: 9e-6},
+         "fp32tc": {1: 9e-5, 2: 1e-4, 3: 1.5e-4, 4: 8e-5, 5: 1e-4}}
+# states: depth relative to max h, momentum relative to max h sqrt(g max h), by
+# configuration and tier (observed x 10)
+TOL_STATE = {"hump100": {"fp64": 3e-14, "fp32": 3e-8, "fp32tc": 5e-7},
+             "tsunami": {"fp64": 1.5e-13, "fp32": 4e-7, "fp32tc": 4e-7},
+             "one_element": {"fp64": 3e-14, "fp32": 1.3e-6, "fp32tc": 1.3e-6},
+             "tsunami_n1": {"fp64": 1.5e-14, "fp32tc": 3e-7}}
+TOL_R_ONE = {"fp64": 9e-13, "fp32": 5e-6, "fp32tc": 8e-5}
+# still water at eta = 0.3, relative to g (max h)^2 max|r_x|; exactly zero in FP32
+TOL_LAKE = {"fp64": 5e-15, "fp32": 0.0, "fp32tc": 0.0}
+# small dam break (branchy): L1 over all elements; max norm over the elements away
+# from the front; FP64 everywhere (observed x 10)
+DAM_SMALL_L1 = {"fp32": 1e-6, "fp32tc": 8e-7}
+DAM_SMALL_AWAY = {"fp32": 2.3e-5, "fp32tc": 3e-5}
+DAM_SMALL_FP64 = 6e-13
 
 
 @pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
@@ -68,7 +82,7 @@ def test_rhs_matches_oracle(N, precision):
     R_g = s.rhs().cpu().numpy().astype(np.float64)
     errs = [np.abs(R_g[c] - R_o[c]).max() / np.abs(R_o[c]).max() for c in range(3)]
     _report(f"rhs N={N} {precision}", e_h=errs[0], e_hu=errs[1], e_hv=errs[2])
-    assert max(errs) < TOL_R[precision]
+    assert max(errs) < TOL_R[precision][N]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32tc"])
@@ -88,10 +102,8 @@ def test_lake_at_rest(precision, bed):
     R = s.rhs().cpu().numpy()
     scale = 9.81 * 1.3 ** 2 * max(np.abs(om.rx).max(), np.abs(om.sy).max())
     _report(f"lake eta=0.3 {bed} {precision}", rel=float(np.abs(R).max() / scale))
-    # FP32: unit round-off 6e-8 times the ~Np*Ncub-term contractions (observed ~1e-6);
-    # split-BF16: 2^-16 per product instead of 2^-24
-    tol = {"fp64": 1e-13, "fp32": 1e-5, "fp32tc": 1e-3}[precision]
-    assert np.abs(R).max() < tol * scale
+    # FP32 tiers: the element reference split leaves nothing to round (exactly zero)
+    assert np.abs(R).max() <= TOL_LAKE[precision] * scale
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32tc"])
@@ -106,7 +118,7 @@ def test_hump_square_ab3_100_steps(precision):
     hmax = integ.q_end[0].max()
     _report(f"hump100 {precision}", eh=eh / hmax, em=em / (hmax * np.sqrt(9.81 * hmax)))
     assert abs(t - integ.time) < 1e-12 * integ.time
-    tol = TOL_STATE[precision]
+    tol = TOL_STATE["hump100"][precision]
     assert eh < tol * hmax and em < tol * hmax * np.sqrt(9.81 * hmax)
 
 
@@ -122,7 +134,7 @@ def test_mrab_tsunami_levels(precision):
     eh, em, _ = state_errors(s, integ)
     hmax = integ.q_end[0].max()
     _report(f"tsunami L={integ.L} {precision}", eh=eh / hmax, em=em / (hmax * np.sqrt(9.81 * hmax)))
-    tol = TOL_STATE[precision]
+    tol = TOL_STATE["tsunami"][precision]
     assert eh < tol * hmax and em < tol * hmax * np.sqrt(9.81 * hmax)
 
 
@@ -139,12 +151,34 @@ def test_dam_break_small_pp_tvb(precision):
     eh = np.abs(h - q[0]).max()
     em = max(np.abs(hu - q[1]).max(), np.abs(hv - q[2]).max())
     l1 = np.abs(h - q[0]).sum() / np.abs(q[0]).sum()
-    _report(f"dambreak {precision}", eh=eh, em=em, l1=l1, hmin=h.min())
+    # max norm away from the front: elements whose wet/dry state agrees with the
+    # oracle's, in columns of square cells more than two columns from any column where
+    # the oracle's column-mean wet/dry state changes (a front moves by decisions taken
+    # in different precisions)
+    w = ref.mean_w
+    cx = om.cx
+    dx = 20.0 / 40
+    col = np.floor(cx / dx).astype(np.int64)
+    hb_o = q[0] @ w
+    colh = np.bincount(col, weights=hb_o, minlength=40) / np.bincount(col, minlength=40)
+    wetc = colh > 1e-3
+    change = np.nonzero(wetc[1:] != wetc[:-1])[0]
+    dist = np.full(40, 99)
+    for c in change:
+        dist = np.minimum(dist, np.minimum(np.abs(np.arange(40) - c), np.abs(np.arange(40) - (c + 1))))
+    keep = (dist[col] > 2) & (((h @ w) > 1e-3) == (hb_o > 1e-3))
+    hmax = q[0].max()
+    ehk = np.abs(h - q[0])[keep].max() / hmax
+    emk = max(np.abs(hu - q[1])[keep].max(), np.abs(hv - q[2])[keep].max()) / (hmax * np.sqrt(9.81 * hmax))
+    _report(f"dambreak {precision}", eh=eh, em=em, l1=l1, hmin=h.min(), eh_away=ehk, em_away=emk,
+            kept=float(keep.mean()))
     assert h.min() >= -1e-6
+    assert keep.mean() > 0.5
     if precision == "fp64":
-        assert eh < 1e-9 and em < 1e-9
+        assert eh < DAM_SMALL_FP64 and em < DAM_SMALL_FP64
     else:
-        assert l1 < (1e-4 if precision == "fp32" else 4e-4)
+        assert l1 < DAM_SMALL_L1[precision]
+        assert ehk < DAM_SMALL_AWAY[precision] and emk < DAM_SMALL_AWAY[precision]
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp32tc"])
@@ -259,8 +293,9 @@ def test_single_element_all_walls(precision):
     eh, em, _ = state_errors(s, integ)
     hmax = integ.q_end[0].max()
     _report(f"one element {precision}", eR=e, eh=eh / hmax, em=em / (hmax * np.sqrt(9.81 * hmax)))
-    assert e < TOL_R[precision]
-    assert eh < TOL_STATE[precision] * hmax and em < TOL_STATE[precision] * hmax * np.sqrt(9.81 * hmax)
+    tol = TOL_STATE["one_element"][precision]
+    assert e < TOL_R_ONE[precision]
+    assert eh < tol * hmax and em < tol * hmax * np.sqrt(9.81 * hmax)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32tc"])
@@ -276,5 +311,5 @@ def test_order_one_multirate_beach(precision):
     eh, em, _ = state_errors(s, integ)
     hmax = integ.q_end[0].max()
     _report(f"tsunami N=1 L={integ.L} {precision}", eh=eh / hmax, em=em / (hmax * np.sqrt(9.81 * hmax)))
-    tol = TOL_STATE[precision]
+    tol = TOL_STATE["tsunami_n1"][precision]
     assert eh < tol * hmax and em < tol * hmax * np.sqrt(9.81 * hmax)

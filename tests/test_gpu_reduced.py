@@ -13,7 +13,12 @@ import numpy as np
 import pytest
 
 from tests.gpu_helpers import both, state_errors
-from tests.test_gpu_parity import TOL_R, TOL_STATE, _rhs_case
+from tests.test_gpu_parity import _rhs_case
+
+# bounds frozen at about ten times the errors observed on GB300 (the design notes list
+# them): R per field relative to max|R| over N = 2..5; the 4-level beach's states
+TOL_R_2N = {"fp64": 1.3e-13, "fp32": 8e-6, "fp32tc": 2e-4}
+TOL_STATE_2N = {"fp64": 1.5e-13, "fp32": 4e-7, "fp32tc": 4e-7}
 from workloads import scenarios as sc
 
 pytestmark = pytest.mark.gpu
@@ -39,7 +44,7 @@ def test_reduced_rhs_matches_oracle(N, precision):
     R_g = s.rhs().cpu().numpy().astype(np.float64)
     errs = [np.abs(R_g[c] - R_o[c]).max() / np.abs(R_o[c]).max() for c in range(3)]
     print(f"PARITY order-2N rhs N={N} {precision} " + " ".join(f"{e:.3e}" for e in errs), flush=True)
-    assert max(errs) < TOL_R[precision]
+    assert max(errs) < TOL_R_2N[precision]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32tc"])
@@ -54,7 +59,7 @@ def test_reduced_lake_at_rest(precision, bed):
     R = s.rhs().cpu().numpy()
     scale = 9.81 * 1.3 ** 2 * max(np.abs(om.rx).max(), np.abs(om.sy).max())
     print(f"PARITY order-2N lake eta=0.3 {bed} {precision} rel={np.abs(R).max() / scale:.3e}", flush=True)
-    assert np.abs(R).max() < {"fp64": 1e-13, "fp32": 1e-5, "fp32tc": 1e-3}[precision] * scale
+    assert np.abs(R).max() <= {"fp64": 5e-15, "fp32": 0.0, "fp32tc": 0.0}[precision] * scale
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32tc"])
@@ -69,7 +74,7 @@ def test_reduced_mrab_tsunami_levels(precision):
     hmax = integ.q_end[0].max()
     print(f"PARITY order-2N tsunami L={integ.L} {precision} eh={eh / hmax:.3e} "
           f"em={em / (hmax * np.sqrt(9.81 * hmax)):.3e}", flush=True)
-    tol = TOL_STATE[precision]
+    tol = TOL_STATE_2N[precision]
     assert eh < tol * hmax and em < tol * hmax * np.sqrt(9.81 * hmax)
 
 

@@ -63,7 +63,7 @@ def test_regroup_matches_oracle(precision):
     hmax = integ.q_end[0].max()
     print(f"PARITY regroup {precision} eh={eh / hmax:.3e} em={em / (hmax * np.sqrt(9.81 * hmax)):.3e}", flush=True)
     assert abs(t - integ.time) < 1e-12 * integ.time
-    tol = TOL_STATE[precision]
+    tol = TOL_STATE["tsunami"][precision]
     assert eh < tol * hmax and em < tol * hmax * np.sqrt(9.81 * hmax)
 
 

@@ -231,33 +231,46 @@ def _rare_exact(x, y, t):
     return h, h * u, 0.0 * h
 
 
-def _rare_scenario(nx, N=2):
-    scn = sc.Scenario(name=f"rarefaction_{nx}", N=N, g=1.0, h0=1e-5, cfl=0.1, nlevels=1, limiter_mask=1,
+def _rare_scenario(nx, N=2, cfl=0.1):
+    scn = sc.Scenario(name=f"rarefaction_{nx}", N=N, g=1.0, h0=1e-5, cfl=cfl, nlevels=1, limiter_mask=1,
                       tvb_M=0.0, mesh=lambda: meshes.structured_rect(0, 50, 0, 40, nx, nx * 4 // 5),
                       bathymetry=lambda x, y, cx=None, cy=None: 0.0 * x, init=None)
     scn.init = lambda x, y, cx, cy, B: _rare_exact(x, y, 2.0)
     return scn
 
 
-@pytest.mark.parametrize("N", [1, 2])
+# Bounds on the mean rates over H = 1.25, 0.625, 0.3125 at the paper's CFL 0.03 (it
+# chose that small a number to keep the time-stepping error out of the spatial
+# rates), within 0.2 of the printed ones except N = 2 global (measured 1.24 over both
+# refinements against the printed 1.5; the design notes give what was tried). N = 3
+# runs on the tensor-core tier (the FP64 tier needs ~2 minutes there; the single
+# precision tiers' errors stay within 10 % of FP64's, test below).
+RARE_BOUNDS = {1: (1.2, 2.0, "fp64"), 2: (1.1, 2.8, "fp64"), 3: (1.3, 2.7, "fp32tc")}
+
+
+@pytest.mark.parametrize("N", [1, 2, 3])
 def test_rarefaction_wave_rates(N):
-    """Section 6.4 reports global L2 rates of about 1.5 and rates of 2.2 - 3.0 away from
-    the front and the rarefaction's head (N = 2: 1.5 and 3.0; tests/golden). Bounds here:
-    1.0 and 2.5 over H = 1.25, 0.625, 0.3125 (FP64), exact mass accounting, depth >= the
-    dry depth."""
+    """Section 6.4 reports global L2 rates of 1.4, 1.5, 1.5 (N = 1, 2, 3) and rates of
+    2.2, 3.0, 2.9 away from the front and the rarefaction's head (tests/golden). Bounds
+    here (RARE_BOUNDS): within 0.2 of those but N = 2 global; exact mass accounting,
+    depth >= the dry depth."""
     import json
     import os
     paper = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
     pr = paper["rarefaction_rates"]
-    res = _wetdry_errors(lambda nx: _rare_scenario(nx, N), [40, 80, 160], _rare_exact,
-                         lambda m: (m.cx > 15) & (m.cx < 35), 2.0, 10.0, "fp64")
+    bg, bl, precision = RARE_BOUNDS[N]
+    res = _wetdry_errors(lambda nx: _rare_scenario(nx, N, cfl=0.03), [40, 80, 160], _rare_exact,
+                         lambda m: (m.cx > 15) & (m.cx < 35), 2.0, 10.0, precision)
     g, l = _rate([r[0] for r in res]), _rate([r[1] for r in res])
-    print(f"PARITY rarefaction N={N} fp64 global " + " ".join(f"{r[0]:.3e}" for r in res)
+    print(f"PARITY rarefaction N={N} {precision} CFL 0.03 global " + " ".join(f"{r[0]:.3e}" for r in res)
           + " local " + " ".join(f"{r[1]:.3e}" for r in res) + f" rates {g:.2f} {l:.2f} (paper: "
           f"{pr['global'][N - 1]} {pr['local_15_35'][N - 1]})", flush=True)
-    assert g >= 1.0 and l >= {1: 1.7, 2: 2.5}[N]
-    assert max(r[2] for r in res) < 1e-12
-    assert min(r[3] for r in res) >= 1e-5 - 1e-15
+    assert abs(bg - pr["global"][N - 1]) <= 0.2 or N == 2
+    assert abs(bl - pr["local_15_35"][N - 1]) <= 0.2
+    assert g >= bg and l >= bl
+    drift_tol = 1e-12 if precision == "fp64" else 1e-5
+    assert max(r[2] for r in res) < drift_tol
+    assert min(r[3] for r in res) >= 1e-5 - (1e-15 if precision == "fp64" else 1e-10)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp32tc"])
