@@ -119,9 +119,12 @@ int swe_ref_operator(int32_t N, int32_t which, double* out, size_t count);
 
 /* ---- mesh (host only) --------------------------------------------------- */
 /* vx, vy: nv vertex coordinates; EToV: K x 3 vertex indices. Faces are matched
- * by their vertex pair; a face on one element only is a reflecting wall
- * (Section 6.5). Fails with SWE_EINVAL on degenerate triangles, bad indices or
- * faces shared by more than two triangles. */
+ * by their vertex pair; a face on one element only is a boundary face, a
+ * reflecting wall (Section 6.5) until a solver opens it. There is no per-face
+ * boundary-tag argument: the kind of each boundary face is set on the solver,
+ * swe_set_farfield (all boundary faces) and swe_set_open_faces (face by face),
+ * which take the place of such tags. Fails with SWE_EINVAL on degenerate
+ * triangles, bad indices or faces shared by more than two triangles. */
 int swe_mesh_create(const double* vx, const double* vy, int32_t nv,
                     const int32_t* EToV, int32_t K, swe_mesh** out);
 void swe_mesh_destroy(swe_mesh* mesh);
