@@ -168,16 +168,16 @@ struct LimitParams {
 
 // ---- persistent batched launch ------------------------------------------
 // Many scenarios advance in one persistent kernel per (tier, scheme and order)
-// group. The work is a queue of tickets; a ticket is one tile of 128 elements of one
+// group. The work is a queue of tickets; a ticket is one tile of elements of one
 // phase (the stage kernel or the TVB limiter of one finest substep) of one
-// scenario. Tickets are ordered phase by phase, round-robin over the scenarios, so a
+// scenario, taken by one warp. Tickets are ordered phase by phase, round-robin over the scenarios, so a
 // ticket depends only on tickets handed out before it (its scenario's earlier
 // phases): the lowest outstanding ticket can always run, with or without every CTA
 // resident.
 
-constexpr int kBatchTile = 128;     // threads per CTA
-constexpr int kBatchStageTile = 256;  // elements per stage ticket: two warp-tiles per warp
-constexpr int kBatchTvbTile = 512;  // elements per TVB ticket (the limiter is cheap per element)
+constexpr int kBatchTile = 128;       // threads per CTA (four warps, each taking its own tickets)
+constexpr int kBatchStageTile = 64;   // elements per stage ticket: two warp-tiles
+constexpr int kBatchTvbTile = 128;    // elements per TVB ticket: four per lane
 constexpr int kBatchMaxScn = 48;    // scenarios per group launch (kernel-parameter space)
 
 template <typename T>
@@ -213,6 +213,10 @@ struct BatchLaunch {
   BatchScn<T> scn[kBatchMaxScn];
   const BatchSeg* segs;
   const int* seg_of;  // [tickets] the segment of each ticket
+  // [segments] the stage kernel's and the limiter's parameters of each segment,
+  // built on the host (read-only while the kernel runs)
+  const StageParams<T>* __restrict__ stage_p;
+  const LimitParams<T>* __restrict__ limit_p;
   BatchCtl* ctl;
   int* done;          // [nscn] tiles completed (run or skipped) per scenario
   int* ran;           // [nscn] tiles run per scenario

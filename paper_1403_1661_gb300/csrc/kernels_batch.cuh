@@ -1,7 +1,7 @@
 // Persistent batched launch: many scenarios of one (tier, scheme and order) group
 // advanced by one kernel that takes its work from a device ticket queue.
 //
-// A ticket is one tile of elements (kBatchStageTile for the stage kernel: R,
+// A ticket, taken by one warp, is one tile of elements (kBatchStageTile for the stage kernel: R,
 // Adams-Bashforth commit and positivity limiter, Algorithms 1 and 3; kBatchTvbTile
 // for the TVB limiter, Section 5.3) of one phase of one scenario, a phase being one
 // of those two kernels at one finest substep of the scenario's multirate schedule.
@@ -13,9 +13,10 @@
 // other scenarios carry on. The first phase of a scenario also waits for its release
 // flag, which the host sets for every scenario it does not hold back.
 //
-// Memory ordering: a CTA that finishes a tile makes its stores visible (a
-// device-scope fence in every thread, then a barrier) before it adds to its
-// scenario's counter; a CTA that
+// Memory ordering: a warp that finishes a tile orders its lanes' stores before its
+// counter update with a warp barrier followed by a device-scope fence in the lane
+// that updates the counter (cumulative over what the barrier ordered, the pattern of
+// a grid-wide barrier); a warp that
 // waits reads the counter with acquire semantics, then the arrays other CTAs wrote
 // with ordinary (coherent) loads, never through the read-only data path.
 #pragma once
@@ -67,24 +68,37 @@ __device__ __forceinline__ int batch_wait(const BatchLaunch<T>& bl, const BatchS
   return 1;
 }
 
+// L2 prefetch of the node planes of the state and the bed of elements [e0, e0 + n)
+// of a scenario at substep k (the buffer each element reads: the parity of its
+// level's activation count), one 128-byte line per lane and plane. Hints only:
+// every address lies inside its array.
+template <typename T, int N>
+__device__ __forceinline__ void batch_prefetch_stage(const BatchScn<T>& B, long long k, int e0, int n, int lane) {
+  constexpr int NP = Dims<N>::NP;
+  const size_t ks = (size_t)B.sc.KS, fstride = (size_t)NP * ks;
+  const long long a = k >> (level_of(B.sc, e0) - 1);
+  const T* q = B.s.q + (size_t)(a & 1) * 3 * fstride + e0;
+  constexpr int per_line = 128 / sizeof(T);
+  const int lines = (n + per_line - 1) / per_line;
+  for (int w = lane; w < 4 * NP * lines; w += 32) {
+    const int pl = w / lines, ln = w - pl * lines;
+    const T* base = pl < 3 * NP ? q + (size_t)pl * ks : B.s.B + e0 + (size_t)(pl - 3 * NP) * ks;
+    prefetch_l2(base + ln * per_line);
+  }
+}
+
 // kTC: the tensor-core stage body (FP32 tier); otherwise the SIMT body (T = float
-// or double). The CTA has kBatchTile threads: four warps with two warp-tiles of 32
-// elements each per stage ticket for the tensor-core body, elements strided over
-// the threads for the SIMT body and the TVB limiter.
+// or double). Every warp of the CTA takes tickets on its own (no barrier in the
+// loop): a stage ticket is two warp-tiles of 32 elements, a TVB ticket 128 elements,
+// four to a lane. Lane 0 takes the warp's next ticket and looks up its segment
+// while the warp works on the current one, and the warp prefetches the next stage
+// ticket's node planes to L2, as the separate launch does a tile ahead.
 template <typename T, int N, bool kTC>
 __global__ void __launch_bounds__(kBatchTile, kTC ? 2 : 1) k_batch(const __grid_constant__ BatchLaunch<T> bl) {
-  static_assert(kBatchTile == kTcBlock && kBatchStageTile % (32 * kTcWarps) == 0,
-                "a tensor-core stage ticket is a whole number of warp-tiles per warp of the CTA");
+  static_assert(kBatchTile == kTcBlock, "the CTA is the tensor-core stage kernel's");
+  static_assert(kBatchStageTile % 32 == 0 && kBatchTvbTile % 32 == 0, "whole warp-tiles per ticket");
   static_assert(sizeof(BatchLaunch<T>) <= 32000, "batch launch parameters exceed the kernel-parameter space");
-  static_assert(offsetof(StageParams<T>, s) == offsetof(BatchScn<T>, s) &&
-                    offsetof(StageParams<T>, sc) == offsetof(BatchScn<T>, sc) &&
-                    offsetof(StageParams<T>, ph) == offsetof(BatchScn<T>, ph) &&
-                    offsetof(LimitParams<T>, ph) == offsetof(BatchScn<T>, ph),
-                "StageParams and LimitParams begin with the members of BatchScn");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ StageParams<T> s_p;
-  __shared__ LimitParams<T> s_lp;
-  __shared__ int s_seg, s_tile, s_go;
   T* sops = reinterpret_cast<T*>(smem_raw);
   // every scenario of the group has the same operators: stage the first one's
   if constexpr (kTC) {
@@ -92,86 +106,69 @@ __global__ void __launch_bounds__(kBatchTile, kTC ? 2 : 1) k_batch(const __grid_
   } else {
     stage_ops<T, N>(sops, bl.scn[0].s.ops);
   }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int total = __ldcg(&bl.ctl->total);
-  // thread 0 takes the next ticket and looks up its segment while the CTA works on
-  // the current one, so that the atomic and the lookups do not stall the CTA
   int ticket = 0, next_sg = -1;
-  if (threadIdx.x == 0) {
+  if (lane == 0) {
     ticket = atomicAdd(&bl.ctl->head, 1);
     if (ticket < total) next_sg = __ldcg(bl.seg_of + ticket);
   }
   for (;;) {
-    if (threadIdx.x == 0) {
-      int sg = -1, tile = 0, go = 0;
-      if (ticket < total) {
-        sg = next_sg;
-        tile = ticket - __ldcg(&bl.segs[sg].t0);
-        go = batch_wait(bl, bl.segs[sg]);
-        ticket = atomicAdd(&bl.ctl->head, 1);
-        if (ticket < total) next_sg = __ldcg(bl.seg_of + ticket);
-      }
-      s_seg = sg;
-      s_tile = tile;
-      s_go = go;
+    int sg = -1, tile = 0, go = 0;
+    if (lane == 0 && ticket < total) {
+      sg = next_sg;
+      tile = ticket - __ldcg(&bl.segs[sg].t0);
+      go = batch_wait(bl, bl.segs[sg]);
+      ticket = atomicAdd(&bl.ctl->head, 1);
+      next_sg = ticket < total ? __ldcg(bl.seg_of + ticket) : -1;
     }
-    __syncthreads();
-    const int sg = s_seg;
+    sg = __shfl_sync(0xffffffffu, sg, 0);
     if (sg < 0) break;
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    go = __shfl_sync(0xffffffffu, go, 0);
     const BatchSeg S = bl.segs[sg];
-    if (s_go) {
-      // the scenario's parameters: StageParams and LimitParams begin with the
-      // members of BatchScn (DevState, Sched, Phys), copied a word per thread
-      {
-        static_assert(sizeof(BatchScn<T>) % 4 == 0, "word copy");
-        const int* src = reinterpret_cast<const int*>(&bl.scn[S.scn]);
-        int* dp = reinterpret_cast<int*>(&s_p);
-        int* dl = reinterpret_cast<int*>(&s_lp);
-        for (int w = threadIdx.x; w < (int)(sizeof(BatchScn<T>) / 4); w += blockDim.x) {
-          const int v = src[w];
-          dp[w] = v;
-          dl[w] = v;
-        }
-      }
-      if (threadIdx.x == 0) {
-        s_p.j = S.j;
-        s_p.nactive = S.nactive;
-        s_p.mode = 0;
-        s_p.out = nullptr;
-        s_p.perm = nullptr;
-        s_lp.j = S.j;
-        s_lp.nactive = S.nactive;
-        s_lp.post_stage = 1;
-      }
-      __syncthreads();
+    if (go) {
+      // the segment's parameters, built on the host and read-only here (global
+      // memory, so that the stage body's shared-memory traffic never aliases them)
+      const StageParams<T>& wp = bl.stage_p[sg];
+      const LimitParams<T>& wl = bl.limit_p[sg];
       // the substep count: the scenario's macro counter (advanced only after the
       // launch) times its period, plus the phase's offset in this call
-      const long long k = __ldcg(s_p.s.macro) * (long long)bl.period[S.scn] + S.kofs;
-      // the same out-of-line bodies as the separate launches, over this ticket's tile
+      const long long k = __ldcg(wp.s.macro) * (long long)bl.period[S.scn] + S.kofs;
+      // the warp's next stage ticket: its planes start moving to L2 now
+      {
+        const int nsg = __shfl_sync(0xffffffffu, next_sg, 0);
+        const int nt = __shfl_sync(0xffffffffu, ticket, 0);
+        if (nsg >= 0) {
+          const BatchSeg Sn = bl.segs[nsg];
+          if (Sn.kind == 0) {
+            const int e0 = (nt - Sn.t0) * kBatchStageTile;
+            const long long kn = __ldcg(bl.scn[Sn.scn].s.macro) * (long long)bl.period[Sn.scn] + Sn.kofs;
+            batch_prefetch_stage<T, N>(bl.scn[Sn.scn], kn, e0, min(kBatchStageTile, Sn.nactive - e0), lane);
+          }
+        }
+      }
       double injected = 0.0;
       if (S.kind == 0) {
         if constexpr (kTC) {
-          // warp w takes warp-tiles t0 + w and t0 + w + 4 of the ticket's eight,
-          // prefetching the second while it works on the first
-          const int warp = threadIdx.x >> 5;
           float* sw = sops + TcSmem<N>::OPS + warp * TcSmem<N>::WARP;
-          const int t0 = s_tile * (kBatchStageTile / 32);
-          injected = stage_tc_range<N>(s_p, k, sops, sw, t0 + warp, kTcWarps,
-                                       min(t0 + kBatchStageTile / 32, (S.nactive + 31) / 32), true);
+          const int t0 = tile * (kBatchStageTile / 32);
+          injected = stage_tc_range<N>(wp, k, sops, sw, t0, 1, min(t0 + kBatchStageTile / 32, (S.nactive + 31) / 32),
+                                       true);
         } else {
-          const int e0 = s_tile * kBatchStageTile;
-          injected = stage_range<T, N>(s_p, sops, e0 + threadIdx.x, kBatchTile,
-                                       min(e0 + kBatchStageTile, S.nactive), k);
+          const int e0 = tile * kBatchStageTile;
+          injected = stage_range<T, N>(wp, sops, e0 + lane, 32, min(e0 + kBatchStageTile, S.nactive), k);
         }
       } else {
-        const int e0 = s_tile * kBatchTvbTile;
-        tvb_range<T, N>(s_lp, sops, e0 + threadIdx.x, kBatchTile, min(e0 + kBatchTvbTile, S.nactive), k);
+        const int e0 = tile * kBatchTvbTile;
+        tvb_range<T, N>(wl, sops, e0 + lane, 32, min(e0 + kBatchTvbTile, S.nactive), k);
       }
-      if (injected != 0.0) atomicAdd(s_p.s.acc, injected);
+      if (injected != 0.0) atomicAdd(wp.s.acc, injected);
     }
-    __threadfence();   // this thread's stores of the tile are visible device-wide
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      if (s_go) atomicAdd(bl.ran + S.scn, 1);
+    __syncwarp();   // the lanes' stores of the tile are issued and ordered before lane 0's
+    if (lane == 0) {
+      __threadfence();   // ... which a device-scope fence makes visible before the counter moves
+      if (go) atomicAdd(bl.ran + S.scn, 1);
       atomicAdd(bl.done + S.scn, 1);
     }
   }

@@ -168,6 +168,7 @@ struct BatchGroup {
   int code = 0;
   std::vector<int> idx;              // solvers of the batch in this group
   size_t off_ctl = 0, off_segs = 0, off_cnt = 0, off_release = 0, off_nmacro = 0, off_segof = 0;
+  size_t off_sparams = 0, off_lparams = 0;   // per segment: stage and limiter parameters
   int seg_cap = 0;
   int ticket_cap = 0;
   std::vector<int> seg_of;           // host copy of this call's ticket -> segment table
@@ -1709,6 +1710,13 @@ size_t batch_layout(std::vector<BatchGroup>& gs, swe_solver* const* solvers, int
     off = align256(off + n * sizeof(int));
     g.off_segof = off;
     off = align256(off + (size_t)tcap * sizeof(int));
+    static_assert(sizeof(swe::StageParams<float>) == sizeof(swe::StageParams<double>) &&
+                      sizeof(swe::LimitParams<float>) == sizeof(swe::LimitParams<double>),
+                  "parameter tables sized the same for both precisions");
+    g.off_sparams = off;
+    off = align256(off + (size_t)cap * sizeof(swe::StageParams<float>));
+    g.off_lparams = off;
+    off = align256(off + (size_t)cap * sizeof(swe::LimitParams<float>));
   }
   return off;
 }
@@ -1769,6 +1777,8 @@ swe::BatchLaunch<T> batch_params(const swe_batch* b, const BatchGroup& g) {
   const size_t n = g.idx.size();
   bl.segs = reinterpret_cast<const swe::BatchSeg*>(b->ws + g.off_segs);
   bl.seg_of = reinterpret_cast<const int*>(b->ws + g.off_segof);
+  bl.stage_p = reinterpret_cast<const swe::StageParams<T>*>(b->ws + g.off_sparams);
+  bl.limit_p = reinterpret_cast<const swe::LimitParams<T>*>(b->ws + g.off_lparams);
   bl.ctl = reinterpret_cast<swe::BatchCtl*>(b->ws + g.off_ctl);
   bl.done = reinterpret_cast<int*>(b->ws + g.off_cnt);
   bl.ran = bl.done + n;
@@ -1776,6 +1786,33 @@ swe::BatchLaunch<T> batch_params(const swe_batch* b, const BatchGroup& g) {
   bl.release = reinterpret_cast<const int*>(b->ws + g.off_release);
   bl.nscn = (int)n;
   return bl;
+}
+
+// The stage kernel's and the TVB limiter's parameters of every segment, built here
+// and read by the persistent kernel from the workspace.
+template <typename T>
+int batch_upload_params(swe_batch* b, const BatchGroup& g) {
+  std::vector<swe::StageParams<T>> sp(g.segs.size());
+  std::vector<swe::LimitParams<T>> lp(g.segs.size());
+  for (size_t q = 0; q < g.segs.size(); ++q) {
+    const swe::BatchSeg& S = g.segs[q];
+    swe_solver* s = b->solvers[g.idx[S.scn]];
+    std::memset(&sp[q], 0, sizeof(sp[q]));
+    std::memset(&lp[q], 0, sizeof(lp[q]));
+    sp[q].s = lp[q].s = dev_state<T>(s);
+    sp[q].sc = lp[q].sc = sched_of(s);
+    sp[q].ph = lp[q].ph = phys_of(s, s->prm.limiter_mask);
+    sp[q].j = lp[q].j = S.j;
+    sp[q].nactive = lp[q].nactive = S.nactive;
+    sp[q].mode = 0;
+    lp[q].post_stage = 1;
+  }
+  SWE_CUDA(cudaMemcpyAsync(b->ws + g.off_sparams, sp.data(), sp.size() * sizeof(sp[0]), cudaMemcpyHostToDevice,
+                           b->stream));
+  SWE_CUDA(cudaMemcpyAsync(b->ws + g.off_lparams, lp.data(), lp.size() * sizeof(lp[0]), cudaMemcpyHostToDevice,
+                           b->stream));
+  // pageable host memory: the copies above have taken the data when they return
+  return SWE_OK;
 }
 
 template <typename T>
@@ -1923,6 +1960,8 @@ int swe_batch_step(swe_batch* b, const int32_t* n_macro_each, int32_t* status_ea
                                  cudaMemcpyHostToDevice, b->stream));
         SWE_CUDA(cudaMemcpyAsync(b->ws + g.off_segof, g.seg_of.data(), g.seg_of.size() * sizeof(int),
                                  cudaMemcpyHostToDevice, b->stream));
+        const int rc = g.fp64 ? batch_upload_params<double>(b, g) : batch_upload_params<float>(b, g);
+        if (rc) return rc;
       }
     }
     swe::BatchCtl ctl;
