@@ -180,14 +180,7 @@ constexpr int kBatchStageTile = 64;   // elements per stage ticket: two warp-til
 constexpr int kBatchTvbTile = 128;    // elements per TVB ticket: four per lane
 constexpr int kBatchMaxScn = 48;    // scenarios per group launch (kernel-parameter space)
 
-template <typename T>
-struct BatchScn {
-  DevState<T> s;
-  Sched sc;
-  Phys ph;          // with the scenario's limiter mask applied
-};
-
-struct BatchSeg {   // one phase of one scenario: tickets [t0, t0 + ntiles)
+struct alignas(16) BatchSeg {   // one phase of one scenario: tickets [t0, t0 + ntiles)
   int t0;
   int ntiles;
   int need;         // tiles of this scenario that must be complete first
@@ -197,8 +190,9 @@ struct BatchSeg {   // one phase of one scenario: tickets [t0, t0 + ntiles)
   int j;            // substep within the macro step
   int kofs;         // k of this phase minus k at the start of the call
   int first;        // the scenario's first phase in this call: waits for its release
-  int pad;
+  int pad[3];
 };
+static_assert(sizeof(BatchSeg) == 48, "a segment is three 16-byte words");
 
 struct BatchCtl {   // per group, in the batch workspace
   int head;         // next ticket
@@ -210,12 +204,15 @@ struct BatchCtl {   // per group, in the batch workspace
 
 template <typename T>
 struct BatchLaunch {
-  BatchScn<T> scn[kBatchMaxScn];
+  // the stage kernel's parameters of each scenario (j = 0, nactive = K, mode 0; a
+  // segment supplies the substep and the active count). They stay in the
+  // kernel-parameter space: the stage body reads them through the constant cache,
+  // which the streaming node data never evicts
+  StageParams<T> scn[kBatchMaxScn];
   const BatchSeg* segs;
   const int* seg_of;  // [tickets] the segment of each ticket
-  // [segments] the stage kernel's and the limiter's parameters of each segment,
-  // built on the host (read-only while the kernel runs)
-  const StageParams<T>* __restrict__ stage_p;
+  // [segments] the limiter's parameters of each segment, built on the host
+  // (read-only while the kernel runs)
   const LimitParams<T>* __restrict__ limit_p;
   BatchCtl* ctl;
   int* done;          // [nscn] tiles completed (run or skipped) per scenario

@@ -73,7 +73,7 @@ __device__ __forceinline__ int batch_wait(const BatchLaunch<T>& bl, const BatchS
 // level's activation count), one 128-byte line per lane and plane. Hints only:
 // every address lies inside its array.
 template <typename T, int N>
-__device__ __forceinline__ void batch_prefetch_stage(const BatchScn<T>& B, long long k, int e0, int n, int lane) {
+__device__ __forceinline__ void batch_prefetch_stage(const StageParams<T>& B, long long k, int e0, int n, int lane) {
   constexpr int NP = Dims<N>::NP;
   const size_t ks = (size_t)B.sc.KS, fstride = (size_t)NP * ks;
   const long long a = k >> (level_of(B.sc, e0) - 1);
@@ -87,20 +87,37 @@ __device__ __forceinline__ void batch_prefetch_stage(const BatchScn<T>& B, long 
   }
 }
 
+__device__ __forceinline__ BatchSeg load_seg(const BatchSeg* p) {
+  BatchSeg S;
+  const int4* src = reinterpret_cast<const int4*>(p);
+  int4* dst = reinterpret_cast<int4*>(&S);
+  dst[0] = __ldg(src);
+  dst[1] = __ldg(src + 1);
+  dst[2] = __ldg(src + 2);
+  return S;
+}
+
 // kTC: the tensor-core stage body (FP32 tier); otherwise the SIMT body (T = float
 // or double). Every warp of the CTA takes tickets on its own (no barrier in the
 // loop): a stage ticket is two warp-tiles of 32 elements, a TVB ticket 128 elements,
-// four to a lane. Lane 0 takes the warp's next ticket and looks up its segment
-// while the warp works on the current one, and the warp prefetches the next stage
-// ticket's node planes to L2, as the separate launch does a tile ahead.
+// four to a lane. Lane 0 holds the warp's next ticket with its segment record,
+// fetched while the warp works on the current one, and waits only when a ticket
+// opens a segment it has not yet waited for (the tiles a segment needs are the same
+// for all its tickets). The warp prefetches the next stage ticket's node planes to
+// L2, as the separate launch does a tile ahead.
 template <typename T, int N, bool kTC>
 __global__ void __launch_bounds__(kBatchTile, kTC ? 2 : 1) k_batch(const __grid_constant__ BatchLaunch<T> bl) {
   static_assert(kBatchTile == kTcBlock, "the CTA is the tensor-core stage kernel's");
   static_assert(kBatchStageTile % 32 == 0 && kBatchTvbTile % 32 == 0, "whole warp-tiles per ticket");
   static_assert(sizeof(BatchLaunch<T>) <= 32000, "batch launch parameters exceed the kernel-parameter space");
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long s_k0[kBatchMaxScn];   // finest substep count at the start of the call
   T* sops = reinterpret_cast<T*>(smem_raw);
+  // the macro counters move only after the launch (the finish kernel): read once
+  for (int i = threadIdx.x; i < bl.nscn; i += blockDim.x)
+    s_k0[i] = __ldcg(bl.scn[i].s.macro) * (long long)bl.period[i];
   // every scenario of the group has the same operators: stage the first one's
+  // (the staging ends with a CTA barrier, which also publishes s_k0)
   if constexpr (kTC) {
     stage_ops<T, N, TcSmem<N>::OPS>(sops, bl.scn[0].s.ops);
   } else {
@@ -108,68 +125,89 @@ __global__ void __launch_bounds__(kBatchTile, kTC ? 2 : 1) k_batch(const __grid_
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int total = __ldcg(&bl.ctl->total);
-  int ticket = 0, next_sg = -1;
+  // lane 0: the next ticket and its segment
+  int ticket = 0, nsg = -1, ok_sg = -1;
+  BatchSeg nS;
   if (lane == 0) {
     ticket = atomicAdd(&bl.ctl->head, 1);
-    if (ticket < total) next_sg = __ldcg(bl.seg_of + ticket);
+    if (ticket < total) {
+      nsg = __ldg(bl.seg_of + ticket);
+      nS = load_seg(bl.segs + nsg);
+    }
   }
   for (;;) {
-    int sg = -1, tile = 0, go = 0;
-    if (lane == 0 && ticket < total) {
-      sg = next_sg;
-      tile = ticket - __ldcg(&bl.segs[sg].t0);
-      go = batch_wait(bl, bl.segs[sg]);
+    // lane 0 takes the held ticket, waits if it opens a segment, and fetches the next
+    int sg = -1, tile = 0, go = 0, scn = 0, kind = 0, nactive = 0, kofs = 0;
+    int pkind = -1, pscn = 0, pe0 = 0, pn = 0, pkofs = 0;   // the next ticket, for the prefetch
+    if (lane == 0 && nsg >= 0) {
+      const BatchSeg S = nS;
+      sg = nsg;
+      tile = ticket - S.t0;
+      scn = S.scn;
+      kind = S.kind;
+      nactive = S.nactive;
+      kofs = S.kofs;
+      go = sg == ok_sg ? 1 : batch_wait(bl, S);
+      if (go) ok_sg = sg;
       ticket = atomicAdd(&bl.ctl->head, 1);
-      next_sg = ticket < total ? __ldcg(bl.seg_of + ticket) : -1;
+      nsg = -1;
+      if (ticket < total) {
+        nsg = __ldg(bl.seg_of + ticket);
+        nS = load_seg(bl.segs + nsg);
+        pkind = nS.kind;
+        pscn = nS.scn;
+        pe0 = (ticket - nS.t0) * kBatchStageTile;
+        pn = min(kBatchStageTile, nS.nactive - pe0);
+        pkofs = nS.kofs;
+      }
     }
     sg = __shfl_sync(0xffffffffu, sg, 0);
     if (sg < 0) break;
     tile = __shfl_sync(0xffffffffu, tile, 0);
     go = __shfl_sync(0xffffffffu, go, 0);
-    const BatchSeg S = bl.segs[sg];
+    scn = __shfl_sync(0xffffffffu, scn, 0);
+    kind = __shfl_sync(0xffffffffu, kind, 0);
+    nactive = __shfl_sync(0xffffffffu, nactive, 0);
+    kofs = __shfl_sync(0xffffffffu, kofs, 0);
+    pkind = __shfl_sync(0xffffffffu, pkind, 0);
     if (go) {
-      // the segment's parameters, built on the host and read-only here (global
-      // memory, so that the stage body's shared-memory traffic never aliases them)
-      const StageParams<T>& wp = bl.stage_p[sg];
+      // the scenario's stage parameters (kernel-parameter space) and the segment's
+      // limiter parameters (built on the host, read-only here)
+      const StageParams<T>& wp = bl.scn[scn];
       const LimitParams<T>& wl = bl.limit_p[sg];
-      // the substep count: the scenario's macro counter (advanced only after the
-      // launch) times its period, plus the phase's offset in this call
-      const long long k = __ldcg(wp.s.macro) * (long long)bl.period[S.scn] + S.kofs;
+      // the substep count: the scenario's count at the start of the call plus the
+      // phase's offset in this call
+      const long long k = s_k0[scn] + kofs;
       // the warp's next stage ticket: its planes start moving to L2 now
-      {
-        const int nsg = __shfl_sync(0xffffffffu, next_sg, 0);
-        const int nt = __shfl_sync(0xffffffffu, ticket, 0);
-        if (nsg >= 0) {
-          const BatchSeg Sn = bl.segs[nsg];
-          if (Sn.kind == 0) {
-            const int e0 = (nt - Sn.t0) * kBatchStageTile;
-            const long long kn = __ldcg(bl.scn[Sn.scn].s.macro) * (long long)bl.period[Sn.scn] + Sn.kofs;
-            batch_prefetch_stage<T, N>(bl.scn[Sn.scn], kn, e0, min(kBatchStageTile, Sn.nactive - e0), lane);
-          }
-        }
+      if (pkind == 0) {
+        pscn = __shfl_sync(0xffffffffu, pscn, 0);
+        pe0 = __shfl_sync(0xffffffffu, pe0, 0);
+        pn = __shfl_sync(0xffffffffu, pn, 0);
+        pkofs = __shfl_sync(0xffffffffu, pkofs, 0);
+        batch_prefetch_stage<T, N>(bl.scn[pscn], s_k0[pscn] + pkofs, pe0, pn, lane);
       }
       double injected = 0.0;
-      if (S.kind == 0) {
+      if (kind == 0) {
         if constexpr (kTC) {
           float* sw = sops + TcSmem<N>::OPS + warp * TcSmem<N>::WARP;
           const int t0 = tile * (kBatchStageTile / 32);
-          injected = stage_tc_range<N>(wp, k, sops, sw, t0, 1, min(t0 + kBatchStageTile / 32, (S.nactive + 31) / 32),
-                                       true);
+          const int t1 = min(t0 + kBatchStageTile / 32, (nactive + 31) / 32);
+          injected = stage_tc_range<N>(wp, k, nactive, sops, sw, t0, 1, t1, true);
         } else {
           const int e0 = tile * kBatchStageTile;
-          injected = stage_range<T, N>(wp, sops, e0 + lane, 32, min(e0 + kBatchStageTile, S.nactive), k);
+          injected = stage_range<T, N>(wp, sops, e0 + lane, 32, min(e0 + kBatchStageTile, nactive), k);
         }
       } else {
         const int e0 = tile * kBatchTvbTile;
-        tvb_range<T, N>(wl, sops, e0 + lane, 32, min(e0 + kBatchTvbTile, S.nactive), k);
+        tvb_range<T, N>(wl, sops, e0 + lane, 32, min(e0 + kBatchTvbTile, nactive), k);
       }
       if (injected != 0.0) atomicAdd(wp.s.acc, injected);
     }
     __syncwarp();   // the lanes' stores of the tile are issued and ordered before lane 0's
     if (lane == 0) {
       __threadfence();   // ... which a device-scope fence makes visible before the counter moves
-      if (go) atomicAdd(bl.ran + S.scn, 1);
-      atomicAdd(bl.done + S.scn, 1);
+      if (go) atomicAdd(bl.ran + scn, 1);
+      atomicAdd(bl.done + scn, 1);
     }
   }
 }

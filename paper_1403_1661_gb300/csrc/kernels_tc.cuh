@@ -90,11 +90,13 @@ struct TcSmem {
 
 // One warp-tile of 32 elements (element e = 32 tile + lane): load, surface fluxes,
 // volume term and lift on tensor cores, commit and limiter. k: the finest substep
-// count of the schedule; next_tile: the warp's next tile (its planes are prefetched
-// to L2), or -1; sw: the warp's shared tiles.
+// count of the schedule; nactive: elements [0, nactive) are active at this substep;
+// next_tile: the warp's next tile (its planes are prefetched to L2), or -1; sw: the
+// warp's shared tiles.
 template <int N>
-__device__ __forceinline__ void stage_tc_warp(const StageParams<float>& p, long long k, const float* sops,
-                                              float* sw, int tile, int next_tile, double* injected) {
+__device__ __forceinline__ void stage_tc_warp(const StageParams<float>& p, long long k, int nactive,
+                                              const float* sops, float* sw, int tile, int next_tile,
+                                              double* injected) {
   using D = Dims<N>;
   using C = TcDims<N>;
   using TL = TcLayout<N>;
@@ -115,7 +117,7 @@ __device__ __forceinline__ void stage_tc_warp(const StageParams<float>& p, long 
   const size_t ks = (size_t)sc.KS, fstride = (size_t)NP * ks, bstride = 3 * fstride;
   // ---- load: lane = element; each node plane is one coalesced 128-byte line ----
   const int e = tile * 32 + lane;
-  const bool valid = e < p.nactive;
+  const bool valid = e < nactive;
   int lev = 1;
   long long a = 0;
   if (valid) {
@@ -150,7 +152,7 @@ __device__ __forceinline__ void stage_tc_warp(const StageParams<float>& p, long 
   // the tile; these are hints, every address lies inside its array)
   {
     const int e0n = next_tile * 32;
-    if (next_tile >= 0 && e0n < p.nactive) {
+    if (next_tile >= 0 && e0n < nactive) {
       const long long an = k >> (level_of(sc, e0n) - 1);
       const float* qn = p.s.q + (size_t)(an & 1) * bstride + e0n;
       for (int pl = lane; pl < 4 * NP; pl += 32)
@@ -491,11 +493,11 @@ __device__ __forceinline__ void stage_tc_warp(const StageParams<float>& p, long 
 // slower: its parameters become memory loads).
 template <int N>
 __device__ __forceinline__ double stage_tc_range(const StageParams<float>& __restrict__ p, long long k,
-                                              const float* __restrict__ sops, float* sw, int t0, int step,
-                                              int t1, bool prefetch) {
+                                              int nactive, const float* __restrict__ sops, float* sw, int t0,
+                                              int step, int t1, bool prefetch) {
   double injected = 0.0;
   for (int tile = t0; tile < t1; tile += step)
-    stage_tc_warp<N>(p, k, sops, sw, tile, prefetch ? tile + step : -1, &injected);
+    stage_tc_warp<N>(p, k, nactive, sops, sw, tile, prefetch ? tile + step : -1, &injected);
   return injected;
 }
 
@@ -515,7 +517,7 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(const __grid_constant_
   const long long k = (*p.s.macro) * (1LL << (p.sc.L - 1)) + p.j;
   const int ntiles = (p.nactive + 31) / 32;
   const double injected =
-      stage_tc_range<N>(p, k, sops, sw, blockIdx.x * kTcWarps + warp, gridDim.x * kTcWarps, ntiles, true);
+      stage_tc_range<N>(p, k, p.nactive, sops, sw, blockIdx.x * kTcWarps + warp, gridDim.x * kTcWarps, ntiles, true);
   if (injected != 0.0) atomicAdd(p.s.acc, injected);
 }
 

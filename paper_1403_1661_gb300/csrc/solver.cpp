@@ -168,7 +168,7 @@ struct BatchGroup {
   int code = 0;
   std::vector<int> idx;              // solvers of the batch in this group
   size_t off_ctl = 0, off_segs = 0, off_cnt = 0, off_release = 0, off_nmacro = 0, off_segof = 0;
-  size_t off_sparams = 0, off_lparams = 0;   // per segment: stage and limiter parameters
+  size_t off_lparams = 0;   // per segment: limiter parameters
   int seg_cap = 0;
   int ticket_cap = 0;
   std::vector<int> seg_of;           // host copy of this call's ticket -> segment table
@@ -1710,11 +1710,8 @@ size_t batch_layout(std::vector<BatchGroup>& gs, swe_solver* const* solvers, int
     off = align256(off + n * sizeof(int));
     g.off_segof = off;
     off = align256(off + (size_t)tcap * sizeof(int));
-    static_assert(sizeof(swe::StageParams<float>) == sizeof(swe::StageParams<double>) &&
-                      sizeof(swe::LimitParams<float>) == sizeof(swe::LimitParams<double>),
+    static_assert(sizeof(swe::LimitParams<float>) == sizeof(swe::LimitParams<double>),
                   "parameter tables sized the same for both precisions");
-    g.off_sparams = off;
-    off = align256(off + (size_t)cap * sizeof(swe::StageParams<float>));
     g.off_lparams = off;
     off = align256(off + (size_t)cap * sizeof(swe::LimitParams<float>));
   }
@@ -1772,12 +1769,14 @@ swe::BatchLaunch<T> batch_params(const swe_batch* b, const BatchGroup& g) {
     bl.scn[a].s = dev_state<T>(s);
     bl.scn[a].sc = sched_of(s);
     bl.scn[a].ph = phys_of(s, s->prm.limiter_mask);
+    bl.scn[a].j = 0;
+    bl.scn[a].nactive = s->K;
+    bl.scn[a].mode = 0;
     bl.period[a] = batch_period(s);
   }
   const size_t n = g.idx.size();
   bl.segs = reinterpret_cast<const swe::BatchSeg*>(b->ws + g.off_segs);
   bl.seg_of = reinterpret_cast<const int*>(b->ws + g.off_segof);
-  bl.stage_p = reinterpret_cast<const swe::StageParams<T>*>(b->ws + g.off_sparams);
   bl.limit_p = reinterpret_cast<const swe::LimitParams<T>*>(b->ws + g.off_lparams);
   bl.ctl = reinterpret_cast<swe::BatchCtl*>(b->ws + g.off_ctl);
   bl.done = reinterpret_cast<int*>(b->ws + g.off_cnt);
@@ -1788,27 +1787,22 @@ swe::BatchLaunch<T> batch_params(const swe_batch* b, const BatchGroup& g) {
   return bl;
 }
 
-// The stage kernel's and the TVB limiter's parameters of every segment, built here
-// and read by the persistent kernel from the workspace.
+// The TVB limiter's parameters of every segment, built here and read by the
+// persistent kernel from the workspace.
 template <typename T>
 int batch_upload_params(swe_batch* b, const BatchGroup& g) {
-  std::vector<swe::StageParams<T>> sp(g.segs.size());
   std::vector<swe::LimitParams<T>> lp(g.segs.size());
   for (size_t q = 0; q < g.segs.size(); ++q) {
     const swe::BatchSeg& S = g.segs[q];
     swe_solver* s = b->solvers[g.idx[S.scn]];
-    std::memset(&sp[q], 0, sizeof(sp[q]));
     std::memset(&lp[q], 0, sizeof(lp[q]));
-    sp[q].s = lp[q].s = dev_state<T>(s);
-    sp[q].sc = lp[q].sc = sched_of(s);
-    sp[q].ph = lp[q].ph = phys_of(s, s->prm.limiter_mask);
-    sp[q].j = lp[q].j = S.j;
-    sp[q].nactive = lp[q].nactive = S.nactive;
-    sp[q].mode = 0;
+    lp[q].s = dev_state<T>(s);
+    lp[q].sc = sched_of(s);
+    lp[q].ph = phys_of(s, s->prm.limiter_mask);
+    lp[q].j = S.j;
+    lp[q].nactive = S.nactive;
     lp[q].post_stage = 1;
   }
-  SWE_CUDA(cudaMemcpyAsync(b->ws + g.off_sparams, sp.data(), sp.size() * sizeof(sp[0]), cudaMemcpyHostToDevice,
-                           b->stream));
   SWE_CUDA(cudaMemcpyAsync(b->ws + g.off_lparams, lp.data(), lp.size() * sizeof(lp[0]), cudaMemcpyHostToDevice,
                            b->stream));
   // pageable host memory: the copies above have taken the data when they return
