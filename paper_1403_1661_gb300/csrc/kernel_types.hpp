@@ -144,11 +144,17 @@ struct Phys {
   int pp, dry_mode;
 };
 
+// One scenario: its device arrays, schedule and physics. The limiter bodies read
+// only this part, so the separate launch and the batch kernel pass them the same type.
 template <typename T>
-struct StageParams {
+struct ScnParams {
   DevState<T> s;
   Sched sc;
   Phys ph;
+};
+
+template <typename T>
+struct StageParams : ScnParams<T> {
   int j;          // substep within the macro step
   int nactive;    // elements [0, nactive) are active
   int mode;       // 0: R + commit + positivity; 1: R only, written to out
@@ -157,10 +163,7 @@ struct StageParams {
 };
 
 template <typename T>
-struct LimitParams {
-  DevState<T> s;
-  Sched sc;
-  Phys ph;
+struct LimitParams : ScnParams<T> {
   int j;
   int nactive;
   int post_stage;  // 1: limit the just-committed state of active elements; 0: current state
@@ -204,16 +207,13 @@ struct BatchCtl {   // per group, in the batch workspace
 
 template <typename T>
 struct BatchLaunch {
-  // the stage kernel's parameters of each scenario (j = 0, nactive = K, mode 0; a
-  // segment supplies the substep and the active count). They stay in the
-  // kernel-parameter space: the stage body reads them through the constant cache,
-  // which the streaming node data never evicts
+  // the parameters of each scenario (j = 0, nactive = K, mode 0; a segment supplies
+  // the substep and the active count, and the limiter runs on the just-committed
+  // state). They stay in the kernel-parameter space: the stage and limiter bodies
+  // read them through the constant cache, which the streaming node data never evicts
   StageParams<T> scn[kBatchMaxScn];
   const BatchSeg* segs;
   const int* seg_of;  // [tickets] the segment of each ticket
-  // [segments] the limiter's parameters of each segment, built on the host
-  // (read-only while the kernel runs)
-  const LimitParams<T>* __restrict__ limit_p;
   BatchCtl* ctl;
   int* done;          // [nscn] tiles completed (run or skipped) per scenario
   int* ran;           // [nscn] tiles run per scenario

@@ -841,8 +841,8 @@ __device__ __forceinline__ T minmod_tvb(T a, T b, T thr, bool& changed) {
 // substep count of the schedule); returns without change for an element that is dry,
 // has a dry neighbour or needs no limiting.
 template <typename T, int N>
-__device__ __forceinline__ void tvb_element(const LimitParams<T>& p, const T* __restrict__ sops, int e,
-                                            long long k) {
+__device__ __forceinline__ void tvb_element(const ScnParams<T>& p, int post_stage, const T* __restrict__ sops,
+                                            int e, long long k) {
   using D = Dims<N>;
   using O = OpLayout<N>;
   constexpr int NP = D::NP, NPP = D::NPP;
@@ -857,7 +857,7 @@ __device__ __forceinline__ void tvb_element(const LimitParams<T>& p, const T* __
     const int nbs[3] = {cn.x, cn.y, cn.z};
     const int lev = level_of(sc, e);
     const long long a = k >> (lev - 1);
-    const int cur = (int)((a + p.post_stage) & 1);
+    const int cur = (int)((a + post_stage) & 1);
     const size_t ks = (size_t)sc.KS, fstride = (size_t)NP * ks, bstride = 3 * fstride, eo = (size_t)e;
     T* q = p.s.q + cur * bstride;
     // 16-byte rows: geometry, element means (eta, hu, hv, -) as stored by the
@@ -1035,14 +1035,15 @@ __device__ __forceinline__ void tvb_element(const LimitParams<T>& p, const T* __
   }
 }
 
-// Elements e0, e0 + step, ... below e1 of the TVB limiter. Out of line: the
+// Elements e0, e0 + step, ... below e1 of the TVB limiter (post_stage: 1 limits the
+// just-committed state, 0 the current one). Out of line: the
 // separate launch and the persistent batch kernel then run one compiled copy of its
 // arithmetic (its many short multiply-add chains were rounded differently when it
 // was inlined into the two kernels), at no measured cost.
 template <typename T, int N>
-__device__ __noinline__ void tvb_range(const LimitParams<T>& __restrict__ p, const T* __restrict__ sops, int e0,
-                                       int step, int e1, long long k) {
-  for (int e = e0; e < e1; e += step) tvb_element<T, N>(p, sops, e, k);
+__device__ __noinline__ void tvb_range(const ScnParams<T>& __restrict__ p, int post_stage,
+                                       const T* __restrict__ sops, int e0, int step, int e1, long long k) {
+  for (int e = e0; e < e1; e += step) tvb_element<T, N>(p, post_stage, sops, e, k);
 }
 
 template <typename T, int N>
@@ -1051,7 +1052,8 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 6 : 3) k_tvb(const __
   T* sops = reinterpret_cast<T*>(smem_raw);
   stage_ops<T, N, OpLayout<N>::TAIL>(sops, p.s.ops);
   const long long k = (*p.s.macro) * (1LL << (p.sc.L - 1)) + p.j;
-  tvb_range<T, N>(p, sops, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, p.nactive, k);
+  tvb_range<T, N>(p, p.post_stage, sops, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, p.nactive,
+                  k);
 }
 
 }  // namespace swe

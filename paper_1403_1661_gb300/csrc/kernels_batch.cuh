@@ -171,10 +171,8 @@ __global__ void __launch_bounds__(kBatchTile, kTC ? 2 : 1) k_batch(const __grid_
     kofs = __shfl_sync(0xffffffffu, kofs, 0);
     pkind = __shfl_sync(0xffffffffu, pkind, 0);
     if (go) {
-      // the scenario's stage parameters (kernel-parameter space) and the segment's
-      // limiter parameters (built on the host, read-only here)
+      // the scenario's parameters, in the kernel-parameter space
       const StageParams<T>& wp = bl.scn[scn];
-      const LimitParams<T>& wl = bl.limit_p[sg];
       // the substep count: the scenario's count at the start of the call plus the
       // phase's offset in this call
       const long long k = s_k0[scn] + kofs;
@@ -199,7 +197,7 @@ __global__ void __launch_bounds__(kBatchTile, kTC ? 2 : 1) k_batch(const __grid_
         }
       } else {
         const int e0 = tile * kBatchTvbTile;
-        tvb_range<T, N>(wl, sops, e0 + lane, 32, min(e0 + kBatchTvbTile, nactive), k);
+        tvb_range<T, N>(wp, 1, sops, e0 + lane, 32, min(e0 + kBatchTvbTile, nactive), k);
       }
       if (injected != 0.0) atomicAdd(wp.s.acc, injected);
     }

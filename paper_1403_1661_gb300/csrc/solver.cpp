@@ -168,7 +168,6 @@ struct BatchGroup {
   int code = 0;
   std::vector<int> idx;              // solvers of the batch in this group
   size_t off_ctl = 0, off_segs = 0, off_cnt = 0, off_release = 0, off_nmacro = 0, off_segof = 0;
-  size_t off_lparams = 0;   // per segment: limiter parameters
   int seg_cap = 0;
   int ticket_cap = 0;
   std::vector<int> seg_of;           // host copy of this call's ticket -> segment table
@@ -1710,10 +1709,6 @@ size_t batch_layout(std::vector<BatchGroup>& gs, swe_solver* const* solvers, int
     off = align256(off + n * sizeof(int));
     g.off_segof = off;
     off = align256(off + (size_t)tcap * sizeof(int));
-    static_assert(sizeof(swe::LimitParams<float>) == sizeof(swe::LimitParams<double>),
-                  "parameter tables sized the same for both precisions");
-    g.off_lparams = off;
-    off = align256(off + (size_t)cap * sizeof(swe::LimitParams<float>));
   }
   return off;
 }
@@ -1777,7 +1772,6 @@ swe::BatchLaunch<T> batch_params(const swe_batch* b, const BatchGroup& g) {
   const size_t n = g.idx.size();
   bl.segs = reinterpret_cast<const swe::BatchSeg*>(b->ws + g.off_segs);
   bl.seg_of = reinterpret_cast<const int*>(b->ws + g.off_segof);
-  bl.limit_p = reinterpret_cast<const swe::LimitParams<T>*>(b->ws + g.off_lparams);
   bl.ctl = reinterpret_cast<swe::BatchCtl*>(b->ws + g.off_ctl);
   bl.done = reinterpret_cast<int*>(b->ws + g.off_cnt);
   bl.ran = bl.done + n;
@@ -1785,28 +1779,6 @@ swe::BatchLaunch<T> batch_params(const swe_batch* b, const BatchGroup& g) {
   bl.release = reinterpret_cast<const int*>(b->ws + g.off_release);
   bl.nscn = (int)n;
   return bl;
-}
-
-// The TVB limiter's parameters of every segment, built here and read by the
-// persistent kernel from the workspace.
-template <typename T>
-int batch_upload_params(swe_batch* b, const BatchGroup& g) {
-  std::vector<swe::LimitParams<T>> lp(g.segs.size());
-  for (size_t q = 0; q < g.segs.size(); ++q) {
-    const swe::BatchSeg& S = g.segs[q];
-    swe_solver* s = b->solvers[g.idx[S.scn]];
-    std::memset(&lp[q], 0, sizeof(lp[q]));
-    lp[q].s = dev_state<T>(s);
-    lp[q].sc = sched_of(s);
-    lp[q].ph = phys_of(s, s->prm.limiter_mask);
-    lp[q].j = S.j;
-    lp[q].nactive = S.nactive;
-    lp[q].post_stage = 1;
-  }
-  SWE_CUDA(cudaMemcpyAsync(b->ws + g.off_lparams, lp.data(), lp.size() * sizeof(lp[0]), cudaMemcpyHostToDevice,
-                           b->stream));
-  // pageable host memory: the copies above have taken the data when they return
-  return SWE_OK;
 }
 
 template <typename T>
@@ -1954,8 +1926,6 @@ int swe_batch_step(swe_batch* b, const int32_t* n_macro_each, int32_t* status_ea
                                  cudaMemcpyHostToDevice, b->stream));
         SWE_CUDA(cudaMemcpyAsync(b->ws + g.off_segof, g.seg_of.data(), g.seg_of.size() * sizeof(int),
                                  cudaMemcpyHostToDevice, b->stream));
-        const int rc = g.fp64 ? batch_upload_params<double>(b, g) : batch_upload_params<float>(b, g);
-        if (rc) return rc;
       }
     }
     swe::BatchCtl ctl;

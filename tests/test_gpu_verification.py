@@ -242,10 +242,12 @@ def _rare_scenario(nx, N=2, cfl=0.1):
 # Bounds on the mean rates over H = 1.25, 0.625, 0.3125 at the paper's CFL 0.03 (it
 # chose that small a number to keep the time-stepping error out of the spatial
 # rates), within 0.2 of the printed ones except N = 2 global (measured 1.24 over both
-# refinements against the printed 1.5; the design notes give what was tried). N = 3
-# runs on the tensor-core tier (the FP64 tier needs ~2 minutes there; the single
-# precision tiers' errors stay within 10 % of FP64's, test below).
-RARE_BOUNDS = {1: (1.2, 2.0, "fp64"), 2: (1.1, 2.8, "fp64"), 3: (1.3, 2.7, "fp32tc")}
+# refinements against the printed 1.5; the design notes give what was tried). All
+# orders run in FP64, as the paper's did: at N = 3 on the finest mesh (about 10^4
+# steps, a third of the domain near the dry depth) both single-precision tiers lose
+# the local rate (local error 6.9e-3 against 6.1e-5 in FP64, unaccounted mass 1.2e-4),
+# while at N = 2 they stay within 10 % of FP64 (test below).
+RARE_BOUNDS = {1: (1.2, 2.0, "fp64"), 2: (1.1, 2.8, "fp64"), 3: (1.3, 2.7, "fp64")}
 
 
 @pytest.mark.parametrize("N", [1, 2, 3])
@@ -265,8 +267,8 @@ def test_rarefaction_wave_rates(N):
     print(f"PARITY rarefaction N={N} {precision} CFL 0.03 global " + " ".join(f"{r[0]:.3e}" for r in res)
           + " local " + " ".join(f"{r[1]:.3e}" for r in res) + f" rates {g:.2f} {l:.2f} (paper: "
           f"{pr['global'][N - 1]} {pr['local_15_35'][N - 1]})", flush=True)
-    assert abs(bg - pr["global"][N - 1]) <= 0.2 or N == 2
-    assert abs(bl - pr["local_15_35"][N - 1]) <= 0.2
+    assert abs(bg - pr["global"][N - 1]) <= 0.2 + 1e-9 or N == 2
+    assert abs(bl - pr["local_15_35"][N - 1]) <= 0.2 + 1e-9
     assert g >= bg and l >= bl
     drift_tol = 1e-12 if precision == "fp64" else 1e-5
     assert max(r[2] for r in res) < drift_tol
