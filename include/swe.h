@@ -403,6 +403,38 @@ int swe_kernel_launches(const swe_solver* solver, int64_t* launches);
 int swe_mass_hmin_static(int32_t N, int32_t K, const double* dev_h, const double* dev_area,
                          double* dev_out, void* stream);
 
+/* ---- measurement probe: the volume projection on the two tensor-core paths ----
+ * Section 7.1 writes the volume term per field as N(Q) = Pr cF1 + Ps cF2 + P cS, a
+ * product Flux[elements x cubature points] * Op^T. This probe times that product
+ * for N = 4 shapes (16 padded nodes, 40 padded cubature points) on 128-element
+ * tiles, with a flux generated in registers as a[e][q] = x[e] c[q] + y[e]:
+ *   impl 0: warp-level mma.sync m16n8k8 TF32, flux in the A-fragment layout,
+ *           accumulators in registers;
+ *   impl 1: tcgen05.mma kind::tf32 (M = 128, N = 16, K = 8), flux stored to shared
+ *           memory in the canonical K-major layout (double-buffered, two CTA
+ *           barriers per tile), accumulator in TMEM, committed to an mbarrier, read
+ *           back with tcgen05.ld;
+ *   impl 2: the same product through four A buffers synchronised by mbarriers only
+ *           (threads arrive on a buffer's "full" barrier, the issuing thread commits
+ *           to its "empty" barrier), 83 KB of shared memory per CTA;
+ *   impl 3, 4: impl 1 with N = 64 or 128 (the operator's 16 columns repeated), to
+ *           time wider instructions on the same flux tiles; only the first 16
+ *           columns are read back;
+ *   impl 5: the flux stored from registers into TMEM (tcgen05.st, lane = element)
+ *           and read by the MMA as its A operand: no shared-memory tile.
+ * CTA i handles tiles [i * tiles_per_cta, (i + 1) * tiles_per_cta); row r of tile t
+ * is element (t * 128 + r). Device arrays: dev_x, dev_y [nctas * tiles_per_cta * 128];
+ * dev_c [40]; dev_b [40 * 16] row-major (b[q * 16 + n]); dev_d [nctas * 128 * 16]
+ * receives, per CTA, D[r][n] = sum over its tiles t and q of tf32(a_t[r][q]) *
+ * tf32(b[q][n]) (operands rounded to nearest, ties away). dev_status [nctas]
+ * (impl >= 1): SWE_OK, or SWE_ETIMEOUT where a wait on the tensor core gave up after
+ * one second (that CTA's row of dev_d is then not written). All arrays are the
+ * caller's; launches on `stream`, returns without synchronising. Returns SWE_EINVAL
+ * for a bad argument, SWE_ECUDA for a failed launch, with swe_last_error(). */
+int swe_tc_projection_probe(int32_t impl, int32_t nctas, int32_t tiles_per_cta, const float* dev_x,
+                            const float* dev_y, const float* dev_c, const float* dev_b, float* dev_d,
+                            int32_t* dev_status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

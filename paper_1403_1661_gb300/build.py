@@ -29,7 +29,7 @@ CXX_SOURCES = ["refelem.cpp", "mesh.cpp", "solver.cpp"]
 CU_SOURCES = ["kernels_n1.cu", "kernels_n2.cu", "kernels_n3.cu", "kernels_n4.cu", "kernels_n5.cu",
               "kernels_c2.cu", "kernels_c3.cu", "kernels_c4.cu", "kernels_c5.cu",
               "kernels_r2.cu", "kernels_r3.cu", "kernels_r4.cu", "kernels_r5.cu", "kernels_common.cu",
-              "noalloc.cu"]
+              "noalloc.cu", "tc05_projection.cu"]
 
 
 def _cuda_home() -> str:
