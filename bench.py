@@ -559,6 +559,18 @@ def run_batched(args, steps=5):
                 m += 1
             per_macro += int(sum(counts[:(L if j == 0 else m)]))
         d_step[so] = per_macro
+    # the same solvers stepped one by one, each replaying its own graph on its own
+    # stream (enqueued back to back, so their kernels overlap on the GPU): the
+    # schedule the persistent kernel replaces
+    torch.cuda.synchronize()
+    d1 = sum(so.stats()["dof_updates"] for so in solvers)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for so in solvers:
+            so.step(1)
+    torch.cuda.synchronize()
+    ms_alone = (time.perf_counter() - t0) * 1e3
+    dofs_alone = sum(so.stats()["dof_updates"] for so in solvers) - d1
     bpe = {N: stage_bytes_per_element(N, 4 if args.precision != "fp64" else 8) for N in {s.N for s in scns}}
     byts = sum(d_step[so] * bpe[s_.N] for s_, so in zip(scns, solvers))
     peak, peak_kind = measured_peaks()
@@ -574,7 +586,11 @@ def run_batched(args, steps=5):
                                  "whole step time (the TVB work inside the same kernels is not counted)",
                         "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"},
            "step": "one graph replay = one macro step of every scenario: per (tier, order) group one "
-                   "persistent kernel over a device ticket queue"}
+                   "persistent kernel over a device ticket queue",
+           "per_solver_streams": {"value": dofs_alone / (ms_alone / 1e3), "unit": UNIT,
+                                  "ms_per_step": ms_alone / steps,
+                                  "note": "same solvers and steps, each solver's own captured graph on its own "
+                                          "stream, host wall clock"}}
     b.close()
     for so in solvers:
         so.close()
@@ -587,7 +603,7 @@ def run_served(args):
     from workloads import scenarios as sc
     stream = sc.served_stream(duration=args.serve_seconds)
     reqs = requests_from_stream(stream, substeps=500)
-    srv = Server(budget_bytes=150e9, max_slots=64, macro_per_round=4, prep_workers=8,
+    srv = Server(budget_bytes=150e9, max_slots=64, macro_per_round=4, prep_workers=8, start_workers=8,
                  factory=GpuFactory(args.precision))
     out = srv.run(reqs)
     torch.cuda.synchronize()
@@ -596,7 +612,7 @@ def run_served(args):
             "peak_running": out["peak_running"], "peak_gb": out["peak_bytes"] / 1e9,
             "rejected": out["rejected"], "failed": out["failed"],
             "arrivals": f"Poisson 50/s for {args.serve_seconds:.0f} s, K log-uniform 2k-1M, N in {{2,3,4}}, "
-                        f"500 MRAB substeps each, HBM budget 150 GB"}
+                        f"500 MRAB substeps each, HBM budget 150 GB; 8 preparation and 8 creation threads"}
 
 
 def _oracle_rate(scn, substeps):

@@ -161,11 +161,15 @@ class _GpuJob:
 
 class Server:
     def __init__(self, budget_bytes=150e9, max_slots=64, macro_per_round=2, prep_workers=4, factory=None,
-                 clock=time.perf_counter, sleep=time.sleep, health_every=16):
+                 clock=time.perf_counter, sleep=time.sleep, health_every=16, start_workers=0):
         self.budget = float(budget_bytes)
         self.max_slots = int(max_slots)
         self.macro_per_round = int(macro_per_round)
         self.prep_workers = int(prep_workers)
+        # start_workers > 0: admitted solves are created (device workspace, inputs,
+        # levels) on that many threads, so the loop that issues the running solves'
+        # steps never waits for a creation; 0 creates them in the loop itself
+        self.start_workers = int(start_workers)
         self.factory = factory if factory is not None else GpuFactory()
         self.clock = clock
         self.sleep = sleep
@@ -192,6 +196,7 @@ class Server:
         pending = collections.deque(reqs)
         preparing = collections.deque()          # (req, future) in arrival order
         ready = collections.deque()               # (req, prepared), FIFO
+        starting = collections.deque()            # (req, future of the job), admitted
         running = []                              # [req, job, remaining_macro, rounds]
         used = 0.0
         peak_used = 0.0
@@ -205,8 +210,13 @@ class Server:
             r.finished = self.clock() - t0
             ended.append(r)
 
+        def admit(r, job):
+            r.admitted = self.clock() - t0
+            running.append([r, job, int(math.ceil(r.substeps / job.macro_period)), 0])
+
+        starter = cf.ThreadPoolExecutor(max_workers=self.start_workers) if self.start_workers > 0 else None
         with cf.ThreadPoolExecutor(max_workers=self.prep_workers) as pool:
-            while pending or preparing or ready or running:
+            while pending or preparing or ready or starting or running:
                 now = self.clock() - t0
                 progressed = False
                 while pending and pending[0].arrival <= now:
@@ -239,18 +249,34 @@ class Server:
                     ready = keep
                     progressed = True
                 # admission: first come first served, by budget and slots
-                while ready and len(running) < self.max_slots and used + ready[0][0].bytes <= self.budget:
+                while (ready and len(running) + len(starting) < self.max_slots
+                       and used + ready[0][0].bytes <= self.budget):
                     r, prep = ready.popleft()
                     progressed = True
+                    if starter is not None:
+                        used += r.bytes
+                        peak_used = max(peak_used, used)
+                        starting.append((r, starter.submit(self.factory.start, r, prep)))
+                        continue
                     try:
                         job = self.factory.start(r, prep)
                     except Exception as ex:          # e.g. the device refused the workspace
                         end(r, "failed", f"start failed: {ex}")
                         continue
-                    r.admitted = self.clock() - t0
                     used += r.bytes
                     peak_used = max(peak_used, used)
-                    running.append([r, job, int(math.ceil(r.substeps / job.macro_period)), 0])
+                    admit(r, job)
+                # solves whose creation finished join the running ones, in admission order
+                while starting and starting[0][1].done():
+                    r, fut = starting.popleft()
+                    progressed = True
+                    try:
+                        job = fut.result()
+                    except Exception as ex:
+                        used -= r.bytes
+                        end(r, "failed", f"start failed: {ex}")
+                        continue
+                    admit(r, job)
                 peak_running = max(peak_running, len(running))
                 # issue work and retire finished, failed or cancelled solves
                 still = []
@@ -289,6 +315,8 @@ class Server:
                 if not progressed:
                     nxt = pending[0].arrival - (self.clock() - t0) if pending else 0.0
                     self.sleep(max(0.0002, min(nxt, 0.002)))
+        if starter is not None:
+            starter.shutdown(wait=True)
         wall = self.clock() - t0
         lat = np.array([r.finished - r.arrival for r in done]) if done else np.zeros(1)
         dofs = sum(r.dof_updates for r in done)

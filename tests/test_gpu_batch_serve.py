@@ -106,7 +106,8 @@ def test_served_results_equal_alone():
     from paper_1403_1661_gb300.serve import GpuFactory, Request, Server
     scns = _mix()
     reqs = [Request(rid=i, arrival=0.002 * i, scenario=s, substeps=24) for i, s in enumerate(scns)]
-    srv = Server(budget_bytes=2e9, max_slots=3, macro_per_round=1, factory=GpuFactory("fp32tc", keep_state=True))
+    srv = Server(budget_bytes=2e9, max_slots=3, macro_per_round=1, factory=GpuFactory("fp32tc", keep_state=True),
+                 start_workers=2)
     out = srv.run(reqs)
     assert out["requests"] == len(scns) and out["p99_s"] >= out["p50_s"] > 0
     for r in out["done"]:

@@ -78,13 +78,13 @@ class FakeFactory:
 
 
 def _run(sizes, arrivals, budget, slots, substeps=40, step_time=10.0, cancel_at=None, server_cancel=(),
-         health_every=2, **faults):
+         health_every=2, start_workers=0, **faults):
     # fake device time per macro step is large against the host loop's own time,
     # so admission order does not depend on how fast the preparation threads run
     clock = FakeClock()
     fac = FakeFactory(clock, sizes, step_time, **faults)
     srv = Server(budget_bytes=budget, max_slots=slots, macro_per_round=2, prep_workers=1, factory=fac,
-                 clock=clock, sleep=clock.sleep, health_every=health_every)
+                 clock=clock, sleep=clock.sleep, health_every=health_every, start_workers=start_workers)
     cancel_at = cancel_at or {}
     reqs = [Request(rid=i, arrival=a, scenario=None, substeps=substeps, cancel_at=cancel_at.get(i))
             for i, a in enumerate(arrivals)]
@@ -134,6 +134,20 @@ def test_failed_preparation_or_start_stays_with_its_request():
     errs = {r.rid: r.error for r in out["ended"]}
     assert "not conforming" in errs[1] and "workspace refused" in errs[2]
     assert out["failed"] == 1 and out["rejected"] == 1
+
+
+def test_threaded_start_serves_all_and_keeps_failures_with_their_request():
+    # solves created on two threads: admission stays first come first served, a
+    # failed creation gives its memory back and the others are served
+    _, fac, out = _run([10] * 6, [0.0] * 6, budget=20, slots=3, bad_start={2}, start_workers=2)
+    st = _status(out)
+    assert st == {0: "done", 1: "done", 2: "failed", 3: "done", 4: "done", 5: "done"}
+    assert "workspace refused" in [r.error for r in out["ended"] if r.rid == 2][0]
+    assert out["peak_bytes"] <= 20 and out["peak_running"] <= 2
+    admitted = [r.admitted for r in sorted(out["done"], key=lambda r: r.rid)]
+    assert admitted == sorted(admitted)
+    for r in out["done"]:
+        assert r.dof_updates == 100 * math.ceil(40 / 4)
 
 
 def test_nonfinite_solve_is_stopped_and_its_memory_admits_the_next():
