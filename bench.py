@@ -577,7 +577,7 @@ def run_batched(args, steps=5):
     ach = byts / (ms / steps / 1e3) / 1e9
     out = {"value": dofs / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "scenarios": len(scns),
            "triangles": int(sum(so.K for so in solvers)), "orders": sorted({s.N for s in scns}),
-           "autotuned_ctas_per_sm": {str(k): v for k, v in tuned.items()},
+           "autotuned": {str(k): v for k, v in tuned.items()},
            "gpu_launches_per_step": (b.launches() - l0) / steps,
            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                         "kernel": "k_batch (persistent; stage + TVB tickets)",
@@ -591,6 +591,24 @@ def run_batched(args, steps=5):
                                   "ms_per_step": ms_alone / steps,
                                   "note": "same solvers and steps, each solver's own captured graph on its own "
                                           "stream, host wall clock"}}
+    b.close()
+    # the same batch at the default shape (as many CTAs as fit, four warps per
+    # tensor-core CTA): what the tuning buys
+    default = {"ctas_per_sm": 0, "tc_warps": 4 if args.precision == "fp32tc" else None}
+    for so in solvers:
+        so.set_launch_config(default)
+    b = P.Batch(solvers, max_macro=1)
+    b.step(1)
+    torch.cuda.synchronize()
+    d2 = sum(so.stats()["dof_updates"] for so in solvers)
+    e0.record(b.stream)
+    for _ in range(steps):
+        b.step(1)
+    e1.record(b.stream)
+    torch.cuda.synchronize()
+    ms_u = e0.elapsed_time(e1)
+    out["untuned"] = {"value": (sum(so.stats()["dof_updates"] for so in solvers) - d2) / (ms_u / 1e3),
+                      "unit": UNIT, "ms_per_step": ms_u / steps, "shape": default}
     b.close()
     for so in solvers:
         so.close()

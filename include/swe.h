@@ -322,7 +322,7 @@ int swe_batch_create(swe_solver* const* solvers, int32_t n, int32_t max_macro, v
  * nothing launched, for a count outside 0..max_macro, a solver without a valid
  * level-synchronous state, or a solver whose levels, element order, launch shape
  * or boundary faces changed since swe_batch_create (swe_set_levels,
- * swe_setup_levels, swe_regroup, swe_set_launch_config, swe_set_farfield,
+ * swe_setup_levels, swe_regroup, swe_set_launch_config, swe_set_tc_warps, swe_set_farfield,
  * swe_set_open_faces, swe_set_full_state): create the batch again. */
 int swe_batch_step(swe_batch* batch, const int32_t* n_macro_each, int32_t* status_each);
 
@@ -359,6 +359,16 @@ int swe_set_open_faces(swe_solver* solver, const uint8_t* open);
  * SM in their grid-stride loops (0 = as many as fit). Used by the autotuner;
  * results do not depend on it. */
 int swe_set_launch_config(swe_solver* solver, int32_t ctas_per_sm);
+
+/* Warps per CTA of the tensor-core stage kernel and of the persistent batch kernel
+ * (FP32 tensor-core tier; default 4). Each warp owns its shared-memory tiles and the
+ * CTA one copy of the operators, so more warps per CTA share that copy: at N = 5
+ * (29 KB of tiles per warp) seven warps fit on an SM as one CTA where two CTAs of
+ * four do not. warps in 1..8; SWE_EINVAL when that many warps' tiles do not fit on
+ * an SM, SWE_EUNSUPPORTED on the other tiers. Used by the autotuner; results do not
+ * depend on it. A batch takes the warps of the first solver of each group at
+ * swe_batch_create. */
+int swe_set_tc_warps(swe_solver* solver, int32_t warps);
 
 /* Advance n finest substeps like swe_substep, timing every kernel launch with CUDA
  * events on the solver's stream (synchronises at the end). out[0..5]: total ms of

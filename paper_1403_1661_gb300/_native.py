@@ -97,6 +97,7 @@ SIGNATURES = {
     "swe_batch_launches": (C.c_int, [_vp, _i64p]),
     "swe_batch_destroy": (None, [_vp]),
     "swe_set_launch_config": (C.c_int, [_vp, C.c_int32]),
+    "swe_set_tc_warps": (C.c_int, [_vp, C.c_int32]),
     "swe_mass_hmin_static": (C.c_int, [C.c_int32, C.c_int32, _vp, _vp, _vp, _vp]),
     "swe_tc_projection_probe": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }

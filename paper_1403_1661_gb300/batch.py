@@ -85,10 +85,21 @@ class Batch:
 
 
 # ---------------------------------------------------------------------------
-# autotuner: CTAs per SM of the grid-stride kernels, per (order, precision, GPU)
+# autotuner: launch shapes per (order, precision, GPU) -- CTAs per SM of the
+# grid-stride kernels and, on the tensor-core tier, warps per CTA of the
+# tensor-core stage and batch kernels
 
 CACHE = os.path.join(BUILD, "autotune.json")
-CANDIDATES = (1, 2, 3, 4, 0)
+CTAS = (1, 2, 3, 4, 0)            # CTAs per SM (0 = as many as fit)
+TC_WARPS = (2, 3, 4, 5, 6, 7, 8)  # warps per CTA of the tensor-core kernels
+
+
+def candidates_for(precision):
+    """Every launch shape the tuner tries: (ctas_per_sm, tc_warps), tc_warps None
+    off the tensor-core tier."""
+    if precision == "fp32tc":
+        return tuple((c, w) for w in TC_WARPS for c in CTAS)
+    return tuple((c, None) for c in CTAS)
 
 
 def _gpu_key():
@@ -103,23 +114,31 @@ def _load_cache():
         return {}
 
 
-def tune(N, precision, candidates=CANDIDATES, reps=3, force=False, verbose=False):
-    """Time one macro step of a seeded sample problem of order N for every
-    candidate launch shape and return the fastest (ctas_per_sm, 0 = max). Only a
-    search over the full candidate set reads or writes the cache, so a narrower
-    search never stands in for it."""
+def tune(N, precision, candidates=None, reps=3, force=False, verbose=False):
+    """Time one macro step of a seeded sample problem of order N (an 80,000-triangle
+    beach, 4 levels) for every candidate launch shape and return the fastest as
+    {"ctas_per_sm": c, "tc_warps": w}. Shapes that do not fit on an SM are skipped.
+    Only a search over the full candidate set reads or writes the cache, so a
+    narrower search never stands in for it."""
     import torch
     from workloads import scenarios as sc
     from .solver import solver_from_scenario
-    key = f"{_gpu_key()}/N{N}/{precision}"
-    full = tuple(candidates) == tuple(CANDIDATES)
+    full_set = candidates_for(precision)
+    cands = full_set if candidates is None else tuple(candidates)
+    key = f"{_gpu_key()}/N{N}/{precision}/shape"
+    full = cands == full_set
     cache = _load_cache()
     if full and key in cache and not force:
-        return cache[key]["ctas_per_sm"]
-    s = solver_from_scenario(sc.tsunami(nx=240, ny=60, N=N, nlevels=4), precision=precision)
+        return dict(cache[key]["shape"])
+    s = solver_from_scenario(sc.tsunami(nx=400, ny=100, N=N, nlevels=4), precision=precision)
     timings = {}
-    for c in candidates:
-        s.set_launch_config(c)
+    for c, w in cands:
+        try:
+            s.set_launch_config({"ctas_per_sm": c, "tc_warps": w})
+        except nat.SWEError as ex:
+            if ex.code == nat.SWE_EINVAL:     # that many warps' tiles do not fit on an SM
+                continue
+            raise
         s.step(1)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -128,15 +147,17 @@ def tune(N, precision, candidates=CANDIDATES, reps=3, force=False, verbose=False
         s.step(reps)
         e1.record(s.stream)
         torch.cuda.synchronize()
-        timings[c] = e0.elapsed_time(e1) / reps
-    best = min(timings, key=timings.get)
+        timings[(c, w)] = e0.elapsed_time(e1) / reps
+    s.close()
+    c, w = min(timings, key=timings.get)
+    best = {"ctas_per_sm": c, "tc_warps": w}
     if full:
-        cache[key] = {"ctas_per_sm": best, "ms_per_macro_step": timings, "when": time.time()}
+        cache[key] = {"shape": best, "ms_per_macro_step": {f"{k[0]}/{k[1]}": v for k, v in timings.items()},
+                      "when": time.time()}
         os.makedirs(os.path.dirname(CACHE), exist_ok=True)
         json.dump(cache, open(CACHE, "w"), indent=1, default=str)
     if verbose:
         print(f"autotune {key}: {timings} -> {best}")
-    s.close()
     return best
 
 

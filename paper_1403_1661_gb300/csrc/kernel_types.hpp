@@ -178,7 +178,8 @@ struct LimitParams : ScnParams<T> {
 // phases): the lowest outstanding ticket can always run, with or without every CTA
 // resident.
 
-constexpr int kBatchTile = 128;       // threads per CTA (four warps, each taking its own tickets)
+constexpr int kBatchTile = 128;       // threads per CTA of the SIMT body (four warps, each taking its own
+                                      // tickets); the tensor-core body runs the solvers' warps per CTA
 constexpr int kBatchStageTile = 64;   // elements per stage ticket: two warp-tiles
 constexpr int kBatchTvbTile = 128;    // elements per TVB ticket: four per lane
 constexpr int kBatchMaxScn = 48;    // scenarios per group launch (kernel-parameter space)

@@ -106,8 +106,7 @@ __device__ __forceinline__ BatchSeg load_seg(const BatchSeg* p) {
 // for all its tickets). The warp prefetches the next stage ticket's node planes to
 // L2, as the separate launch does a tile ahead.
 template <typename T, int N, bool kTC>
-__global__ void __launch_bounds__(kBatchTile, kTC ? 2 : 1) k_batch(const __grid_constant__ BatchLaunch<T> bl) {
-  static_assert(kBatchTile == kTcBlock, "the CTA is the tensor-core stage kernel's");
+__global__ void __launch_bounds__(kTC ? kTcMaxBlock : kBatchTile, 1) k_batch(const __grid_constant__ BatchLaunch<T> bl) {
   static_assert(kBatchStageTile % 32 == 0 && kBatchTvbTile % 32 == 0, "whole warp-tiles per ticket");
   static_assert(sizeof(BatchLaunch<T>) <= 32000, "batch launch parameters exceed the kernel-parameter space");
   extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -28,8 +28,10 @@
 
 namespace swe {
 
-constexpr int kTcWarps = 4;
+constexpr int kTcWarps = 4;                  // warps per CTA unless a solver sets another count
 constexpr int kTcBlock = 32 * kTcWarps;
+constexpr int kTcMaxWarps = 8;               // 8 warps x 32 threads x 255 registers fill the register file
+constexpr int kTcMaxBlock = 32 * kTcMaxWarps;
 
 __device__ __forceinline__ void mma_k16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
   asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -85,7 +87,9 @@ struct TcSmem {
   static constexpr int MD = GEO + 32 * 4;
   static constexpr int WARP = MD + 32;                   // floats per warp
   static constexpr int OPS = OpLayout<N>::TAIL;          // floats of per-element operators (staged first)
-  static constexpr int BYTES = (OPS + kTcWarps * WARP) * 4;
+  // dynamic shared memory of a CTA of `warps` warps: one operator copy, one tile set per warp
+  static constexpr int bytes(int warps) { return (OPS + warps * WARP) * 4; }
+  static constexpr int BYTES = bytes(kTcWarps);
 };
 
 // One warp-tile of 32 elements (element e = 32 tile + lane): load, surface fluxes,
@@ -502,7 +506,9 @@ __device__ __forceinline__ double stage_tc_range(const StageParams<float>& __res
 }
 
 template <int N>
-__global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(const __grid_constant__ StageParams<float> p) {
+// CTA: blockDim.x / 32 warps (1 to kTcMaxWarps), each with its own shared tiles after
+// the CTA's operator copy.
+__global__ void __launch_bounds__(kTcMaxBlock, 1) k_stage_tc(const __grid_constant__ StageParams<float> p) {
   using SM = TcSmem<N>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sops = reinterpret_cast<float*>(smem_raw);                       // [0, OPS)
@@ -512,12 +518,12 @@ __global__ void __launch_bounds__(kTcBlock, 2) k_stage_tc(const __grid_constant_
     for (int i = threadIdx.x; i < SM::OPS / 4; i += blockDim.x) dst[i] = __ldg(src + i);
     __syncthreads();
   }
-  const int warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   float* sw = sops + SM::OPS + warp * SM::WARP;
   const long long k = (*p.s.macro) * (1LL << (p.sc.L - 1)) + p.j;
   const int ntiles = (p.nactive + 31) / 32;
   const double injected =
-      stage_tc_range<N>(p, k, p.nactive, sops, sw, blockIdx.x * kTcWarps + warp, gridDim.x * kTcWarps, ntiles, true);
+      stage_tc_range<N>(p, k, p.nactive, sops, sw, blockIdx.x * nw + warp, gridDim.x * nw, ntiles, true);
   if (injected != 0.0) atomicAdd(p.s.acc, injected);
 }
 

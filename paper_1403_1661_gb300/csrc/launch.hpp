@@ -16,6 +16,7 @@ struct KernelCfg {
   int smem_lim = 0;        // the per-element operators (limiter kernels)
   int grid_stage = 0, grid_pos = 0, grid_tvb = 0, grid_stats = 0;
   int smem_tc = 0, grid_tc = 0;   // tensor-core stage kernel (FP32 only)
+  int tc_warps = 4;               // warps per CTA of the tensor-core stage and batch kernels
   int grid_stage_g = 0;           // stage kernel with the operators in global memory
   int grid_split_t = 0, grid_split_v = 0, grid_split_s = 0;   // kernel-split ablation
   int smem_batch = 0, occ_batch = 0;         // persistent batch kernel, SIMT body
@@ -41,6 +42,10 @@ struct Launchers {
   // Persistent batch kernel over a group of scenarios of this order (tc: the
   // tensor-core stage body, FP32 only), grid CTAs.
   cudaError_t (*batch)(const BatchLaunch<T>& bl, bool tc, int grid, const KernelCfg&, cudaStream_t);
+  // Warps per CTA of the tensor-core kernels (FP32 only): sets tc_warps, their
+  // shared memory and grids in cfg; cudaErrorInvalidValue when that many warps'
+  // tiles do not fit on an SM.
+  cudaError_t (*tc_config)(KernelCfg* cfg, int warps);
 };
 
 // Registered per order by kernels_n*.cu; nullptr when the order is not built.

@@ -137,6 +137,7 @@ struct swe_solver {
   size_t ws_bytes = 0;
   Layout lay;
   swe::KernelCfg cfg;
+  int ctas_per_sm = 0;           // cap of swe_set_launch_config (0 = as many as fit)
   const swe::Launchers<float>* lf = nullptr;
   const swe::Launchers<double>* ld = nullptr;
   // host copies
@@ -1598,22 +1599,42 @@ int swe_level_info(const swe_solver* s, int32_t* L, int32_t* counts, double* dt_
   return SWE_OK;
 }
 
-int swe_set_launch_config(swe_solver* s, int32_t ctas_per_sm) {
-  if (!s || ctas_per_sm < 0) return fail(SWE_EINVAL, "bad arguments");
+namespace {
+// s->cfg from the occupancy limits in s->cfg_max and the solver's CTA cap
+int apply_launch_config(swe_solver* s) {
   int dev = 0, nsm = 0;
   SWE_CUDA(cudaGetDevice(&dev));
   SWE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   auto cap = [&](int maxgrid) {
-    if (ctas_per_sm == 0) return maxgrid;
-    const int g = nsm * ctas_per_sm;
+    if (s->ctas_per_sm == 0) return maxgrid;
+    const int g = nsm * s->ctas_per_sm;
     return g < maxgrid ? g : maxgrid;
   };
+  s->cfg = s->cfg_max;
   s->cfg.grid_stage = cap(s->cfg_max.grid_stage);
   s->cfg.grid_tc = cap(s->cfg_max.grid_tc);
   s->cfg.grid_tvb = cap(s->cfg_max.grid_tvb);
   s->cfg.grid_pos = cap(s->cfg_max.grid_pos);
   invalidate_graph(s);
   return SWE_OK;
+}
+}  // namespace
+
+int swe_set_launch_config(swe_solver* s, int32_t ctas_per_sm) {
+  if (!s || ctas_per_sm < 0) return fail(SWE_EINVAL, "bad arguments");
+  s->ctas_per_sm = ctas_per_sm;
+  return apply_launch_config(s);
+}
+
+int swe_set_tc_warps(swe_solver* s, int32_t warps) {
+  if (!s) return fail(SWE_EINVAL, "bad arguments");
+  if (!s->tc) return fail(SWE_EUNSUPPORTED, "warps per CTA apply to the FP32 tensor-core tier only");
+  swe::KernelCfg c = s->cfg_max;
+  const cudaError_t e = s->lf->tc_config(&c, warps);
+  if (e == cudaErrorInvalidValue) return fail(SWE_EINVAL, "that many warps per CTA do not fit on an SM (1..8)");
+  if (e != cudaSuccess) return fail(SWE_ECUDA, std::string("tc_config: ") + cudaGetErrorString(e));
+  s->cfg_max = c;
+  return apply_launch_config(s);
 }
 
 int swe_set_farfield(swe_solver* s, int32_t enable, double h, double hu, double hv) {

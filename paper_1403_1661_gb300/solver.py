@@ -288,8 +288,20 @@ class Solver:
         nat.check(nat.lib().swe_kernel_launches(self.handle, C.byref(n)), "swe_kernel_launches")
         return n.value
 
-    def set_launch_config(self, ctas_per_sm):
-        nat.check(nat.lib().swe_set_launch_config(self.handle, int(ctas_per_sm)), "swe_set_launch_config")
+    def set_launch_config(self, shape):
+        """A launch shape: CTAs per SM of the grid-stride kernels (an int, 0 = as
+        many as fit), or a dict {"ctas_per_sm": c, "tc_warps": w} as the autotuner
+        returns it (tc_warps: warps per CTA of the tensor-core kernels)."""
+        if isinstance(shape, dict):
+            nat.check(nat.lib().swe_set_launch_config(self.handle, int(shape.get("ctas_per_sm", 0))),
+                      "swe_set_launch_config")
+            if shape.get("tc_warps") is not None:
+                self.set_tc_warps(shape["tc_warps"])
+        else:
+            nat.check(nat.lib().swe_set_launch_config(self.handle, int(shape)), "swe_set_launch_config")
+
+    def set_tc_warps(self, warps):
+        nat.check(nat.lib().swe_set_tc_warps(self.handle, int(warps)), "swe_set_tc_warps")
 
     def profile_substeps(self, n):
         """Run n substeps with CUDA events around every kernel; per-kernel totals."""

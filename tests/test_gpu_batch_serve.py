@@ -121,10 +121,11 @@ def test_served_results_equal_alone():
 
 def test_autotuner_and_launch_config_do_not_change_results():
     import paper_1403_1661_gb300 as P
+    from paper_1403_1661_gb300 import _native as nat
     from paper_1403_1661_gb300 import batch
     before = open(batch.CACHE).read() if os.path.exists(batch.CACHE) else None
-    best = P.tune(3, "fp32tc", candidates=(1, 0), reps=1, force=True)
-    assert best in (1, 0)
+    best = P.tune(3, "fp32tc", candidates=((1, 4), (0, 2), (0, 8)), reps=1, force=True)
+    assert (best["ctas_per_sm"], best["tc_warps"]) in ((1, 4), (0, 2), (0, 8))
     # a narrower search leaves the cached full-search results alone
     after = open(batch.CACHE).read() if os.path.exists(batch.CACHE) else None
     assert after == before
@@ -136,6 +137,27 @@ def test_autotuner_and_launch_config_do_not_change_results():
     b.step(2)
     for u, v in zip(a.get_state()[:3], b.get_state()[:3]):
         assert np.array_equal(u, v)
+    # warps per tensor-core CTA: every count that fits gives the same state, alone
+    # and in a batch; one that does not fit is refused
+    scn5 = sc.tsunami(nx=40, ny=10, N=5, nlevels=4)
+    ref = P.solver_from_scenario(scn5, precision="fp32tc")
+    ref.step(2)
+    want = ref.get_state()[:3]
+    for w in (1, 3, 7):
+        c = P.solver_from_scenario(scn5, precision="fp32tc")
+        c.set_tc_warps(w)
+        c.step(2)
+        for u, v in zip(want, c.get_state()[:3]):
+            assert np.array_equal(u, v)
+        d = P.solver_from_scenario(scn5, precision="fp32tc")
+        d.set_launch_config({"ctas_per_sm": 0, "tc_warps": w})
+        bb = P.Batch([d], max_macro=2)
+        bb.step(2)
+        for u, v in zip(want, d.get_state()[:3]):
+            assert np.array_equal(u, v)
+        bb.close()
+    with pytest.raises(nat.SWEError):
+        ref.set_tc_warps(8)        # 8 x 29 KB of N = 5 tiles exceed an SM's shared memory
 
 
 def test_full_ensemble_batch_equals_alone_on_a_sample():
