@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-colloc", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-scenarios", type=int, default=64)
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--oracle-configs", action="store_true")
     ap.add_argument("--oracle-configs-child", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -625,7 +625,22 @@ def run_served(args):
                  factory=GpuFactory(args.precision))
     out = srv.run(reqs)
     torch.cuda.synchronize()
+    # stage-kernel algorithmic bytes of every element-stage served, over the wall time
+    ts = 4 if args.precision != "fp64" else 8
+    byts = 0.0
+    for r in out["done"]:
+        N = r.scenario.N
+        # a DOF-update is one field (eta, hu, hv) at one node: 3 Np per element-stage
+        byts += r.dof_updates / (3 * (N + 1) * (N + 2) // 2) * stage_bytes_per_element(N, ts)
+    peak, peak_kind = measured_peaks()
+    ach = byts / out["wall_s"] / 1e9
+    offered = sum(r.dof_updates for r in out["done"]) / args.serve_seconds
     return {"requests": out["requests"], "p50_s": out["p50_s"], "p99_s": out["p99_s"], "mean_s": out["mean_s"],
+            "offered_dof_per_s": offered,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "basis": "stage-kernel algorithmic bytes of every element-stage of the served requests "
+                                  "over the wall time (TVB and host work not counted)",
+                         "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"},
             "aggregate_dof_per_s": out["aggregate_dof_per_s"], "wall_s": out["wall_s"],
             "peak_running": out["peak_running"], "peak_gb": out["peak_bytes"] / 1e9,
             "rejected": out["rejected"], "failed": out["failed"],

@@ -18,10 +18,13 @@
 //           MMAs of the tile into a TMEM accumulator and commits them to an
 //           mbarrier; the A tile is double-buffered, so the next tile's flux is
 //           computed while the tensor core reads the previous one. After the last
-//           tile each warp reads its 32 TMEM lanes back with tcgen05.ld.
+//           tile each warp reads its 32 TMEM lanes back with tcgen05.ld;
+//   impl 2  impl 1 through four A buffers synchronised by mbarriers only;
+//   impl 3, 4  impl 1 with N = 64 or 128 (the operator's columns repeated);
+//   impl 5  the flux stored to TMEM (tcgen05.st) and read by the MMA as A.
 //
-// Both accumulate D = sum over the CTA's tiles of A_t B and write it once, so the
-// timed work is flux generation plus projection; both round the operands to TF32
+// All accumulate D = sum over the CTA's tiles of A_t B and write it once, so the
+// timed work is flux generation plus projection; all round the operands to TF32
 // the same way (cvt.rna), so their results agree up to summation order.
 #include <cuda_runtime.h>
 

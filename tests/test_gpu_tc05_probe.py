@@ -1,9 +1,9 @@
 """The volume-projection probe (Section 7.1's N(Q) = Pr cF1 + ..., one field, N = 4
 shapes) on both tensor-core paths: warp-level mma.sync and tcgen05 with a TMEM
 accumulator (variants: CTA barriers, an mbarrier pipeline, wider instructions that
-repeat the operator's columns, and the flux stored to TMEM as the A operand). All must equal the product written
-out in numpy with the same TF32 operand rounding; the timings are printed for the
-design notes."""
+repeat the operator's columns, and the flux stored to TMEM as the A operand). All
+must equal the product written out in numpy with the same TF32 operand rounding;
+the timings are printed for the design notes."""
 import ctypes as C
 
 import numpy as np
