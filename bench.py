@@ -619,10 +619,12 @@ def run_served(args):
     import torch
     from paper_1403_1661_gb300.serve import GpuFactory, Server, requests_from_stream
     from workloads import scenarios as sc
+    import paper_1403_1661_gb300 as P
     stream = sc.served_stream(duration=args.serve_seconds)
     reqs = requests_from_stream(stream, substeps=500)
+    tuned = {N: P.tune(N, args.precision) for N in sorted({r.scenario.N for r in reqs})}
     srv = Server(budget_bytes=150e9, max_slots=64, macro_per_round=4, prep_workers=8, start_workers=8,
-                 factory=GpuFactory(args.precision))
+                 factory=GpuFactory(args.precision, tuned=tuned))
     out = srv.run(reqs)
     torch.cuda.synchronize()
     # stage-kernel algorithmic bytes of every element-stage served, over the wall time
@@ -643,6 +645,7 @@ def run_served(args):
                          "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"},
             "aggregate_dof_per_s": out["aggregate_dof_per_s"], "wall_s": out["wall_s"],
             "peak_running": out["peak_running"], "peak_gb": out["peak_bytes"] / 1e9,
+            "autotuned": {str(k): v for k, v in tuned.items()},
             "rejected": out["rejected"], "failed": out["failed"],
             "arrivals": f"Poisson 50/s for {args.serve_seconds:.0f} s, K log-uniform 2k-1M, N in {{2,3,4}}, "
                         f"500 MRAB substeps each, HBM budget 150 GB; 8 preparation and 8 creation threads"}
