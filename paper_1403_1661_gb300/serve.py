@@ -28,6 +28,7 @@ retired at its next idle point without a result.
 from __future__ import annotations
 
 import collections
+import contextlib
 import concurrent.futures as cf
 import dataclasses
 import math
@@ -214,8 +215,10 @@ class Server:
             r.admitted = self.clock() - t0
             running.append([r, job, int(math.ceil(r.substeps / job.macro_period)), 0])
 
-        starter = cf.ThreadPoolExecutor(max_workers=self.start_workers) if self.start_workers > 0 else None
-        with cf.ThreadPoolExecutor(max_workers=self.prep_workers) as pool:
+        with contextlib.ExitStack() as pools:   # both pools shut down however the loop ends
+            pool = pools.enter_context(cf.ThreadPoolExecutor(max_workers=self.prep_workers))
+            starter = (pools.enter_context(cf.ThreadPoolExecutor(max_workers=self.start_workers))
+                       if self.start_workers > 0 else None)
             while pending or preparing or ready or starting or running:
                 now = self.clock() - t0
                 progressed = False
@@ -315,8 +318,6 @@ class Server:
                 if not progressed:
                     nxt = pending[0].arrival - (self.clock() - t0) if pending else 0.0
                     self.sleep(max(0.0002, min(nxt, 0.002)))
-        if starter is not None:
-            starter.shutdown(wait=True)
         wall = self.clock() - t0
         lat = np.array([r.finished - r.arrival for r in done]) if done else np.zeros(1)
         dofs = sum(r.dof_updates for r in done)
