@@ -286,8 +286,10 @@ int swe_level_info(const swe_solver* solver, int32_t* L, int32_t* counts, double
  * (Algorithms 1-3 per scenario, unchanged). The solvers are grouped by precision
  * tier and scheme / order (at most 48 per group); each group is advanced by ONE
  * persistent kernel that takes its work from a device queue of tickets, one ticket
- * being a tile of 128 elements of one phase (the stage kernel or the TVB limiter of
- * one finest substep) of one scenario. Tickets are ordered phase by phase,
+ * being a tile of elements (64 of the stage kernel's phase, 128 of the TVB
+ * limiter's, each phase one finest substep) of one scenario, taken by one warp. The
+ * kernel's CTAs have the warps per CTA of the group's first solver
+ * (swe_set_tc_warps on the tensor-core tier). Tickets are ordered phase by phase,
  * round-robin over the scenarios, and a ticket waits (bounded in time) until every
  * tile of its scenario's earlier phases is complete, so uneven scenarios fill each
  * other's gaps. One batch step is one replay of a captured CUDA graph (per group:
