@@ -162,6 +162,15 @@ int swe_solver_create(const swe_mesh* mesh, const swe_params* params,
                       void* dev_workspace, size_t bytes, void* stream, swe_solver** out);
 void swe_solver_destroy(swe_solver* solver);
 
+/* A new non-blocking CUDA stream (cudaStream_t) for one solver or batch, and its
+ * release (waits for the stream's work first). Each solver needs a stream of its
+ * own: its macro step is captured into a CUDA graph on that stream, and work that
+ * another thread enqueues on a stream while it is capturing invalidates the
+ * capture. Stream pools that hand the same stream to several users therefore do
+ * not fit. SWE_EINVAL for a NULL argument, SWE_ECUDA when the runtime fails. */
+int swe_stream_create(void** out);
+int swe_stream_destroy(void* stream);
+
 /* Nodal bathymetry B (K x Np, host, FP64). Must precede swe_set_state. */
 int swe_set_bathymetry(swe_solver* solver, const double* B);
 

@@ -68,6 +68,8 @@ SIGNATURES = {
     "swe_workspace_bytes": (C.c_int, [_vp, C.POINTER(swe_params), C.POINTER(C.c_size_t)]),
     "swe_solver_create": (C.c_int, [_vp, C.POINTER(swe_params), _vp, C.c_size_t, _vp, C.POINTER(_vp)]),
     "swe_solver_destroy": (None, [_vp]),
+    "swe_stream_create": (C.c_int, [C.POINTER(C.c_void_p)]),
+    "swe_stream_destroy": (C.c_int, [_vp]),
     "swe_set_bathymetry": (C.c_int, [_vp, _dp]),
     "swe_set_state": (C.c_int, [_vp, _dp, _dp, _dp]),
     "swe_setup_levels": (C.c_int, [_vp, _ip, _dp]),

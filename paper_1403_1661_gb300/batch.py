@@ -11,6 +11,7 @@ import numpy as np
 
 from . import _native as nat
 from .build import BUILD
+from .solver import own_stream, release_stream
 
 
 class Batch:
@@ -29,8 +30,9 @@ class Batch:
         nbytes = C.c_size_t()
         nat.check(nat.lib().swe_batch_workspace_bytes(handles, n, self.max_macro, C.byref(nbytes)),
                   "swe_batch_workspace_bytes")
+        self._own_stream = None
         with torch.cuda.device(dev):
-            self.stream = torch.cuda.Stream(dev) if stream is None else stream
+            self.stream = own_stream(self) if stream is None else stream
             self.workspace = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=dev)
         h = C.c_void_p()
         with torch.cuda.device(dev):
@@ -76,6 +78,7 @@ class Batch:
             nat.lib().swe_batch_destroy(self.handle)
             self.handle = None
             self.workspace = None
+        release_stream(self)
 
     def __del__(self):
         try:

@@ -1193,6 +1193,23 @@ void swe_solver_destroy(swe_solver* solver) {
   delete solver;
 }
 
+int swe_stream_create(void** out) {
+  if (!out) return fail(SWE_EINVAL, "NULL argument");
+  *out = nullptr;
+  cudaStream_t st = nullptr;
+  SWE_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  *out = st;
+  return SWE_OK;
+}
+
+int swe_stream_destroy(void* stream) {
+  if (!stream) return fail(SWE_EINVAL, "NULL stream");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  SWE_CUDA(cudaStreamSynchronize(st));
+  SWE_CUDA(cudaStreamDestroy(st));
+  return SWE_OK;
+}
+
 int swe_set_bathymetry(swe_solver* s, const double* B) {
   if (!s || !B) return fail(SWE_EINVAL, "NULL argument");
   const size_t n = (size_t)s->K * s->Np;

@@ -133,9 +133,12 @@ class Solver:
         nat.check(L.swe_workspace_bytes(mesh.handle, C.byref(self.prm), C.byref(nbytes)),
                   "swe_workspace_bytes")
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self._own_stream = None
         with torch.cuda.device(self.device):
-            # a stream of its own: CUDA graphs cannot be captured on the legacy default stream
-            self.stream = torch.cuda.Stream(self.device) if stream is None else stream
+            # a stream of its own (not one from torch's pool, which hands the same
+            # stream to several users): the macro step is captured into a CUDA graph
+            # on it, and work another thread enqueues there meanwhile would void that
+            self.stream = own_stream(self) if stream is None else stream
             self.workspace = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=self.device)
             self.stream.wait_stream(torch.cuda.current_stream(self.device))
         base = self.workspace.data_ptr()
@@ -328,12 +331,30 @@ class Solver:
             nat.lib().swe_solver_destroy(self.handle)
             self.handle = None
             self.workspace = None
+        release_stream(self)
 
     def __del__(self):
         try:
             self.close()
         except Exception:
             pass
+
+
+def own_stream(owner):
+    """A dedicated non-blocking stream created by the library, wrapped for torch;
+    owner._own_stream keeps the handle for release_stream."""
+    import torch
+    h = C.c_void_p()
+    nat.check(nat.lib().swe_stream_create(C.byref(h)), "swe_stream_create")
+    owner._own_stream = h.value
+    return torch.cuda.ExternalStream(h.value, device=torch.cuda.current_device())
+
+
+def release_stream(owner):
+    h = getattr(owner, "_own_stream", None)
+    if h:
+        owner._own_stream = None
+        nat.lib().swe_stream_destroy(C.c_void_p(h))
 
 
 def scenario_inputs(scn, mesh: Mesh):
