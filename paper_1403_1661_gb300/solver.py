@@ -207,8 +207,9 @@ class Solver:
         cur = torch.cuda.current_stream(self.device)
         self.stream.wait_stream(cur)
         nat.check(nat.lib().swe_rhs(self.handle, C.c_void_p(out.data_ptr())), "swe_rhs")
+        # the caller's stream waits for the solver's: out stays the caller stream's
+        # tensor (no record_stream, which would tie it to a stream that close() ends)
         cur.wait_stream(self.stream)
-        out.record_stream(self.stream)
         return out
 
     def rhs_variant(self, variant, scratch=None):
@@ -230,9 +231,6 @@ class Solver:
         nat.check(nat.lib().swe_rhs_variant(self.handle, int(variant), C.c_void_p(out.data_ptr()), sp, sb),
                   "swe_rhs_variant")
         cur.wait_stream(self.stream)
-        out.record_stream(self.stream)
-        if need.value:
-            scratch.record_stream(self.stream)
         return out
 
     def rhs_scratch_bytes(self, variant):
