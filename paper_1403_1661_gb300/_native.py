@@ -41,7 +41,7 @@ class swe_params(C.Structure):
     _fields_ = [("g", C.c_double), ("h0", C.c_double), ("eps", C.c_double), ("tvb_M", C.c_double),
                 ("tvb_nu", C.c_double), ("cfl", C.c_double), ("N", C.c_int32),
                 ("nlevels_max", C.c_int32), ("precision", C.c_int32), ("limiter_mask", C.c_int32),
-                ("dry_mode", C.c_int32), ("scheme", C.c_int32)]
+                ("dry_mode", C.c_int32), ("scheme", C.c_int32), ("compensated", C.c_int32)]
 
 
 _dp = C.POINTER(C.c_double)

@@ -124,6 +124,8 @@ struct DevState {
   double* acc;          // accumulators: [0] injected mass
   int* flags;           // [0] non-finite state detected
   long long* macro;     // macro-step counter (advanced on the device)
+  T* comp;              // [NP][KS] rounding error of the last elevation update, or nullptr
+                        // (not compensated)
 };
 
 struct Sched {

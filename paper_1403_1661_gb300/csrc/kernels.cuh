@@ -543,8 +543,11 @@ __device__ __forceinline__ void add_reference_pressure(const T* __restrict__ sop
 }
 
 // Adams-Bashforth commit (Algorithm 1) and positivity limiter (Algorithm 3) of
-// element e (mode 0), or the R output in the caller's layout (mode 1).
-template <typename T, int N>
+// element e (mode 0), or the R output in the caller's layout (mode 1). kComp: the
+// elevation's increments are summed first and added to the state with the rounding
+// error of the previous update subtracted (a compensated sum, p.s.comp), so the
+// single-precision state does not drift in total mass step after step.
+template <typename T, int N, bool kComp = false>
 __device__ __forceinline__ void commit_and_limit(const StageParams<T>& p, const T* __restrict__ sops, int e,
                                                  int lev, long long a, T (&eta)[Dims<N>::NPP],
                                                  T (&hu)[Dims<N>::NPP], T (&hv)[Dims<N>::NPP],
@@ -590,12 +593,17 @@ __device__ __forceinline__ void commit_and_limit(const StageParams<T>& p, const 
   ab_partial_weights<T>(depth, T(0.5), wh);
   const T m0 = dtl * wh[0], m1 = dtl * wh[1], m2 = dtl * wh[2];
   T x0[NP], x1[NP], x2[NP];
+  T d0[kComp ? NP : 1];   // compensated: the elevation's increment of this step
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
     x0[i] = eta[i] + m0 * R0[i];
     x1[i] = hu[i] + m0 * R1[i];
     x2[i] = hv[i] + m0 * R2[i];
-    eta[i] += c0 * R0[i];
+    if constexpr (kComp) {
+      d0[i] = c0 * R0[i];
+    } else {
+      eta[i] += c0 * R0[i];
+    }
     hu[i] += c0 * R1[i];
     hv[i] += c0 * R2[i];
   }
@@ -606,12 +614,28 @@ __device__ __forceinline__ void commit_and_limit(const StageParams<T>& p, const 
     for (int i = 0; i < NP; ++i) {
       const T r0 = ldm(rs + i * ks), r1 = ldm(rs + fstride + i * ks);
       const T r2 = ldm(rs + 2 * fstride + i * ks);
-      eta[i] += cs * r0;
+      if constexpr (kComp) {
+        d0[i] += cs * r0;
+      } else {
+        eta[i] += cs * r0;
+      }
       hu[i] += cs * r1;
       hv[i] += cs * r2;
       x0[i] += ms * r0;
       x1[i] += ms * r1;
       x2[i] += ms * r2;
+    }
+  }
+  if constexpr (kComp) {
+    // eta + d with the previous rounding error c taken back: y = d - c, t = eta + y,
+    // and the new error c = (t - eta) - y (exact when |eta| >= |y|)
+    T* cp = p.s.comp + eo;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      const T y = d0[i] - ldm(cp + i * ks);
+      const T t = eta[i] + y;
+      cp[i * ks] = (t - eta[i]) - y;
+      eta[i] = t;
     }
   }
   if ((__ldg(reinterpret_cast<const int*>(p.s.conn + e) + 3) >> 12) & 1) {
@@ -706,8 +730,8 @@ __device__ __forceinline__ void volume_term(const T* __restrict__ sops, const T 
 
 // One element of the stage: R(Q) (volume + surface + lift), then the
 // Adams-Bashforth commit and the positivity limiter (mode 0) or R only (mode 1).
-// k is the finest substep count of the schedule.
-template <typename T, int N>
+// k is the finest substep count of the schedule; kComp: compensated elevation update.
+template <typename T, int N, bool kComp = false>
 __device__ __forceinline__ void stage_element(const StageParams<T>& p, const T* __restrict__ sops, int e,
                                               long long k, double* injected) {
   using D = Dims<N>;
@@ -741,23 +765,24 @@ __device__ __forceinline__ void stage_element(const StageParams<T>& p, const T* 
   auto own = [&](int f, int jn) -> T { return f == 0 ? eta[jn] : (f == 1 ? hu[jn] : (f == 2 ? hv[jn] : bb[jn])); };
   surface_lift<T, N, false>(p, sops, e, k, own, rx, ry, sx, sy, md, R0, R1, R2);
   add_reference_pressure<T, N>(sops, eta, bb, g, rx, ry, sx, sy, R1, R2);
-  commit_and_limit<T, N>(p, sops, e, lev, a, eta, hu, hv, bb, rx, ry, sx, sy, R0, R1, R2, injected);
+  commit_and_limit<T, N, kComp>(p, sops, e, lev, a, eta, hu, hv, bb, rx, ry, sx, sy, R0, R1, R2, injected);
 }
 
 // Elements e0, e0 + step, ... below e1 of the stage; returns the mass the
 // positivity limiter's dry resets injected (inlined by the separate launch and the
 // persistent batch kernel alike).
-template <typename T, int N>
+template <typename T, int N, bool kComp = false>
 __device__ __forceinline__ double stage_range(const StageParams<T>& __restrict__ p, const T* __restrict__ sops,
                                            int e0, int step, int e1, long long k) {
   double injected = 0.0;
-  for (int e = e0; e < e1; e += step) stage_element<T, N>(p, sops, e, k, &injected);
+  for (int e = e0; e < e1; e += step) stage_element<T, N, kComp>(p, sops, e, k, &injected);
   return injected;
 }
 
 // kGlobalOps: the operators are read from global memory (through L1) instead of
 // the block's shared-memory copy (the operator-placement comparison of Section 7.4).
-template <typename T, int N, bool kGlobalOps = false>
+// kComp: compensated elevation update (p.s.comp).
+template <typename T, int N, bool kGlobalOps = false, bool kComp = false>
 __global__ void __launch_bounds__(kBlock) k_stage(const __grid_constant__ StageParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const T* sops;
@@ -774,8 +799,8 @@ __global__ void __launch_bounds__(kBlock) k_stage(const __grid_constant__ StageP
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p.nactive; e += gridDim.x * blockDim.x)
       stage_element<T, N>(p, sops, e, k, &injected);
   } else {
-    injected = stage_range<T, N>(p, sops, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x,
-                                 p.nactive, k);
+    injected = stage_range<T, N, kComp>(p, sops, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x,
+                                        p.nactive, k);
   }
   if (injected != 0.0) atomicAdd(p.s.acc, injected);
 }

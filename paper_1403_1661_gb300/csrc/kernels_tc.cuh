@@ -96,8 +96,8 @@ struct TcSmem {
 // volume term and lift on tensor cores, commit and limiter. k: the finest substep
 // count of the schedule; nactive: elements [0, nactive) are active at this substep;
 // next_tile: the warp's next tile (its planes are prefetched to L2), or -1; sw: the
-// warp's shared tiles.
-template <int N>
+// warp's shared tiles; kComp: compensated elevation update in the commit.
+template <int N, bool kComp = false>
 __device__ __forceinline__ void stage_tc_warp(const StageParams<float>& p, long long k, int nactive,
                                               const float* sops, float* sw, int tile, int next_tile,
                                               double* injected) {
@@ -169,6 +169,8 @@ __device__ __forceinline__ void stage_tc_warp(const StageParams<float>& p, long 
         const float* rs = p.s.ring + (size_t)((a0 - s) % 3) * bstride + e0;
         for (int pl = lane; pl < 3 * NP; pl += 32) prefetch_l2(rs + pl * ks);
       }
+      if constexpr (kComp)
+        for (int pl = lane; pl < NP; pl += 32) prefetch_l2(p.s.comp + e0 + pl * ks);
     }
   }
 
@@ -484,7 +486,7 @@ __device__ __forceinline__ void stage_tc_warp(const StageParams<float>& p, long 
       hv[i] = my[(2 * KP + i) * LS];
       bb[i] = my[(3 * KP + i) * LS];
     }
-    commit_and_limit<float, N>(p, sops, e, lev, a, eta, hu, hv, bb, ge.x, ge.y, ge.z, ge.w, R0, R1, R2,
+    commit_and_limit<float, N, kComp>(p, sops, e, lev, a, eta, hu, hv, bb, ge.x, ge.y, ge.z, ge.w, R0, R1, R2,
                                injected);
   }
   __syncwarp();
@@ -495,19 +497,19 @@ __device__ __forceinline__ void stage_tc_warp(const StageParams<float>& p, long 
 // the mass the positivity limiter's dry resets injected. The separate launch and
 // the persistent batch kernel both inline it (out of line the body ran 1.5 times
 // slower: its parameters become memory loads).
-template <int N>
+template <int N, bool kComp = false>
 __device__ __forceinline__ double stage_tc_range(const StageParams<float>& __restrict__ p, long long k,
                                               int nactive, const float* __restrict__ sops, float* sw, int t0,
                                               int step, int t1, bool prefetch) {
   double injected = 0.0;
   for (int tile = t0; tile < t1; tile += step)
-    stage_tc_warp<N>(p, k, nactive, sops, sw, tile, prefetch ? tile + step : -1, &injected);
+    stage_tc_warp<N, kComp>(p, k, nactive, sops, sw, tile, prefetch ? tile + step : -1, &injected);
   return injected;
 }
 
-template <int N>
 // CTA: blockDim.x / 32 warps (1 to kTcMaxWarps), each with its own shared tiles after
-// the CTA's operator copy.
+// the CTA's operator copy. kComp: compensated elevation update (p.s.comp).
+template <int N, bool kComp = false>
 __global__ void __launch_bounds__(kTcMaxBlock, 1) k_stage_tc(const __grid_constant__ StageParams<float> p) {
   using SM = TcSmem<N>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -523,7 +525,7 @@ __global__ void __launch_bounds__(kTcMaxBlock, 1) k_stage_tc(const __grid_consta
   const long long k = (*p.s.macro) * (1LL << (p.sc.L - 1)) + p.j;
   const int ntiles = (p.nactive + 31) / 32;
   const double injected =
-      stage_tc_range<N>(p, k, p.nactive, sops, sw, blockIdx.x * nw + warp, gridDim.x * nw, ntiles, true);
+      stage_tc_range<N, kComp>(p, k, p.nactive, sops, sw, blockIdx.x * nw + warp, gridDim.x * nw, ntiles, true);
   if (injected != 0.0) atomicAdd(p.s.acc, injected);
 }
 

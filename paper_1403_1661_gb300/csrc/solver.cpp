@@ -50,13 +50,15 @@ int np_of(int N) { return (N + 1) * (N + 2) / 2; }
 int ks_of(int K) { return (K + 31) / 32 * 32; }
 
 struct Layout {
-  size_t q, ring, qmid, B, p1, vb, xfer, bcaller, iperm, xflag, geo, conn, tvbg, means, dry, Bbar, ops, tcops, perm, acc, flags, macro, partials, total;
+  size_t comp, q, ring, qmid, B, p1, vb, xfer, bcaller, iperm, xflag, geo, conn, tvbg, means, dry, Bbar, ops, tcops, perm, acc, flags, macro, partials, total;
   int nb_stats;
 };
 
 int tc_size_of(int N);
 
-Layout make_layout(int K, int N, size_t ts, int op_size, int code) {
+// comp: the compensation plane of the surface elevation (single-precision tiers
+// with compensated = 1), else empty
+Layout make_layout(int K, int N, size_t ts, int op_size, int code, bool comp) {
   Layout L;
   const size_t plane = (size_t)np_of(N) * (size_t)ks_of(K);   // one field, all nodes
   size_t off = 0;
@@ -87,6 +89,7 @@ Layout make_layout(int K, int N, size_t ts, int op_size, int code) {
   L.acc = take(8 * 8);
   L.flags = take(4 * 4);
   L.macro = take(8);
+  L.comp = take(comp ? plane * ts : 0);
   L.nb_stats = std::max(1, std::min(1024, (K + 255) / 256));
   L.partials = take((size_t)L.nb_stats * 2 * 8 + 16);
   L.total = off;
@@ -107,6 +110,7 @@ int check_params(const swe_params* p) {
   if (p->scheme != SWE_SCHEME_CUBATURE && p->scheme != SWE_SCHEME_COLLOCATION &&
       p->scheme != SWE_SCHEME_CUBATURE_2N)
     return fail(SWE_EINVAL, "unknown scheme");
+  if (p->compensated != 0 && p->compensated != 1) return fail(SWE_EINVAL, "compensated must be 0 or 1");
   return SWE_OK;
 }
 
@@ -131,6 +135,7 @@ struct swe_solver {
   int KS = 0;                    // element stride of the device node planes
   bool fp64 = false;
   bool tc = false;   // FP32 with tensor-core volume contractions
+  bool comp = false; // single precision with a compensated surface-elevation update
   size_t ts = 4;
   cudaStream_t stream = nullptr;
   char* ws = nullptr;
@@ -219,6 +224,7 @@ swe::DevState<T> dev_state(swe_solver* s) {
   d.acc = reinterpret_cast<double*>(w + s->lay.acc);
   d.flags = reinterpret_cast<int*>(w + s->lay.flags);
   d.macro = reinterpret_cast<long long*>(w + s->lay.macro);
+  d.comp = s->comp ? reinterpret_cast<T*>(w + s->lay.comp) : nullptr;
   return d;
 }
 
@@ -629,6 +635,13 @@ int invalidate_graph(swe_solver* s) {
   return SWE_OK;
 }
 
+// The compensation plane starts at zero whenever the state is set or re-ordered
+// from the host (it holds at most one rounding of each node's elevation).
+int clear_comp(swe_solver* s) {
+  if (s->comp) SWE_CUDA(cudaMemsetAsync(s->ws + s->lay.comp, 0, (size_t)s->Np * s->KS * s->ts, s->stream));
+  return SWE_OK;
+}
+
 int reset_counters(swe_solver* s) {
   s->k = 0;
   SWE_CUDA(cudaMemsetAsync(s->ws + s->lay.macro, 0, 8, s->stream));
@@ -843,6 +856,7 @@ int apply_levels(swe_solver* s, const std::vector<int32_t>& level, double dt_min
     rc = s->fp64 ? upload_raw_t<double>(s, raw) : upload_raw_t<float>(s, raw);
     if (rc) return rc;
     if ((rc = reset_counters(s))) return rc;
+    if ((rc = clear_comp(s))) return rc;
     // recompute the means of the re-ordered state (positivity pass, no limiting),
     // then restore the dry flags of the latest positivity pass
     if ((rc = launch_limit(s, 0, 0, 0, s->K))) return rc;
@@ -920,6 +934,7 @@ int regroup_t(swe_solver* s, const std::vector<int32_t>& lev_new) {
   };
   int rc;
   if ((rc = planes(ring, 9 * np))) return rc;
+  if (s->comp && (rc = planes(reinterpret_cast<T*>(s->ws + s->lay.comp), np))) return rc;
   if ((rc = planes(reinterpret_cast<T*>(s->ws + s->lay.B), np))) return rc;
   if ((rc = planes(reinterpret_cast<T*>(s->ws + s->lay.vb), 3))) return rc;
   if ((rc = planes(reinterpret_cast<T*>(s->ws + s->lay.p1), 9))) return rc;
@@ -1130,7 +1145,8 @@ int swe_workspace_bytes(const swe_mesh* mesh, const swe_params* params, size_t* 
   const bool fp64 = params->precision == SWE_FP64;
   int opsz = fp64 ? swe::launchers_for<double>(scheme_code(params))->op_size
                   : swe::launchers_for<float>(scheme_code(params))->op_size;
-  *bytes = make_layout(mesh->m.K, params->N, fp64 ? 8 : 4, opsz, scheme_code(params)).total;
+  *bytes = make_layout(mesh->m.K, params->N, fp64 ? 8 : 4, opsz, scheme_code(params),
+                       !fp64 && params->compensated).total;
   return SWE_OK;
 }
 
@@ -1155,6 +1171,7 @@ int swe_solver_create(const swe_mesh* mesh, const swe_params* params, void* dev_
   s->KS = ks_of(s->K);
   s->fp64 = params->precision == SWE_FP64;
   s->tc = params->precision == SWE_FP32_TC;
+  s->comp = !s->fp64 && params->compensated;
   s->ts = s->fp64 ? 8 : 4;
   s->stream = reinterpret_cast<cudaStream_t>(stream);
   s->ws = reinterpret_cast<char*>(dev_workspace);
@@ -1166,7 +1183,7 @@ int swe_solver_create(const swe_mesh* mesh, const swe_params* params, void* dev_
     s->lf = swe::launchers_for<float>(s->code);
     if (!s->lf) return fail(SWE_EUNSUPPORTED, "order not built");
   }
-  s->lay = make_layout(s->K, s->N, s->ts, s->fp64 ? s->ld->op_size : s->lf->op_size, s->code);
+  s->lay = make_layout(s->K, s->N, s->ts, s->fp64 ? s->ld->op_size : s->lf->op_size, s->code, s->comp);
   if (bytes < s->lay.total) return fail(SWE_ENOMEM, "workspace smaller than swe_workspace_bytes()");
   cudaError_t ce = s->fp64 ? s->ld->prepare(&s->cfg) : s->lf->prepare(&s->cfg);
   if (ce != cudaSuccess) return fail(SWE_ECUDA, std::string("kernel setup: ") + cudaGetErrorString(ce));
@@ -1252,6 +1269,7 @@ int swe_set_state(swe_solver* s, const double* h, const double* hu, const double
   s->launches++;
   int rc;
   if ((rc = reset_counters(s))) return rc;
+  if ((rc = clear_comp(s))) return rc;
   s->t0 = 0.0;
   s->dof_updates = 0;
   SWE_CUDA(cudaMemsetAsync(s->ws + s->lay.acc, 0, 64, s->stream));
@@ -1523,7 +1541,8 @@ int swe_stats(const swe_solver* cs, double* mass, double* injected_mass, double*
   return SWE_OK;
 }
 
-// checkpoint: header + level array + raw device regions [q, ring) .. [means, dry], acc, macro
+// checkpoint: header + level array + raw device regions [q, ring) .. [means, dry], acc, macro and,
+// for a compensated solver, the compensation plane
 namespace {
 struct CkptHeader {
   char magic[8];
@@ -1531,14 +1550,18 @@ struct CkptHeader {
   int64_t k, dof_updates;
   double t0, dt_min;
   uint64_t bytes_q, bytes_ring, bytes_qmid, bytes_means, bytes_dry;
+  uint64_t bytes_comp;   // the compensation plane (compensated solvers), else 0
 };
+
+size_t comp_bytes(const swe_solver* s) { return s->comp ? (size_t)s->Np * s->KS * s->ts : 0; }
 }  // namespace
 
 int swe_full_state_bytes(const swe_solver* s, size_t* bytes) {
   if (!s || !bytes) return fail(SWE_EINVAL, "NULL argument");
   const size_t qb = 2 * 3 * (size_t)s->Np * s->KS * s->ts, rb = 3 * qb / 2;
   const size_t mb = (size_t)s->K * 3 * s->NPP * s->ts;
-  *bytes = sizeof(CkptHeader) + (size_t)s->K * 4 + qb + rb + mb + (size_t)s->K * 4 * s->ts + s->K + 64 + 8;
+  *bytes = sizeof(CkptHeader) + (size_t)s->K * 4 + qb + rb + mb + (size_t)s->K * 4 * s->ts + s->K + 64 + 8 +
+           comp_bytes(s);
   return SWE_OK;
 }
 
@@ -1559,6 +1582,7 @@ int swe_get_full_state(const swe_solver* s, void* host_buf, size_t bytes) {
   h.bytes_qmid = (uint64_t)s->K * 3 * s->NPP * s->ts;
   h.bytes_means = (uint64_t)s->K * 4 * s->ts;
   h.bytes_dry = s->K;
+  h.bytes_comp = comp_bytes(s);
   char* p = reinterpret_cast<char*>(host_buf);
   std::memcpy(p, &h, sizeof(h)); p += sizeof(h);
   std::memcpy(p, s->level.data(), (size_t)s->K * 4); p += (size_t)s->K * 4;
@@ -1569,7 +1593,8 @@ int swe_get_full_state(const swe_solver* s, void* host_buf, size_t bytes) {
   SWE_CUDA(cudaMemcpyAsync(p, s->ws + s->lay.means, h.bytes_means, cudaMemcpyDeviceToHost, st)); p += h.bytes_means;
   SWE_CUDA(cudaMemcpyAsync(p, s->ws + s->lay.dry, h.bytes_dry, cudaMemcpyDeviceToHost, st)); p += h.bytes_dry;
   SWE_CUDA(cudaMemcpyAsync(p, s->ws + s->lay.acc, 64, cudaMemcpyDeviceToHost, st)); p += 64;
-  SWE_CUDA(cudaMemcpyAsync(p, s->ws + s->lay.macro, 8, cudaMemcpyDeviceToHost, st));
+  SWE_CUDA(cudaMemcpyAsync(p, s->ws + s->lay.macro, 8, cudaMemcpyDeviceToHost, st)); p += 8;
+  if (h.bytes_comp) SWE_CUDA(cudaMemcpyAsync(p, s->ws + s->lay.comp, h.bytes_comp, cudaMemcpyDeviceToHost, st));
   SWE_CUDA(cudaStreamSynchronize(st));
   return SWE_OK;
 }
@@ -1584,7 +1609,7 @@ int swe_set_full_state(swe_solver* s, const void* host_buf, size_t bytes) {
   const char* p = reinterpret_cast<const char*>(host_buf);
   std::memcpy(&h, p, sizeof(h)); p += sizeof(h);
   if (std::memcmp(h.magic, "SWEGB300", 8) != 0 || h.K != s->K || h.N != s->N || h.precision != s->prm.precision ||
-      h.scheme != s->prm.scheme)
+      h.scheme != s->prm.scheme || h.bytes_comp != comp_bytes(s))
     return fail(SWE_EINVAL, "checkpoint does not match this solver");
   std::vector<int32_t> lev(s->K);
   std::memcpy(lev.data(), p, (size_t)s->K * 4); p += (size_t)s->K * 4;
@@ -1597,7 +1622,8 @@ int swe_set_full_state(swe_solver* s, const void* host_buf, size_t bytes) {
   SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.means, p, h.bytes_means, cudaMemcpyHostToDevice, st)); p += h.bytes_means;
   SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.dry, p, h.bytes_dry, cudaMemcpyHostToDevice, st)); p += h.bytes_dry;
   SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.acc, p, 64, cudaMemcpyHostToDevice, st)); p += 64;
-  SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.macro, p, 8, cudaMemcpyHostToDevice, st));
+  SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.macro, p, 8, cudaMemcpyHostToDevice, st)); p += 8;
+  if (h.bytes_comp) SWE_CUDA(cudaMemcpyAsync(s->ws + s->lay.comp, p, h.bytes_comp, cudaMemcpyHostToDevice, st));
   SWE_CUDA(cudaMemsetAsync(s->ws + s->lay.flags, 0, 16, st));
   SWE_CUDA(cudaStreamSynchronize(st));
   s->k = h.k;
@@ -1854,6 +1880,7 @@ int swe_batch_create(swe_solver* const* solvers, int32_t n, int32_t max_macro, v
     swe_solver* s = solvers[i];
     if (!s || !s->have_state || !(s->dt_min > 0)) return fail(SWE_EINVAL, "every solver needs state and levels");
     if (!synchronous(s)) return fail(SWE_EINVAL, "every solver must be level-synchronous");
+    if (s->comp) return fail(SWE_EUNSUPPORTED, "a compensated solver cannot join a batch");
     if (!s->stream) return fail(SWE_EINVAL, "batched solvers need their own (non-default) streams");
     for (int j = 0; j < i; ++j)
       if (solvers[j] == s) return fail(SWE_EINVAL, "a solver appears twice in the batch");

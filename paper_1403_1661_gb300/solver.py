@@ -114,7 +114,7 @@ class Solver:
     def __init__(self, mesh: Mesh, N: int, g: float = 9.81, h0: float = 1e-5, cfl: float = 0.5,
                  nlevels_max: int = 1, precision="fp32", limiter_mask: int = 0, tvb_M: float = 0.0,
                  tvb_nu: float = 1.5, dry_mode: int = 0, eps: float = 0.0, device=None, stream=None,
-                 scheme: str = "cubature"):
+                 scheme: str = "cubature", compensated: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -127,7 +127,8 @@ class Solver:
                                   _prec_code(precision), limiter_mask, dry_mode,
                                   {"cubature": nat.SWE_SCHEME_CUBATURE,
                                    "collocation": nat.SWE_SCHEME_COLLOCATION,
-                                   "cubature_2n": nat.SWE_SCHEME_CUBATURE_2N}[scheme])
+                                   "cubature_2n": nat.SWE_SCHEME_CUBATURE_2N}[scheme],
+                                  1 if compensated else 0)
         self.precision = self.prm.precision
         nbytes = C.c_size_t()
         nat.check(L.swe_workspace_bytes(mesh.handle, C.byref(self.prm), C.byref(nbytes)),

@@ -160,3 +160,31 @@ def test_regroup_rule_bit_exact(lib):
         olev, omargin = cfl_regroup_levels(dt, dt_min, old, k, nl)
         assert np.array_equal(out, olev)
         assert margin.value == omargin
+
+
+def test_compensated_workspace_and_validation(lib):
+    """swe_params.compensated: one more elevation plane of Np x KS words on the
+    single-precision tiers, nothing in FP64, anything but 0 or 1 refused."""
+    import paper_1403_1661_gb300 as P
+    vx, vy, E = meshes.structured_rect(0.0, 1.0, 0.0, 1.0, 9, 7)
+    m = P.Mesh(vx, vy, E)
+    K, N = m.K, 3
+    Np, KS = (N + 1) * (N + 2) // 2, (K + 31) // 32 * 32
+
+    def nbytes(precision, comp):
+        prm = lib.swe_params(9.81, 1e-5, 0.0, 0.0, 1.5, 0.5, N, 1, precision, 1, 0, lib.SWE_SCHEME_CUBATURE, comp)
+        out = C.c_size_t()
+        rc = lib.lib().swe_workspace_bytes(m.handle, C.byref(prm), C.byref(out))
+        return rc, out.value
+
+    for prec in (lib.SWE_FP32, lib.SWE_FP32_TC):
+        rc0, b0 = nbytes(prec, 0)
+        rc1, b1 = nbytes(prec, 1)
+        assert rc0 == rc1 == lib.SWE_OK
+        plane = Np * KS * 4
+        assert plane <= b1 - b0 < plane + 256          # the plane, 256-byte aligned
+    rc0, b0 = nbytes(lib.SWE_FP64, 0)
+    rc1, b1 = nbytes(lib.SWE_FP64, 1)
+    assert rc0 == rc1 == lib.SWE_OK and b0 == b1
+    rc, _ = nbytes(lib.SWE_FP32, 2)
+    assert rc == lib.SWE_EINVAL
