@@ -381,7 +381,7 @@ int swe_set_open_faces(swe_solver* solver, const uint8_t* open);
 int swe_set_launch_config(swe_solver* solver, int32_t ctas_per_sm);
 
 /* Warps per CTA of the tensor-core stage kernel and of the persistent batch kernel
- * (FP32 tensor-core tier; default 4). Each warp owns its shared-memory tiles and the
+ * (FP32 tensor-core tier; default 4, 2 at N = 5). Each warp owns its shared-memory tiles and the
  * CTA one copy of the operators, so more warps per CTA share that copy: at N = 5
  * (29 KB of tiles per warp) seven warps fit on an SM as one CTA where two CTAs of
  * four do not. warps in 1..8; SWE_EINVAL when that many warps' tiles do not fit on
