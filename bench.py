@@ -376,7 +376,7 @@ def run_ours(args):
         s64.close()
         del s64
 
-    # the same tier with the compensated elevation update (swe_params.compensated)
+    # the same tier with the compensated state update (swe_params.compensated)
     if rank == 0 and args.precision != "fp64":
         sc_ = P.solver_from_scenario(scn, precision=args.precision, compensated=True)
         sc_.step(2)
@@ -393,8 +393,8 @@ def run_ours(args):
         dc = sc_.stats()["dof_updates"] - d0
         result["compensated"] = {"value": dc / (msc / 1e3), "unit": UNIT, "ms_per_step": msc / nc,
                                  "vs_plain": (dc / (msc / 1e3)) / value,
-                                 "note": "same workload and tier, surface elevation updated with a compensated "
-                                         "sum (mass kept to rounding over long runs)"}
+                                 "note": "same workload and tier, state updated with a compensated sum (mass "
+                                         "kept to rounding, FP64's accuracy over long runs)"}
         sc_.close()
         del sc_
 

@@ -90,13 +90,13 @@ typedef struct swe_solver swe_solver;
  *                same with rules of integration order 2N) or
  *                SWE_SCHEME_COLLOCATION (fluxes at the nodes and face nodes,
  *                their interpolants integrated exactly)
- *   compensated  single-precision tiers: 1 = the surface elevation is updated
+ *   compensated  single-precision tiers: 1 = the state (eta, hu, hv) is updated
  *                with a compensated sum (each commit's rounding error is kept in
- *                a workspace plane and taken back at the next), so the total mass
- *                keeps to about 3e-13 of itself per step instead of about 5e-9,
- *                and long runs stay about 1000 times closer to FP64; about 13 %
- *                more time per macro step. 0 (default) or 1; ignored in FP64. A
- *                compensated solver cannot join a batch. */
+ *                three workspace planes and taken back at the next), so the total
+ *                mass keeps to about 3e-13 of itself per step instead of about 5e-9
+ *                and long runs keep FP64's accuracy (the plain update accumulates
+ *                its rounding); about 11 % more time per macro step. 0 (default)
+ *                or 1; ignored in FP64. A compensated solver cannot join a batch. */
 typedef struct {
   double g, h0, eps, tvb_M, tvb_nu, cfl;
   int32_t N, nlevels_max, precision, limiter_mask, dry_mode, scheme;

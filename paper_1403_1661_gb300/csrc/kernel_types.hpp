@@ -124,7 +124,7 @@ struct DevState {
   double* acc;          // accumulators: [0] injected mass
   int* flags;           // [0] non-finite state detected
   long long* macro;     // macro-step counter (advanced on the device)
-  T* comp;              // [NP][KS] rounding error of the last elevation update, or nullptr
+  T* comp;              // [3][NP][KS] rounding error of the last state update, or nullptr
                         // (not compensated)
 };
 

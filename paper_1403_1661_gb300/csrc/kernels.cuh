@@ -543,10 +543,11 @@ __device__ __forceinline__ void add_reference_pressure(const T* __restrict__ sop
 }
 
 // Adams-Bashforth commit (Algorithm 1) and positivity limiter (Algorithm 3) of
-// element e (mode 0), or the R output in the caller's layout (mode 1). kComp: the
-// elevation's increments are summed first and added to the state with the rounding
-// error of the previous update subtracted (a compensated sum, p.s.comp), so the
-// single-precision state does not drift in total mass step after step.
+// element e (mode 0), or the R output in the caller's layout (mode 1). kComp: each
+// field's increments are summed first and added to the state with the rounding
+// error of the previous update taken back (a compensated sum, p.s.comp), so the
+// single-precision state neither drifts in total mass nor accumulates its rounding
+// step after step.
 template <typename T, int N, bool kComp = false>
 __device__ __forceinline__ void commit_and_limit(const StageParams<T>& p, const T* __restrict__ sops, int e,
                                                  int lev, long long a, T (&eta)[Dims<N>::NPP],
@@ -593,7 +594,7 @@ __device__ __forceinline__ void commit_and_limit(const StageParams<T>& p, const 
   ab_partial_weights<T>(depth, T(0.5), wh);
   const T m0 = dtl * wh[0], m1 = dtl * wh[1], m2 = dtl * wh[2];
   T x0[NP], x1[NP], x2[NP];
-  T d0[kComp ? NP : 1];   // compensated: the elevation's increment of this step
+  T d0[kComp ? NP : 1], d1[kComp ? NP : 1], d2[kComp ? NP : 1];   // compensated: the increments
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
     x0[i] = eta[i] + m0 * R0[i];
@@ -601,11 +602,13 @@ __device__ __forceinline__ void commit_and_limit(const StageParams<T>& p, const 
     x2[i] = hv[i] + m0 * R2[i];
     if constexpr (kComp) {
       d0[i] = c0 * R0[i];
+      d1[i] = c0 * R1[i];
+      d2[i] = c0 * R2[i];
     } else {
       eta[i] += c0 * R0[i];
+      hu[i] += c0 * R1[i];
+      hv[i] += c0 * R2[i];
     }
-    hu[i] += c0 * R1[i];
-    hv[i] += c0 * R2[i];
   }
   for (int s = 1; s < depth; ++s) {
     const T cs = s == 1 ? c1 : c2, ms = s == 1 ? m1 : m2;
@@ -616,26 +619,16 @@ __device__ __forceinline__ void commit_and_limit(const StageParams<T>& p, const 
       const T r2 = ldm(rs + 2 * fstride + i * ks);
       if constexpr (kComp) {
         d0[i] += cs * r0;
+        d1[i] += cs * r1;
+        d2[i] += cs * r2;
       } else {
         eta[i] += cs * r0;
+        hu[i] += cs * r1;
+        hv[i] += cs * r2;
       }
-      hu[i] += cs * r1;
-      hv[i] += cs * r2;
       x0[i] += ms * r0;
       x1[i] += ms * r1;
       x2[i] += ms * r2;
-    }
-  }
-  if constexpr (kComp) {
-    // eta + d with the previous rounding error c taken back: y = d - c, t = eta + y,
-    // and the new error c = (t - eta) - y (exact when |eta| >= |y|)
-    T* cp = p.s.comp + eo;
-#pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      const T y = d0[i] - ldm(cp + i * ks);
-      const T t = eta[i] + y;
-      cp[i * ks] = (t - eta[i]) - y;
-      eta[i] = t;
     }
   }
   if ((__ldg(reinterpret_cast<const int*>(p.s.conn + e) + 3) >> 12) & 1) {
@@ -650,6 +643,31 @@ __device__ __forceinline__ void commit_and_limit(const StageParams<T>& p, const 
 #pragma unroll
     for (int i = 0; i < NPP; ++i) row[i] = i < NP ? x2[i] : T(0);
     store_row_global<T, NPP>(qm + 2 * NPP, row);
+  }
+  if constexpr (kComp) {
+    // q + d with the previous rounding error c taken back: y = d - c, t = q + y, and
+    // the new error c = (t - q) - y (exact when |q| >= |y|). All previous errors are
+    // read before the first new one is written, so the loads overlap.
+    T* cp = p.s.comp + eo;
+    T ce[NP], cu[NP], cv[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      ce[i] = ldm(cp + i * ks);
+      cu[i] = ldm(cp + fstride + i * ks);
+      cv[i] = ldm(cp + 2 * fstride + i * ks);
+    }
+    auto add = [&](T& q, T d, T c, T* cout) {
+      const T y = d - c;
+      const T t = q + y;
+      *cout = (t - q) - y;
+      q = t;
+    };
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      add(eta[i], d0[i], ce[i], cp + i * ks);
+      add(hu[i], d1[i], cu[i], cp + fstride + i * ks);
+      add(hv[i], d2[i], cv[i], cp + 2 * fstride + i * ks);
+    }
   }
 
   // ---- positivity limiter (Algorithm 3) and means ----
@@ -730,7 +748,7 @@ __device__ __forceinline__ void volume_term(const T* __restrict__ sops, const T 
 
 // One element of the stage: R(Q) (volume + surface + lift), then the
 // Adams-Bashforth commit and the positivity limiter (mode 0) or R only (mode 1).
-// k is the finest substep count of the schedule; kComp: compensated elevation update.
+// k is the finest substep count of the schedule; kComp: compensated state update.
 template <typename T, int N, bool kComp = false>
 __device__ __forceinline__ void stage_element(const StageParams<T>& p, const T* __restrict__ sops, int e,
                                               long long k, double* injected) {
@@ -781,7 +799,7 @@ __device__ __forceinline__ double stage_range(const StageParams<T>& __restrict__
 
 // kGlobalOps: the operators are read from global memory (through L1) instead of
 // the block's shared-memory copy (the operator-placement comparison of Section 7.4).
-// kComp: compensated elevation update (p.s.comp).
+// kComp: compensated state update (p.s.comp).
 template <typename T, int N, bool kGlobalOps = false, bool kComp = false>
 __global__ void __launch_bounds__(kBlock) k_stage(const __grid_constant__ StageParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

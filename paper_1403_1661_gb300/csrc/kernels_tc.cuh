@@ -96,7 +96,7 @@ struct TcSmem {
 // volume term and lift on tensor cores, commit and limiter. k: the finest substep
 // count of the schedule; nactive: elements [0, nactive) are active at this substep;
 // next_tile: the warp's next tile (its planes are prefetched to L2), or -1; sw: the
-// warp's shared tiles; kComp: compensated elevation update in the commit.
+// warp's shared tiles; kComp: compensated state update in the commit.
 template <int N, bool kComp = false>
 __device__ __forceinline__ void stage_tc_warp(const StageParams<float>& p, long long k, int nactive,
                                               const float* sops, float* sw, int tile, int next_tile,
@@ -170,7 +170,7 @@ __device__ __forceinline__ void stage_tc_warp(const StageParams<float>& p, long 
         for (int pl = lane; pl < 3 * NP; pl += 32) prefetch_l2(rs + pl * ks);
       }
       if constexpr (kComp)
-        for (int pl = lane; pl < NP; pl += 32) prefetch_l2(p.s.comp + e0 + pl * ks);
+        for (int pl = lane; pl < 3 * NP; pl += 32) prefetch_l2(p.s.comp + e0 + pl * ks);
     }
   }
 
@@ -508,7 +508,7 @@ __device__ __forceinline__ double stage_tc_range(const StageParams<float>& __res
 }
 
 // CTA: blockDim.x / 32 warps (1 to kTcMaxWarps), each with its own shared tiles after
-// the CTA's operator copy. kComp: compensated elevation update (p.s.comp).
+// the CTA's operator copy. kComp: compensated state update (p.s.comp).
 template <int N, bool kComp = false>
 __global__ void __launch_bounds__(kTcMaxBlock, 1) k_stage_tc(const __grid_constant__ StageParams<float> p) {
   using SM = TcSmem<N>;

@@ -56,7 +56,7 @@ struct Layout {
 
 int tc_size_of(int N);
 
-// comp: the compensation plane of the surface elevation (single-precision tiers
+// comp: the compensation planes of the state, [3][NP][KS] (single-precision tiers
 // with compensated = 1), else empty
 Layout make_layout(int K, int N, size_t ts, int op_size, int code, bool comp) {
   Layout L;
@@ -89,7 +89,7 @@ Layout make_layout(int K, int N, size_t ts, int op_size, int code, bool comp) {
   L.acc = take(8 * 8);
   L.flags = take(4 * 4);
   L.macro = take(8);
-  L.comp = take(comp ? plane * ts : 0);
+  L.comp = take(comp ? 3 * plane * ts : 0);
   L.nb_stats = std::max(1, std::min(1024, (K + 255) / 256));
   L.partials = take((size_t)L.nb_stats * 2 * 8 + 16);
   L.total = off;
@@ -135,7 +135,7 @@ struct swe_solver {
   int KS = 0;                    // element stride of the device node planes
   bool fp64 = false;
   bool tc = false;   // FP32 with tensor-core volume contractions
-  bool comp = false; // single precision with a compensated surface-elevation update
+  bool comp = false; // single precision with a compensated state update
   size_t ts = 4;
   cudaStream_t stream = nullptr;
   char* ws = nullptr;
@@ -635,10 +635,10 @@ int invalidate_graph(swe_solver* s) {
   return SWE_OK;
 }
 
-// The compensation plane starts at zero whenever the state is set or re-ordered
-// from the host (it holds at most one rounding of each node's elevation).
+// The compensation planes start at zero whenever the state is set or re-ordered
+// from the host (they hold at most one rounding of each node's state).
 int clear_comp(swe_solver* s) {
-  if (s->comp) SWE_CUDA(cudaMemsetAsync(s->ws + s->lay.comp, 0, (size_t)s->Np * s->KS * s->ts, s->stream));
+  if (s->comp) SWE_CUDA(cudaMemsetAsync(s->ws + s->lay.comp, 0, 3 * (size_t)s->Np * s->KS * s->ts, s->stream));
   return SWE_OK;
 }
 
@@ -934,7 +934,7 @@ int regroup_t(swe_solver* s, const std::vector<int32_t>& lev_new) {
   };
   int rc;
   if ((rc = planes(ring, 9 * np))) return rc;
-  if (s->comp && (rc = planes(reinterpret_cast<T*>(s->ws + s->lay.comp), np))) return rc;
+  if (s->comp && (rc = planes(reinterpret_cast<T*>(s->ws + s->lay.comp), 3 * np))) return rc;
   if ((rc = planes(reinterpret_cast<T*>(s->ws + s->lay.B), np))) return rc;
   if ((rc = planes(reinterpret_cast<T*>(s->ws + s->lay.vb), 3))) return rc;
   if ((rc = planes(reinterpret_cast<T*>(s->ws + s->lay.p1), 9))) return rc;
@@ -1542,7 +1542,7 @@ int swe_stats(const swe_solver* cs, double* mass, double* injected_mass, double*
 }
 
 // checkpoint: header + level array + raw device regions [q, ring) .. [means, dry], acc, macro and,
-// for a compensated solver, the compensation plane
+// for a compensated solver, the compensation planes
 namespace {
 struct CkptHeader {
   char magic[8];
@@ -1550,10 +1550,10 @@ struct CkptHeader {
   int64_t k, dof_updates;
   double t0, dt_min;
   uint64_t bytes_q, bytes_ring, bytes_qmid, bytes_means, bytes_dry;
-  uint64_t bytes_comp;   // the compensation plane (compensated solvers), else 0
+  uint64_t bytes_comp;   // the compensation planes (compensated solvers), else 0
 };
 
-size_t comp_bytes(const swe_solver* s) { return s->comp ? (size_t)s->Np * s->KS * s->ts : 0; }
+size_t comp_bytes(const swe_solver* s) { return s->comp ? 3 * (size_t)s->Np * s->KS * s->ts : 0; }
 }  // namespace
 
 int swe_full_state_bytes(const swe_solver* s, size_t* bytes) {

@@ -163,8 +163,8 @@ def test_regroup_rule_bit_exact(lib):
 
 
 def test_compensated_workspace_and_validation(lib):
-    """swe_params.compensated: one more elevation plane of Np x KS words on the
-    single-precision tiers, nothing in FP64, anything but 0 or 1 refused."""
+    """swe_params.compensated: three more planes (eta, hu, hv) of Np x KS words on
+    the single-precision tiers, nothing in FP64, anything but 0 or 1 refused."""
     import paper_1403_1661_gb300 as P
     vx, vy, E = meshes.structured_rect(0.0, 1.0, 0.0, 1.0, 9, 7)
     m = P.Mesh(vx, vy, E)
@@ -181,8 +181,8 @@ def test_compensated_workspace_and_validation(lib):
         rc0, b0 = nbytes(prec, 0)
         rc1, b1 = nbytes(prec, 1)
         assert rc0 == rc1 == lib.SWE_OK
-        plane = Np * KS * 4
-        assert plane <= b1 - b0 < plane + 256          # the plane, 256-byte aligned
+        planes = 3 * Np * KS * 4
+        assert planes <= b1 - b0 < planes + 256        # the planes, 256-byte aligned
     rc0, b0 = nbytes(lib.SWE_FP64, 0)
     rc1, b1 = nbytes(lib.SWE_FP64, 1)
     assert rc0 == rc1 == lib.SWE_OK and b0 == b1
