@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--oracle-configs", action="store_true")
     ap.add_argument("--oracle-configs-child", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-sample-child", nargs=3, metavar=("NX", "NY", "SCHEME"), help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -194,6 +195,21 @@ def oracle_sample(args, nsteps=1, nx=200, ny=50, scheme="cubature"):
     return (integ.dof_updates - d0) / dt, dt, om.K, period
 
 
+SINGLE_THREAD_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+
+
+def oracle_sample_single_thread(args, nx, ny, scheme="cubature"):
+    """oracle_sample (one macro step) in a fresh interpreter whose numerical
+    libraries are limited to one thread, so that the reported core count is the one
+    the oracle used. Returns (DOF-updates/s, seconds, triangles)."""
+    env = dict(os.environ, **SINGLE_THREAD_ENV)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--order", str(args.order),
+                        "--oracle-sample-child", str(nx), str(ny), scheme],
+                       capture_output=True, text=True, env=env, check=True)
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["value"], d["seconds"], d["triangles"]
+
+
 def cpu_info():
     model = ""
     try:
@@ -220,9 +236,11 @@ def run_reference(args):
         dofs_total += v * dt
         t_total += dt
     value = dofs_total / t_total
-    cores, model = cpu_info()
+    _, model = cpu_info()
+    # one thread when this process set the limit before numpy was imported (main)
+    cores = 1 if os.environ.get("OPENBLAS_NUM_THREADS") == "1" else os.cpu_count()
     sample = (f"same scenario at {nx}x{ny}x2 = {2 * nx * ny} triangles (N={args.order}, 4 levels, PP+TVB), "
-              f"one macro step per bench step, FP64 numpy oracle")
+              f"one macro step per bench step, FP64 numpy oracle, {cores} thread(s)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -429,11 +447,12 @@ def run_ours(args):
         result["served"] = run_served(args)
 
     if rank == 0 and not args.no_cpu_baseline:
-        v, dt, Ks, _ = oracle_sample(args, 1, 400, 100)
-        cores, model = cpu_info()
-        result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+        v, dt, Ks = oracle_sample_single_thread(args, 400, 100)
+        _, model = cpu_info()
+        result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                   "sample": f"same scenario at 400x100x2 = {Ks} triangles (N={args.order}, 4 levels, "
-                                            f"PP+TVB), one macro step, FP64 numpy oracle ({dt:.1f} s)",
+                                            f"PP+TVB), one macro step, FP64 numpy oracle ({dt:.1f} s), one thread "
+                                            f"(BLAS and OpenMP limited to one)",
                                   "cpu": model}
     if rank == 0:
         print(json.dumps(result), flush=True)
@@ -471,9 +490,9 @@ def run_collocation(args, scn, P, steps=10):
     peak, kind = measured_peaks()
     out_cpu = None
     if not args.no_cpu_baseline:
-        v, dt, Ks, _ = oracle_sample(args, 1, 400, 100, scheme="collocation")
-        out_cpu = {"value": v, "unit": UNIT, "cores": cpu_info()[0], "kind": "oracle (oracle/colloc.py)",
-                   "sample": f"same scenario at 400x100x2 = {Ks} triangles, one macro step ({dt:.1f} s)"}
+        v, dt, Ks = oracle_sample_single_thread(args, 400, 100, scheme="collocation")
+        out_cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle (oracle/colloc.py)",
+                   "sample": f"same scenario at 400x100x2 = {Ks} triangles, one macro step ({dt:.1f} s), one thread"}
     return {"value": value, "unit": UNIT, "ms_per_step": ms_step, "steps": steps,
             "cpu_oracle": out_cpu,
             "precision": "fp32tc", "kernel": f"k_stage_tc<{16 + args.order}> (collocation code)",
@@ -728,6 +747,15 @@ def oracle_configs():
 
 def main():
     args = parse()
+    if args.oracle_sample_child:
+        nx, ny, scheme = args.oracle_sample_child
+        v, dt, K, _ = oracle_sample(args, 1, int(nx), int(ny), scheme=scheme)
+        print(json.dumps({"value": v, "seconds": dt, "triangles": K}), flush=True)
+        return
+    if args.impl == "reference" and "numpy" not in sys.modules:
+        # the oracle runs in this process: its numerical libraries get one thread,
+        # set before numpy is first imported, so that "cores" is what it used
+        os.environ.update(SINGLE_THREAD_ENV)
     if args.oracle_configs_child:
         oracle_configs_child()
         return
