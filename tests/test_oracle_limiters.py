@@ -309,7 +309,9 @@ def test_tvb_positivity_modification_minimal():
     assert up.sum() >= 2 and (~up).sum() >= 1
     assert np.abs(V2[fired][up].min(axis=1) - hmod).max() < 1e-12
     assert np.abs(V2[fired][~up] - mv[~up]).max() < 1e-13
-    theta = np.clip((mv - hmod) / (mv - Vp[fired].min(axis=1, keepdims=True)), 0.0, 1.0)
+    span = mv - Vp[fired].min(axis=1, keepdims=True)
+    # a flat element (span 0) is left flat whatever theta is; take theta = 0 there
+    theta = np.clip(np.divide(mv - hmod, span, out=np.zeros_like(span), where=span > 0), 0.0, 1.0)
     assert np.abs(V2[fired] - (mv + theta * (Vp[fired] - mv))).max() < 1e-12
     assert np.abs(V2[~fired] - Vp[~fired]).max() < 1e-13
     # the element means are the unmodified ones
