@@ -19,8 +19,10 @@ Failures stay with their request: a request whose preparation fails (an invalid
 mesh, say) or whose workspace exceeds the whole budget is rejected, one whose
 solver cannot be created fails, and a running solve whose state turned
 non-finite (the device flag that swe_stats reports, checked every few rounds
-while the solve is idle and again before its result is returned) is stopped and
-fails; its memory is released and the others carry on. A request can be
+while the solve is idle and again before its result is returned), or whose step,
+check or read-back raises, is stopped and fails; its memory is released and the
+others carry on. If the loop itself is left by an exception, every solve it had
+created is closed before the exception propagates. A request can be
 cancelled from any thread (Server.cancel) or at a scripted time
 (Request.cancel_at): one that has not started is dropped, a running one is
 retired at its next idle point without a result.
@@ -103,13 +105,17 @@ class _GpuJob:
         self.s = Solver(prepared["mesh"], scn.N, g=scn.g, h0=scn.h0, cfl=scn.cfl, nlevels_max=scn.nlevels,
                         precision=factory.precision, limiter_mask=scn.limiter_mask, tvb_M=scn.tvb_M,
                         tvb_nu=scn.tvb_nu, dry_mode=scn.dry_mode)
-        if scn.N in factory.tuned:
-            self.s.set_launch_config(factory.tuned[scn.N])
-        B, h, hu, hv = prepared["inputs"]
-        lev, dtm = prepared["levels"]
-        self.s.set_bathymetry(B)
-        self.s.set_levels(lev, dtm)      # before the state: no re-ordering of uploaded data
-        self.s.set_state(h, hu, hv)
+        try:
+            if scn.N in factory.tuned:
+                self.s.set_launch_config(factory.tuned[scn.N])
+            B, h, hu, hv = prepared["inputs"]
+            lev, dtm = prepared["levels"]
+            self.s.set_bathymetry(B)
+            self.s.set_levels(lev, dtm)      # before the state: no re-ordering of uploaded data
+            self.s.set_state(h, hu, hv)
+        except BaseException:
+            self.s.close()                   # a failed start gives its workspace back at once
+            raise
         L = int(np.max(lev))
         self.macro_period = 2 ** (L - 1)
         self.substeps_left = int(req.substeps)   # finest substeps still to take
@@ -151,9 +157,11 @@ class _GpuJob:
         return not self.s.stats()["nonfinite"]
 
     def finish(self):
-        st = self.s.stats()
-        out = self.s.get_state() if self.factory.keep_state else None
-        self.s.close()
+        try:
+            st = self.s.stats()
+            out = self.s.get_state() if self.factory.keep_state else None
+        finally:
+            self.s.close()
         return out, st["dof_updates"]
 
     def abort(self):
@@ -215,7 +223,29 @@ class Server:
             r.admitted = self.clock() - t0
             running.append([r, job, int(math.ceil(r.substeps / job.macro_period)), 0])
 
+        def drop(r, job, status, error=None):
+            """Retire a running solve without a result and give its memory back."""
+            nonlocal used
+            try:
+                job.abort()
+            except Exception as ex:
+                error = f"{error}; abort failed: {ex}" if error else f"abort failed: {ex}"
+            used -= r.bytes
+            end(r, status, error)
+
+        def release_all():
+            """On leaving the loop by an exception: close the solves still running and
+            those whose creation had finished (the pools have shut down by then)."""
+            for item in running:
+                with contextlib.suppress(Exception):
+                    item[1].abort()
+            for _, fut in starting:
+                if fut.done() and not fut.cancelled() and fut.exception() is None:
+                    with contextlib.suppress(Exception):
+                        fut.result().abort()
+
         with contextlib.ExitStack() as pools:   # both pools shut down however the loop ends
+            pools.callback(release_all)          # runs last: after the pools' shutdown
             pool = pools.enter_context(cf.ThreadPoolExecutor(max_workers=self.prep_workers))
             starter = (pools.enter_context(cf.ThreadPoolExecutor(max_workers=self.start_workers))
                        if self.start_workers > 0 else None)
@@ -285,31 +315,46 @@ class Server:
                 still = []
                 for item in running:
                     r, job, rem, rounds = item
-                    if not job.idle():
+                    try:
+                        idle = job.idle()
+                    except Exception as ex:          # the solve's stream reported an error
+                        drop(r, job, "failed", f"device error: {ex}")
+                        progressed = True
+                        continue
+                    if not idle:
                         still.append(item)
                         continue
                     progressed = True
                     if self._cancelled(r, self.clock() - t0):
-                        job.abort()
-                        used -= r.bytes
-                        end(r, "cancelled")
+                        drop(r, job, "cancelled")
                         continue
                     if hasattr(job, "remaining_macro"):   # the job counts its own substeps
                         rem = item[2] = job.remaining_macro()
                     check = rem == 0 or (self.health_every > 0 and rounds > 0 and rounds % self.health_every == 0)
-                    if check and not getattr(job, "healthy", lambda: True)():
-                        job.abort()
-                        used -= r.bytes
-                        end(r, "failed", "non-finite state")
+                    try:
+                        ok = not check or getattr(job, "healthy", lambda: True)()
+                    except Exception as ex:          # e.g. the device reported an error
+                        drop(r, job, "failed", f"health check failed: {ex}")
+                        continue
+                    if not ok:
+                        drop(r, job, "failed", "non-finite state")
                         continue
                     if rem > 0:
                         n = min(rem, self.macro_per_round)
-                        job.step(n)
+                        try:
+                            job.step(n)
+                        except Exception as ex:      # e.g. a refused regroup or graph launch
+                            drop(r, job, "failed", f"step failed: {ex}")
+                            continue
                         item[2] = rem - n
                         item[3] = rounds + 1
                         still.append(item)
                     else:
-                        r.result, r.dof_updates = job.finish()
+                        try:
+                            r.result, r.dof_updates = job.finish()
+                        except Exception as ex:      # finish closes the solve in any case
+                            drop(r, job, "failed", f"finish failed: {ex}")
+                            continue
                         r.status = "done"
                         r.finished = self.clock() - t0
                         used -= r.bytes

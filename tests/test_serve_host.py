@@ -9,40 +9,52 @@ from paper_1403_1661_gb300.serve import Request, Server
 
 
 class FakeClock:
-    def __init__(self):
+    def __init__(self, limit=1e6):
         self.t = 0.0
+        self.limit = limit     # fake seconds: a loop that never drains fails instead of hanging
 
     def __call__(self):
         return self.t
 
     def sleep(self, dt):
         self.t += dt
+        if self.t > self.limit:
+            raise RuntimeError("fake clock ran past its limit")
 
 
 class FakeJob:
-    def __init__(self, clock, req, rounds_per_step, bad_after=None):
+    def __init__(self, clock, req, rounds_per_step, bad_after=None, raises=None):
         self.clock = clock
         self.macro_period = 4
         self.busy_until = 0.0
         self.steps = 0
         self.dt = rounds_per_step
         self.bad_after = bad_after     # macro steps after which the state is non-finite
+        self.raises = raises or {}     # method name -> macro steps after which it raises
         self.aborted = False
         self.health_checks = 0
 
+    def _maybe_raise(self, what):
+        if what in self.raises and self.steps >= self.raises[what]:
+            raise RuntimeError(f"{what}: launch refused")
+
     def step(self, n):
+        self._maybe_raise("step")
         self.steps += n
         self.busy_until = self.clock() + self.dt * n
 
     def idle(self):
         self.clock.t += 1e-4        # the host loop itself takes time
+        self._maybe_raise("idle")
         return self.clock() >= self.busy_until
 
     def healthy(self):
         self.health_checks += 1
+        self._maybe_raise("healthy")
         return self.bad_after is None or self.steps < self.bad_after
 
     def finish(self):
+        self._maybe_raise("finish")
         return None, 100 * self.steps
 
     def abort(self):
@@ -50,7 +62,7 @@ class FakeJob:
 
 
 class FakeFactory:
-    def __init__(self, clock, sizes, step_time, bad_prepare=(), bad_start=(), bad_after=None):
+    def __init__(self, clock, sizes, step_time, bad_prepare=(), bad_start=(), bad_after=None, raises=None):
         self.clock = clock
         self.sizes = sizes
         self.step_time = step_time
@@ -59,6 +71,7 @@ class FakeFactory:
         self.bad_prepare = set(bad_prepare)
         self.bad_start = set(bad_start)
         self.bad_after = bad_after or {}
+        self.raises = raises or {}      # rid -> {method: macro steps after which it raises}
 
     def prepare(self, req):
         if req.rid in self.bad_prepare:
@@ -72,7 +85,7 @@ class FakeFactory:
         if req.rid in self.bad_start:
             raise RuntimeError("workspace refused")
         self.started.append(req.rid)
-        job = FakeJob(self.clock, req, self.step_time, self.bad_after.get(req.rid))
+        job = FakeJob(self.clock, req, self.step_time, self.bad_after.get(req.rid), self.raises.get(req.rid))
         self.jobs[req.rid] = job
         return job
 
@@ -192,3 +205,36 @@ def test_cancel_from_another_thread():
     th.join()
     out = srv.run([Request(rid=i, arrival=0.0, scenario=None, substeps=40) for i in range(2)])
     assert _status(out) == {0: "done", 1: "cancelled"}
+
+
+def test_step_check_or_readback_error_stays_with_its_request():
+    # room for two solves at a time; four of six raise in a different place (a step
+    # launch, the stream query, the non-finite check, the final read-back): each of
+    # them fails alone and gives its memory back, so the last request is still served
+    raises = {1: {"step": 4}, 2: {"finish": 0}, 3: {"healthy": 2}, 4: {"idle": 6}}
+    _, fac, out = _run([10] * 6, [0.0] * 6, budget=20, slots=6, raises=raises)
+    st = _status(out)
+    assert st == {0: "done", 1: "failed", 2: "failed", 3: "failed", 4: "failed", 5: "done"}
+    errs = {r.rid: r.error for r in out["ended"]}
+    assert errs[1].startswith("step failed") and errs[2].startswith("finish failed")
+    assert errs[3].startswith("health check failed") and errs[4].startswith("device error")
+    assert all(fac.jobs[i].aborted for i in (1, 2, 3, 4))
+    assert not fac.jobs[0].aborted and not fac.jobs[5].aborted
+    assert out["peak_bytes"] <= 20 and out["failed"] == 4 and out["requests"] == 2
+
+
+def test_loop_exception_closes_every_created_solve():
+    # the loop is left by an exception (here the host's sleep) while solves run and
+    # others are being created on worker threads: every solve created is closed
+    clock = FakeClock(limit=25.0)
+    fac = FakeFactory(clock, [10] * 8, 10.0)
+    srv = Server(budget_bytes=40, max_slots=8, macro_per_round=2, prep_workers=1, factory=fac,
+                 clock=clock, sleep=clock.sleep, start_workers=2)
+    reqs = [Request(rid=i, arrival=0.0, scenario=None, substeps=40) for i in range(8)]
+    try:
+        srv.run(reqs)
+        raise AssertionError("the run should have raised")
+    except RuntimeError as ex:
+        assert "past its limit" in str(ex)
+    assert len(fac.jobs) >= 4
+    assert all(j.aborted for j in fac.jobs.values())
