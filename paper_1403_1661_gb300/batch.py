@@ -2,9 +2,12 @@
 autotuner. Argument marshalling only: the work runs in the native library."""
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
+import hashlib
 import json
 import os
+import tempfile
 import time
 
 import numpy as np
@@ -110,11 +113,41 @@ def _gpu_key():
     return torch.cuda.get_device_name().replace(" ", "_")
 
 
+def _sources_key():
+    """Hash of the native sources: a cached shape is used only with the kernels it
+    was measured on."""
+    h = hashlib.sha256()
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".inc", ".hpp", ".cpp")):
+            h.update(f.encode())
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def _load_cache():
     try:
-        return json.load(open(CACHE))
-    except Exception:
+        with open(CACHE) as f:
+            return json.load(f)
+    except Exception:       # absent, or unreadable: tune again
         return {}
+
+
+def _store_cache(cache):
+    """Write the cache by an atomic rename, so a concurrent reader never sees a
+    partial file (a concurrent writer may drop the other's entry: it is re-tuned)."""
+    d = os.path.dirname(CACHE)
+    os.makedirs(d, exist_ok=True)
+    fd, tmp = tempfile.mkstemp(dir=d, prefix=".autotune.", suffix=".json")
+    try:
+        with os.fdopen(fd, "w") as f:
+            json.dump(cache, f, indent=1, default=str)
+        os.replace(tmp, CACHE)
+    except BaseException:
+        with contextlib.suppress(OSError):
+            os.unlink(tmp)
+        raise
 
 
 def tune(N, precision, candidates=None, reps=3, force=False, verbose=False):
@@ -122,7 +155,8 @@ def tune(N, precision, candidates=None, reps=3, force=False, verbose=False):
     beach, 4 levels) for every candidate launch shape and return the fastest as
     {"ctas_per_sm": c, "tc_warps": w}. Shapes that do not fit on an SM are skipped.
     Only a search over the full candidate set reads or writes the cache, so a
-    narrower search never stands in for it."""
+    narrower search never stands in for it; a cached shape is used only with the
+    native sources it was measured on."""
     import torch
     from workloads import scenarios as sc
     from .solver import solver_from_scenario
@@ -130,35 +164,41 @@ def tune(N, precision, candidates=None, reps=3, force=False, verbose=False):
     cands = full_set if candidates is None else tuple(candidates)
     key = f"{_gpu_key()}/N{N}/{precision}/shape"
     full = cands == full_set
+    src = _sources_key()
     cache = _load_cache()
-    if full and key in cache and not force:
-        return dict(cache[key]["shape"])
+    hit = cache.get(key)
+    if full and not force and isinstance(hit, dict) and hit.get("sources") == src:
+        return dict(hit["shape"])
     s = solver_from_scenario(sc.tsunami(nx=400, ny=100, N=N, nlevels=4), precision=precision)
     timings = {}
-    for c, w in cands:
-        try:
-            s.set_launch_config({"ctas_per_sm": c, "tc_warps": w})
-        except nat.SWEError as ex:
-            if ex.code == nat.SWE_EINVAL:     # that many warps' tiles do not fit on an SM
-                continue
-            raise
-        s.step(1)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(s.stream)
-        s.step(reps)
-        e1.record(s.stream)
-        torch.cuda.synchronize()
-        timings[(c, w)] = e0.elapsed_time(e1) / reps
-    s.close()
+    try:
+        for c, w in cands:
+            try:
+                s.set_launch_config({"ctas_per_sm": c, "tc_warps": w})
+            except nat.SWEError as ex:
+                if ex.code == nat.SWE_EINVAL:     # that many warps' tiles do not fit on an SM
+                    continue
+                raise
+            s.step(1)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s.stream)
+            s.step(reps)
+            e1.record(s.stream)
+            torch.cuda.synchronize()
+            timings[(c, w)] = e0.elapsed_time(e1) / reps
+    finally:
+        s.close()
+    if not timings:
+        raise ValueError(f"tune: none of the launch shapes {cands} fits order {N} on this GPU")
     c, w = min(timings, key=timings.get)
     best = {"ctas_per_sm": c, "tc_warps": w}
     if full:
+        cache = _load_cache()            # re-read: another process may have added entries
         cache[key] = {"shape": best, "ms_per_macro_step": {f"{k[0]}/{k[1]}": v for k, v in timings.items()},
-                      "when": time.time()}
-        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
-        json.dump(cache, open(CACHE, "w"), indent=1, default=str)
+                      "sources": src, "when": time.time()}
+        _store_cache(cache)
     if verbose:
         print(f"autotune {key}: {timings} -> {best}")
     return best
