@@ -326,8 +326,9 @@ int swe_batch_workspace_bytes(swe_solver* const* solvers, int32_t n, int32_t max
  * (bytes >= swe_batch_workspace_bytes, 256-byte aligned; owned by the caller, not
  * freed by the library). stream: the batch's own non-default stream. The solvers
  * stay usable on their own; work issued on their streams is ordered before and
- * after a batch step. SWE_ENOMEM if the workspace is too small; SWE_EUNSUPPORTED
- * for a compensated solver (swe_params.compensated). */
+ * after a batch step. The batch keeps pointers to the solvers: destroy it before
+ * any of them. SWE_ENOMEM if the workspace is too small; SWE_EUNSUPPORTED for a
+ * compensated solver (swe_params.compensated). */
 int swe_batch_create(swe_solver* const* solvers, int32_t n, int32_t max_macro, void* dev_workspace,
                      size_t bytes, void* stream, swe_batch** out);
 

@@ -1888,7 +1888,8 @@ int swe_batch_create(swe_solver* const* solvers, int32_t n, int32_t max_macro, v
   if (!stream) return fail(SWE_EINVAL, "the batch needs a non-default stream");
   if (!dev_workspace || (reinterpret_cast<uintptr_t>(dev_workspace) & 255))
     return fail(SWE_EINVAL, "the batch workspace must be 256-byte aligned device memory");
-  std::unique_ptr<swe_batch> b(new (std::nothrow) swe_batch);
+  // every return before the end releases what was created so far (streams, events)
+  std::unique_ptr<swe_batch, void (*)(swe_batch*)> b(new (std::nothrow) swe_batch, swe_batch_destroy);
   if (!b) return fail(SWE_ENOMEM, "host allocation failed");
   b->solvers.assign(solvers, solvers + n);
   b->stream = reinterpret_cast<cudaStream_t>(stream);
@@ -1940,14 +1941,12 @@ int swe_batch_create(swe_solver* const* solvers, int32_t n, int32_t max_macro, v
   cudaError_t ce2 = cudaStreamEndCapture(b->stream, &graph);
   if (ce != cudaSuccess || ce2 != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
-    swe_batch_destroy(b.release());
     return fail(SWE_ECUDA, std::string("batch capture: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
   }
   ce = cudaGraphInstantiate(&b->graph, graph, 0);
   cudaGraphDestroy(graph);
   if (ce != cudaSuccess) {
     b->graph = nullptr;
-    swe_batch_destroy(b.release());
     return fail(SWE_ECUDA, std::string("batch instantiate: ") + cudaGetErrorString(ce));
   }
   *out = b.release();
