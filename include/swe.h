@@ -289,7 +289,11 @@ int swe_stats(const swe_solver* solver, double* mass, double* injected_mass,
 /* Checkpoint: swe_full_state_bytes gives the size of an opaque host buffer
  * holding the state, the Adams-Bashforth history and the substep counter;
  * restoring it into a solver created for the same mesh and parameters resumes
- * bit-identically. */
+ * bit-identically. swe_set_full_state needs the bathymetry set first and returns
+ * SWE_EINVAL, with the solver's state untouched, for a buffer smaller than
+ * swe_full_state_bytes, a buffer written for another mesh size, order, tier, scheme
+ * or compensation, or one whose section sizes, levels (1..nlevels_max), dt_min,
+ * time or step count are invalid. */
 int swe_full_state_bytes(const swe_solver* solver, size_t* bytes);
 int swe_get_full_state(const swe_solver* solver, void* host_buf, size_t bytes);
 int swe_set_full_state(swe_solver* solver, const void* host_buf, size_t bytes);

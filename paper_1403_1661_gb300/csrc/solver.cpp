@@ -1611,8 +1611,19 @@ int swe_set_full_state(swe_solver* s, const void* host_buf, size_t bytes) {
   if (std::memcmp(h.magic, "SWEGB300", 8) != 0 || h.K != s->K || h.N != s->N || h.precision != s->prm.precision ||
       h.scheme != s->prm.scheme || h.bytes_comp != comp_bytes(s))
     return fail(SWE_EINVAL, "checkpoint does not match this solver");
+  // every size and value taken from the buffer is checked before it is used: the
+  // sections must have this solver's layout (a corrupted header must not steer a
+  // copy past a workspace region or past the caller's buffer)
+  const uint64_t bq = 2 * 3 * (uint64_t)s->Np * s->KS * s->ts;
+  if (h.bytes_q != bq || h.bytes_ring != 3 * bq / 2 || h.bytes_qmid != (uint64_t)s->K * 3 * s->NPP * s->ts ||
+      h.bytes_means != (uint64_t)s->K * 4 * s->ts || h.bytes_dry != (uint64_t)s->K)
+    return fail(SWE_EINVAL, "checkpoint section sizes do not match this solver");
+  if (!(h.dt_min > 0) || !std::isfinite(h.dt_min) || !std::isfinite(h.t0) || h.k < 0 || h.dof_updates < 0)
+    return fail(SWE_EINVAL, "checkpoint holds an invalid time, step count or dt_min");
   std::vector<int32_t> lev(s->K);
   std::memcpy(lev.data(), p, (size_t)s->K * 4); p += (size_t)s->K * 4;
+  for (int32_t v : lev)
+    if (v < 1 || v > s->prm.nlevels_max) return fail(SWE_EINVAL, "checkpoint level out of 1..nlevels_max");
   s->have_state = false;  // no state to carry across the re-ordering
   if ((rc = apply_levels(s, lev, h.dt_min))) return rc;
   cudaStream_t st = s->stream;

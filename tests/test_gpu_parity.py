@@ -236,6 +236,45 @@ def test_checkpoint_inside_a_macro_step_bit_identical():
         assert np.array_equal(np.asarray(x), np.asarray(y))
 
 
+def test_corrupted_checkpoint_is_refused_and_the_state_kept():
+    """A checkpoint whose header sizes, levels, dt_min, time or step count are
+    invalid (or that is cut short) is refused with SWE_EINVAL before anything of the
+    solver changes; the intact checkpoint then still resumes bit for bit. Offsets:
+    the 112-byte header (magic, six int32, k and dof_updates int64, t0 and dt_min
+    double, six uint64 section sizes), then K int32 levels."""
+    import paper_1403_1661_gb300 as P
+    from paper_1403_1661_gb300 import _native as nat
+    scn = sc.tsunami(nx=40, ny=10, N=3, nlevels=4)
+    a = P.solver_from_scenario(scn, precision="fp32")
+    a.step(1)
+    ck = a.full_state()
+    b = P.solver_from_scenario(scn, precision="fp32")
+    b.step(2)
+    before = b.get_state()
+
+    def bad(offset, dtype, value):
+        c = ck.copy()
+        c[offset:offset + np.dtype(dtype).itemsize] = np.array([value], dtype).view(np.uint8)
+        return c
+    cases = {"magic": bad(0, np.uint8, 0), "k": bad(32, np.int64, -5), "t0": bad(48, np.float64, np.nan),
+             "dt_min": bad(56, np.float64, -1.0), "bytes_q": bad(64, np.uint64, 1 << 40),
+             "bytes_ring": bad(72, np.uint64, 8), "level 99": bad(112, np.int32, 99),
+             "level 0": bad(112 + 4 * 5, np.int32, 0), "short": ck[:-1]}
+    for name, c in cases.items():
+        with pytest.raises(nat.SWEError) as ei:
+            b.load_full_state(c)
+        assert ei.value.code == nat.SWE_EINVAL, name
+        for x, y in zip(before, b.get_state()):
+            assert np.array_equal(np.asarray(x), np.asarray(y)), name
+    b.load_full_state(ck)
+    a.step(1)
+    b.step(1)
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(np.asarray(x), np.asarray(y))
+    a.close()
+    b.close()
+
+
 def test_mass_conservation_and_stats():
     scn = sc.hump_square(n=16, N=3)
     _, _, model, integ, s = both(scn, "fp64")
