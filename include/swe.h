@@ -199,7 +199,7 @@ int swe_set_state(swe_solver* solver, const double* h, const double* hu, const d
 int swe_setup_levels(swe_solver* solver, int32_t* level_out, double* dt_min_out);
 
 /* Force a level assignment (K, caller order, values 1..nlevels_max) and the
- * finest step dt_min. Restarts the history. */
+ * finest step dt_min (finite, > 0). Restarts the history. SWE_EINVAL otherwise. */
 int swe_set_levels(swe_solver* solver, const int32_t* level, double dt_min);
 
 /* Regroup the elements into MRAB levels at the current level-synchronous time

@@ -1328,7 +1328,7 @@ int swe_regroup(swe_solver* s, const int32_t* level, int32_t* level_out, double*
 
 int swe_set_levels(swe_solver* s, const int32_t* level, double dt_min) {
   if (!s || !level) return fail(SWE_EINVAL, "NULL argument");
-  if (!(dt_min > 0)) return fail(SWE_EINVAL, "dt_min must be > 0");
+  if (!(dt_min > 0) || !std::isfinite(dt_min)) return fail(SWE_EINVAL, "dt_min must be finite and > 0");
   std::vector<int32_t> lev(level, level + s->K);
   for (int32_t v : lev)
     if (v < 1 || v > s->prm.nlevels_max) return fail(SWE_EINVAL, "level out of 1..nlevels_max");
