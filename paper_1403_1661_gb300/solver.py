@@ -33,6 +33,10 @@ class Mesh:
         self.vx = np.ascontiguousarray(vx, np.float64)
         self.vy = np.ascontiguousarray(vy, np.float64)
         self.EToV = np.ascontiguousarray(EToV, np.int32)
+        if self.vx.ndim != 1 or self.vx.shape != self.vy.shape:
+            raise ValueError("vx and vy must be 1-D arrays of the same length")
+        if self.EToV.ndim != 2 or self.EToV.shape[1] != 3:
+            raise ValueError("EToV must have shape (K, 3)")
         h = C.c_void_p()
         nat.check(L.swe_mesh_create(nat.dptr(self.vx), nat.dptr(self.vy), self.vx.size,
                                     nat.iptr(self.EToV), self.EToV.shape[0], C.byref(h)),
@@ -57,7 +61,8 @@ class Mesh:
 
     def levels(self, N, h, hu, hv, g, cfl, nlevels_max):
         """Level grouping (Section 4) the solver would make for this nodal state."""
-        h, hu, hv = (np.ascontiguousarray(a, np.float64) for a in (h, hu, hv))
+        np_ = (N + 1) * (N + 2) // 2
+        h, hu, hv = (np.ascontiguousarray(a, np.float64).reshape(self.K, np_) for a in (h, hu, hv))
         lev = np.zeros(self.K, np.int32)
         dtm = C.c_double()
         nat.check(nat.lib().swe_mesh_levels(self.handle, N, nat.dptr(h), nat.dptr(hu), nat.dptr(hv), g, cfl,
@@ -170,7 +175,7 @@ class Solver:
         return lev, dtm.value
 
     def set_levels(self, level, dt_min):
-        lev = np.ascontiguousarray(level, np.int32)
+        lev = np.ascontiguousarray(level, np.int32).reshape(self.K)
         nat.check(nat.lib().swe_set_levels(self.handle, nat.iptr(lev), float(dt_min)), "swe_set_levels")
         self.level = lev.copy()
 
@@ -193,7 +198,7 @@ class Solver:
         margin = C.c_double()
         lp = None
         if level is not None:
-            lv = np.ascontiguousarray(level, np.int32)
+            lv = np.ascontiguousarray(level, np.int32).reshape(self.K)
             lp = nat.iptr(lv)
         nat.check(nat.lib().swe_regroup(self.handle, lp, nat.iptr(out), C.byref(margin)), "swe_regroup")
         self.level = out

@@ -266,6 +266,10 @@ def test_corrupted_checkpoint_is_refused_and_the_state_kept():
         assert ei.value.code == nat.SWE_EINVAL, name
         for x, y in zip(before, b.get_state()):
             assert np.array_equal(np.asarray(x), np.asarray(y)), name
+    for dtm in (np.inf, np.nan, 0.0):
+        with pytest.raises(nat.SWEError) as ei:
+            b.set_levels(np.ones(b.K, np.int32), dtm)
+        assert ei.value.code == nat.SWE_EINVAL
     b.load_full_state(ck)
     a.step(1)
     b.step(1)

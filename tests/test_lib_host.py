@@ -188,3 +188,25 @@ def test_compensated_workspace_and_validation(lib):
     assert rc0 == rc1 == lib.SWE_OK and b0 == b1
     rc, _ = nbytes(lib.SWE_FP32, 2)
     assert rc == lib.SWE_EINVAL
+
+
+def test_binding_checks_array_shapes(lib):
+    """The Python layer refuses arrays whose shapes do not match the mesh before
+    the library reads them (the C calls take bare pointers and sizes)."""
+    from paper_1403_1661_gb300.solver import Mesh
+    vx, vy, E = meshes.structured_rect(0, 1, 0, 1, 3, 3)
+    with pytest.raises(ValueError):
+        Mesh(vx, vy[:-1], E)
+    with pytest.raises(ValueError):
+        Mesh(vx, vy, E[:, :2])
+    with pytest.raises(ValueError):
+        Mesh(vx, vy, E.reshape(-1))
+    m = Mesh(vx, vy, E)
+    h = np.ones((m.K, 10))                    # N = 3: 10 nodes per element
+    lev, dtm = m.levels(3, h, 0 * h, 0 * h, 9.81, 0.3, 3)
+    assert lev.shape == (m.K,) and dtm > 0
+    with pytest.raises(ValueError):
+        m.levels(3, h[:-1], 0 * h[:-1], 0 * h[:-1], 9.81, 0.3, 3)
+    with pytest.raises(ValueError):
+        m.levels(2, h, 0 * h, 0 * h, 9.81, 0.3, 3)  # N = 2 has 6 nodes per element
+    m.close()
