@@ -228,12 +228,15 @@ class Solver:
                   "swe_rhs_scratch_bytes")
         if need.value and scratch is None:
             scratch = torch.empty(need.value, dtype=torch.uint8, device=self.device)
+        elif need.value and (not scratch.is_cuda or scratch.device != torch.device(self.device)
+                             or not scratch.is_contiguous()):
+            raise ValueError("scratch must be a contiguous tensor on the solver's device")
         dt = torch.float64 if self.precision == nat.SWE_FP64 else torch.float32
         out = torch.empty((3, self.K, self.Np), dtype=dt, device=self.device)
         cur = torch.cuda.current_stream(self.device)
         self.stream.wait_stream(cur)
         sp = C.c_void_p(scratch.data_ptr()) if need.value else None
-        sb = scratch.numel() if need.value else 0
+        sb = scratch.numel() * scratch.element_size() if need.value else 0
         nat.check(nat.lib().swe_rhs_variant(self.handle, int(variant), C.c_void_p(out.data_ptr()), sp, sb),
                   "swe_rhs_variant")
         cur.wait_stream(self.stream)

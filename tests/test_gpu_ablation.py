@@ -69,6 +69,9 @@ def test_variant_argument_checks():
     with pytest.raises(nat.SWEError) as ei:
         s.rhs_variant(nat.SWE_RHS_SPLIT, small)
     assert ei.value.code == nat.SWE_ENOMEM
+    # host memory never reaches the kernels
+    with pytest.raises(ValueError):
+        s.rhs_variant(nat.SWE_RHS_SPLIT, torch.empty(need, dtype=torch.uint8))
     # a caller-provided scratch gives the same R as one allocated per call
     scratch = torch.empty(need, dtype=torch.uint8, device=s.device)
     a = s.rhs_variant(nat.SWE_RHS_SPLIT, scratch).cpu().numpy()
