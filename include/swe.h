@@ -143,7 +143,9 @@ int swe_mesh_connectivity(const swe_mesh* mesh, int32_t* EToE, int32_t* EToF);
 int swe_mesh_node_coords(const swe_mesh* mesh, int32_t N, double* x, double* y);
 
 /* The level grouping swe_setup_levels would make for nodal state (h, hu, hv)
- * (K x Np each, host, caller order): level_out (K, 1-based), dt_min_out. Host only. */
+ * (K x Np each, host, caller order): level_out (K, 1-based), dt_min_out. Host only.
+ * SWE_EINVAL for a non-finite value or a state without any positive depth (the CFL
+ * rule then has no wave speed). */
 int swe_mesh_levels(const swe_mesh* mesh, int32_t N, const double* h, const double* hu,
                     const double* hv, double g, double cfl, int32_t nlevels_max,
                     int32_t* level_out, double* dt_min_out);
@@ -154,7 +156,8 @@ int swe_mesh_levels(const swe_mesh* mesh, int32_t N, const double* h, const doub
  * with 2^{l-1} dt_min <= dt_k in 1..nlevels_max, at most old + 1, at most 1 + the
  * power of two in k; margin_out (may be NULL) = min_k dt_k / (2^{l_k - 1} dt_min).
  * Host arrays, read or written during the call only. SWE_EINVAL for NULL arrays,
- * K < 0, k < 0, dt_min <= 0 or nlevels_max outside 1..8. */
+ * K < 0, k < 0, dt_min not finite and > 0, a step dt_k not finite and > 0, a
+ * current level outside 1..nlevels_max or nlevels_max outside 1..8. */
 int swe_regroup_rule(const double* dt, const int32_t* level, int32_t K, double dt_min, int64_t k,
                      int32_t nlevels_max, int32_t* level_out, double* margin_out);
 
@@ -195,7 +198,9 @@ int swe_set_state(swe_solver* solver, const double* h, const double* hu, const d
  * dt_k = cfl/(N+1)^2 * H_k / a_k, H_k = the inradius, a_k = max over the
  * element's nodes of |u| + sqrt(g max(h, 1e-2 max h)); level l holds
  * 2^{l-1} dt_min <= dt_k < 2^l dt_min (capped at nlevels_max). level_out (K,
- * caller order, 1-based) and dt_min_out may be NULL. Restarts the history. */
+ * caller order, 1-based) and dt_min_out may be NULL. Restarts the history.
+ * SWE_ENAN, with nothing changed, if the state holds a non-finite value;
+ * SWE_EINVAL if it has no positive depth. */
 int swe_setup_levels(swe_solver* solver, int32_t* level_out, double* dt_min_out);
 
 /* Force a level assignment (K, caller order, values 1..nlevels_max) and the

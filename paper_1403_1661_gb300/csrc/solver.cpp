@@ -39,6 +39,20 @@ int fail(int code, const std::string& msg) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// The CFL rule (element_dt) needs a finite nodal state with some positive depth:
+// its maxima would pass over a NaN operand, and with no positive depth there is no
+// wave speed to bound the step. nonfinite_code: what a non-finite value returns.
+int check_cfl_input(const double* h, const double* hu, const double* hv, size_t n, int nonfinite_code) {
+  bool wet = false;
+  for (size_t i = 0; i < n; ++i) {
+    if (!std::isfinite(h[i]) || !std::isfinite(hu[i]) || !std::isfinite(hv[i]))
+      return fail(nonfinite_code, "non-finite state: the CFL rule needs finite values");
+    wet = wet || h[i] > 0.0;
+  }
+  if (!wet) return fail(SWE_EINVAL, "no positive depth: the CFL rule has no wave speed");
+  return SWE_OK;
+}
+
 int npp_of(int N) {
   int np = (N + 1) * (N + 2) / 2;
   return (np + 3) / 4 * 4;
@@ -1116,6 +1130,8 @@ int swe_mesh_levels(const swe_mesh* mesh, int32_t N, const double* h, const doub
   if (!mesh || !h || !hu || !hv || !level_out) return fail(SWE_EINVAL, "NULL argument");
   if (N < 1 || N > 7 || !(g > 0) || !(cfl > 0) || nlevels_max < 1 || nlevels_max > swe::kMaxLevels)
     return fail(SWE_EINVAL, "bad arguments");
+  const size_t np = (size_t)(N + 1) * (N + 2) / 2;
+  if (int rc = check_cfl_input(h, hu, hv, (size_t)mesh->m.K * np, SWE_EINVAL)) return rc;
   std::vector<double> dt;
   swe::element_dt(mesh->m, N, h, hu, hv, g, cfl, dt);
   std::vector<int32_t> lev;
@@ -1128,8 +1144,12 @@ int swe_mesh_levels(const swe_mesh* mesh, int32_t N, const double* h, const doub
 int swe_regroup_rule(const double* dt, const int32_t* level, int32_t K, double dt_min, int64_t k,
                      int32_t nlevels_max, int32_t* level_out, double* margin_out) {
   if (!dt || !level || !level_out || K < 0) return fail(SWE_EINVAL, "bad arguments");
-  if (!(dt_min > 0) || nlevels_max < 1 || nlevels_max > swe::kMaxLevels || k < 0)
+  if (!(dt_min > 0) || !std::isfinite(dt_min) || nlevels_max < 1 || nlevels_max > swe::kMaxLevels || k < 0)
     return fail(SWE_EINVAL, "bad arguments");
+  for (int32_t i = 0; i < K; ++i) {
+    if (!(dt[i] > 0) || !std::isfinite(dt[i])) return fail(SWE_EINVAL, "element steps must be finite and > 0");
+    if (level[i] < 1 || level[i] > nlevels_max) return fail(SWE_EINVAL, "level out of 1..nlevels_max");
+  }
   std::vector<double> d(dt, dt + K);
   std::vector<int32_t> old(level, level + K), lev;
   const double margin = swe::regroup_levels(d, dt_min, old, k, nlevels_max, lev);
@@ -1289,6 +1309,7 @@ int swe_setup_levels(swe_solver* s, int32_t* level_out, double* dt_min_out) {
   std::vector<double> h(n), hu(n), hv(n), dt;
   int rc = download_state(s, h.data(), hu.data(), hv.data());
   if (rc) return rc;
+  if ((rc = check_cfl_input(h.data(), hu.data(), hv.data(), n, SWE_ENAN))) return rc;
   swe::element_dt(s->mesh, s->N, h.data(), hu.data(), hv.data(), s->prm.g, s->prm.cfl, dt);
   std::vector<int32_t> lev;
   double dtmin = swe::assign_levels(dt, s->prm.nlevels_max, lev);

@@ -210,3 +210,49 @@ def test_binding_checks_array_shapes(lib):
     with pytest.raises(ValueError):
         m.levels(2, h, 0 * h, 0 * h, 9.81, 0.3, 3)  # N = 2 has 6 nodes per element
     m.close()
+
+
+def test_level_rules_refuse_invalid_input(lib):
+    """The CFL level rule and the regroup rule refuse what they cannot order: a
+    non-finite state (a NaN would otherwise drop out of the wave-speed maximum), a
+    state with no positive depth, non-finite or non-positive element steps and
+    current levels outside 1..nlevels_max."""
+    import ctypes as C
+    from paper_1403_1661_gb300.solver import Mesh
+    vx, vy, E = meshes.structured_rect(0, 1, 0, 1, 4, 4)
+    m = Mesh(vx, vy, E)
+    h = np.ones((m.K, 6))
+    z = np.zeros_like(h)
+    lev, dtm = m.levels(2, h, z, z, 9.81, 0.3, 3)
+    assert (lev >= 1).all() and np.isfinite(dtm) and dtm > 0
+    for bad in (np.nan, np.inf):
+        for which in range(3):
+            arrs = [h.copy(), z.copy(), z.copy()]
+            arrs[which][3, 2] = bad
+            with pytest.raises(lib.SWEError) as ei:
+                m.levels(2, *arrs, 9.81, 0.3, 3)
+            assert ei.value.code == lib.SWE_EINVAL
+    with pytest.raises(lib.SWEError) as ei:
+        m.levels(2, 0 * h, z, z, 9.81, 0.3, 3)           # dry everywhere
+    assert ei.value.code == lib.SWE_EINVAL
+    m.close()
+
+    K = 16
+    dt = np.full(K, 0.5)
+    old = np.ones(K, np.int32)
+    out = np.zeros(K, np.int32)
+    margin = C.c_double()
+
+    def rule(dt, old, dt_min=0.25, nl=3):
+        return lib.lib().swe_regroup_rule(lib.dptr(dt), lib.iptr(old), K, dt_min, 8, nl, lib.iptr(out),
+                                          C.byref(margin))
+    assert rule(dt, old) == lib.SWE_OK and (out == 2).all()
+    for v in (np.nan, np.inf, 0.0, -1.0):
+        d = dt.copy()
+        d[5] = v
+        assert rule(d, old) == lib.SWE_EINVAL
+    for v in (0, -1, 4):
+        o = old.copy()
+        o[7] = v
+        assert rule(dt, o) == lib.SWE_EINVAL
+    assert rule(dt, old, dt_min=np.inf) == lib.SWE_EINVAL
